@@ -1,0 +1,418 @@
+"""Benchmark of the pair-distance histogram on GB300.
+
+One step = the three headline frames (N = 1,000,000 particles, 1 species,
+uniform at density 0.1, 10,000 bins; no box, orthorhombic and triclinic cell)
+through one dh_histogram_batch call (one persistent pair-kernel launch for all
+three frames), inputs resident in HBM.  Printed on one JSON line:
+
+  value          Gpairs/s of the batched step (device time, CUDA events)
+  e2e            the same metric through the C ABI with pinned HOST buffers:
+                 host->device copy of the coordinates and device->host copy of
+                 the histograms inside the timed region
+  plain          per-frame dh_histogram Gpairs/s for each box type
+  roofline       ALU-bound roofline of the pair kernel
+  cpu_baseline   the FP64 oracle on the host cores, on a bounded sample
+  clocks         nvidia-smi SM clocks and throttle reasons during the timed region
+
+``--impl reference`` times the FP64 oracle (the reference arm of this build) on
+bounded samples of the same workload instead.  Under torchrun each rank runs its
+own replica (frames are independent; no data-path collective) and rank 0
+reports the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as w  # noqa: E402
+
+METRIC = "Gpairs/s binned at N=1M (plain vs batched/served) + p50/p99 frame latency, 1 GB300"
+UNIT = "Gpairs/s"
+BOXES = (w.BOX_NONE, w.BOX_ORTHO, w.BOX_TRICLINIC)
+
+# Algorithmic operations per evaluated pair (float32-pipe-equivalent), from the
+# definition: none: 3 sub, 3 mul/fma for r^2, sqrt, scale, floor, bin compare = 10;
+# orthorhombic: + 3 x (mul by 1/L, nearest integer, fma) = 19; triclinic
+# (single wrap below half the plane spacing): + back substitution (6),
+# 3 nearest integers, d - B k (9) = 28; plus one shared-memory increment for each
+# pair inside r_max.
+OPS_PER_PAIR = {w.BOX_NONE: 10.0, w.BOX_ORTHO: 19.0, w.BOX_TRICLINIC: 28.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def alu_peak_tops(sm_count: int, mhz: float) -> float:
+    return sm_count * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as td
+
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    td.init_process_group(backend=backend)
+    return td
+
+
+def max_over_ranks(td, value: float, device=None) -> float:
+    if td is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(td, value: float, device=None) -> float:
+    if td is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle timing
+
+
+def oracle_sample(frames: list, seconds: float, nthreads: int) -> dict:
+    """Time the FP64 oracle on leading subsets of each frame (same box, r_max, nbins).
+
+    The subset size is calibrated so the three frames together take about
+    `seconds` of wall time on `nthreads` host threads.
+    """
+    import oracle
+
+    rates = []
+    for f in frames:
+        n0 = 1500
+        sub = w.frame_from(f.coords[:n0], [0, n0], f.box_type, f.box, f.r_max, f.nbins)
+        t0 = time.perf_counter()
+        oracle.histogram_frame(sub, nthreads=nthreads)
+        dt = max(time.perf_counter() - t0, 1e-4)
+        rates.append(sub.n_pairs() / dt)
+    per = seconds / len(frames)
+    total_pairs, total_t, sizes = 0, 0.0, []
+    for f, rate in zip(frames, rates):
+        n = int(min(f.n, max(2000, math.sqrt(2.0 * rate * per))))
+        sub = w.frame_from(f.coords[:n], [0, n], f.box_type, f.box, f.r_max, f.nbins)
+        t0 = time.perf_counter()
+        oracle.histogram_frame(sub, nthreads=nthreads)
+        total_t += time.perf_counter() - t0
+        total_pairs += sub.n_pairs()
+        sizes.append(n)
+    return {"gpairs_s": total_pairs / total_t / 1e9, "seconds": total_t, "pairs": total_pairs,
+            "sizes": sizes}
+
+
+def workload_config(args, world: int) -> dict:
+    return {"workload": f"N={args.n} uniform density 0.1, 1 species, {args.nbins} bins; "
+                        "one none + one ortho + one triclinic frame per step (dh_histogram_batch)",
+            "n": args.n, "nbins": args.nbins, "frames_per_step": 3,
+            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"}
+
+
+def headline_frames(n: int, nbins: int) -> list:
+    return [w.headline_frame(b, seed=11 + b, n=n, nbins=nbins) for b in BOXES]
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle as it stands, on the host cores."""
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    frames = headline_frames(args.n, args.nbins)
+    nthreads = os.cpu_count() or 1
+    per_step = args.ref_seconds
+    # calibrate once, then each step evaluates the same bounded sample
+    cal = oracle_sample(frames, per_step, nthreads)
+    subs = [w.frame_from(f.coords[:n], [0, n], f.box_type, f.box, f.r_max, f.nbins)
+            for f, n in zip(frames, cal["sizes"])]
+    pairs_step = sum(s.n_pairs() for s in subs)
+    for _ in range(args.warmup):
+        for s in subs:
+            oracle.histogram_frame(s, nthreads=nthreads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s in subs:
+            oracle.histogram_frame(s, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    value = pairs_step * args.steps / dt / 1e9
+    sample = (f"leading subsets N={cal['sizes']} of the three N={args.n} frames "
+              f"(none/ortho/triclinic, same box, r_max, {args.nbins} bins)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, world),
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import paper_1808_01478_gb300 as dh
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    td = init_dist(world, "nccl")
+    frames = headline_frames(args.n, args.nbins)
+    pairs = [f.n_pairs() for f in frames]
+    pairs_step = sum(pairs)
+
+    ctx = dh.Context(local, flags=dh.DH_CFG_TIMING)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.set_stream(stream)
+    X = [torch.from_numpy(f.coords).to(dev) for f in frames]
+    OUT = [torch.zeros((1, f.nbins), dtype=torch.int64, device=dev) for f in frames]
+    fas = [dh.FrameArgs(X[k], f.offsets, f.box_type, f.box, f.r_max, f.nbins, OUT[k])
+           for k, f in enumerate(frames)]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+
+    # ---- batched step (headline value)
+    for _ in range(args.warmup):
+        ctx.histogram_batch(fas)
+    stats_b = ctx.stats()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if td:
+        td.barrier()
+    torch.cuda.synchronize()
+    step_ms, pair_ms = [], []
+    for _ in range(args.steps):
+        flush_l2()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.histogram_batch(fas)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        pair_ms.append(ctx.stats()["pair_kernel_ms"])
+    torch.cuda.synchronize()
+    if td:
+        td.barrier()
+    clocks = sampler.stop()
+    t_total = max_over_ranks(td, sum(step_ms) / 1e3, dev)
+    all_pairs = sum_over_ranks(td, float(pairs_step * args.steps), dev)
+    value = all_pairs / t_total / 1e9
+    hist_sums = [int(o.sum().item()) for o in OUT]
+
+    # ---- roofline of the pair kernel (device time of its launches in the timed steps)
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    ops = sum(p * (OPS_PER_PAIR[f.box_type] + hs / p) for f, p, hs in zip(frames, pairs, hist_sums))
+    mean_pair_s = statistics.mean(pair_ms) / 1e3
+    achieved = ops / mean_pair_s / 1e12
+    peak = alu_peak_tops(SM_COUNT, sm_max)
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "dh::pair_kernel", "ops_per_step": ops,
+                "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max clock)"}
+
+    # ---- plain per-frame path
+    plain = {}
+    for k, f in enumerate(frames):
+        for _ in range(1):
+            ctx.histogram(X[k], f.offsets, f.box_type, f.box, f.r_max, f.nbins, OUT[k])
+        ts = []
+        for _ in range(max(1, args.plain_steps)):
+            flush_l2()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.histogram(X[k], f.offsets, f.box_type, f.box, f.r_max, f.nbins, OUT[k])
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        st = ctx.stats()
+        plain[w.BOX_NAMES[f.box_type]] = {
+            "gpairs_s": round(pairs[k] / (statistics.mean(ts) / 1e3) / 1e9, 3),
+            "ms": round(statistics.mean(ts), 3),
+            "deferred_frac": round(st["deferred"] / max(1, st["pairs"]), 6),
+        }
+
+    # ---- end to end through the C ABI with pinned host buffers
+    hx = [torch.from_numpy(f.coords).pin_memory() for f in frames]
+    ho = [torch.zeros((1, f.nbins), dtype=torch.int64).pin_memory() for f in frames]
+    hfas = [dh.FrameArgs(hx[k].numpy(), f.offsets, f.box_type, f.box, f.r_max, f.nbins,
+                         ho[k].numpy().view(np.uint64)) for k, f in enumerate(frames)]
+    ctx.histogram_batch(hfas)
+    if td:
+        td.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.histogram_batch(hfas)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(td, time.perf_counter() - t0, dev)
+    e2e_val = sum_over_ranks(td, float(pairs_step * args.e2e_steps), dev) / e2e_s / 1e9
+    e2e_ok = all(int(ho[k].sum()) == hist_sums[k] for k in range(len(frames)))
+    h2d = sum(f.n * 12 for f in frames)
+    d2h = sum(f.nbins * 8 for f in frames)
+
+    launches_per_step = stats_b["kernel_launches"]
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_total / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (binary64 re-decision of near-edge pairs)", "data": "synthetic",
+        "config": dict(workload_config(args, world), pairs_per_step=pairs_step),
+        "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "matches_device_result": e2e_ok},
+        "plain": plain,
+        "batched": {"gpairs_s": round(value, 3), "deferred_frac": round(stats_b["deferred"] / max(1, stats_b["pairs"]), 6)},
+        "served": None,
+        "roofline": roofline,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        nthreads = os.cpu_count() or 1
+        cb = oracle_sample(frames, args.cpu_seconds, nthreads)
+        line["cpu_baseline"] = {"value": round(cb["gpairs_s"], 6), "unit": UNIT, "cores": nthreads,
+                                "kind": "oracle",
+                                "sample": f"leading subsets N={cb['sizes']} of the three frames, "
+                                          f"{cb['pairs']} pairs in {cb['seconds']:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if td:
+        td.destroy_process_group()
+    return 0
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["dh", "reference"], default="dh")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--nbins", type=int, default=10_000)
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * dh.h — C ABI of the GB300 particle-pair distance histogram library (libdh.so).
+ *
+ * What it computes (Reuter & Koefinger, "CADISHI", Sec. 2):
+ *   For one trajectory frame of N particles split into S species (contiguous
+ *   segments of the coordinate array), every unique pair is binned by its
+ *   distance: intra-species pairs i < j (single-species variant of Alg. 1,
+ *   Sec. 2.2) and inter-species pairs, all i in species a and j in species b
+ *   (Alg. 1).  Periodic boxes apply the minimum image convention of Eq. 5
+ *   (orthorhombic: diagonal B, Sec. 2.3; triclinic: general B plus the
+ *   neighbouring-cell search of Sec. 2.3).  The bin of a pair is
+ *   kappa = (int) nbins * r / r_max (Alg. 1), bins are half open
+ *   [kappa dr, (kappa+1) dr) (Eq. 4), and pairs with kappa >= nbins are not
+ *   counted.  Counts are exact unsigned 64-bit integers.
+ *
+ * Exactness: the result equals, bin for bin, the histogram obtained when every
+ * step above is evaluated in IEEE binary64 in this order: d = xj - xi
+ * (coordinates promoted exactly from float32); orthorhombic
+ * k = nearbyint(d * (1/L)), d = fma(-k, L, d); triclinic s = B^-1 d by back
+ * substitution, k = nearbyint(s), d -= B k, then the minimum of |d + B m|^2
+ * over m in {-1,0,1}^3; r^2 = fma(dz,dz, fma(dy,dy, dx*dx));
+ * kappa = floor((nbins * sqrt(r^2)) / r_max).  Most pairs are decided in
+ * float32 arithmetic whose error is bounded; pairs whose float32 value lies
+ * within that bound of a bin edge are re-decided with higher precision.
+ *
+ * Histogram order: the S(S+1)/2 histograms of species pairs (a,b), a <= b, are
+ * stored one after another in the order (0,0),(0,1),...,(0,S-1),(1,1),...,
+ * i.e. histogram h(a,b) = a*S - a*(a-1)/2 + (b-a) occupies
+ * out[h*nbins .. h*nbins + nbins).
+ *
+ * Box matrix: 9 doubles, row-major 3x3 whose COLUMNS are the box vectors
+ * a, b, c (the matrix B of Eq. 5).  DH_BOX_ORTHO requires a diagonal B with
+ * positive entries.  DH_BOX_TRICLINIC requires an upper-triangular B
+ * (a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz)) with positive diagonal, in
+ * reduced form: |bx| <= ax/2, |cx| <= ax/2, |cy| <= by/2.
+ *
+ * Errors: every entry point returns a dh_status; nothing throws across the
+ * ABI.  On DH_ERR_* the output buffer is unspecified (it may be partly
+ * written) and dh_last_error() describes the failure.
+ *
+ * Threads: one dh_ctx may be used from several host threads; calls on one
+ * context are serialised internally.
+ */
+#ifndef DH_H
+#define DH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DH_OK = 0,
+  DH_PENDING = 1,          /* dh_poll: the request has not finished yet */
+  DH_ERR_INVALID = -1,     /* bad argument: offsets, nbins, r_max, box, non-finite coordinates */
+  DH_ERR_NOMEM = -2,       /* device or pinned host memory could not be obtained */
+  DH_ERR_CUDA = -3,        /* a CUDA call failed (message in dh_last_error) */
+  DH_ERR_TIMEOUT = -4,     /* dh_wait ran out of time, or a device wait gave up */
+  DH_ERR_CANCELLED = -5,   /* the request was cancelled before it finished */
+  DH_ERR_NOTFOUND = -6     /* unknown ticket */
+} dh_status;
+
+typedef enum { DH_BOX_NONE = 0, DH_BOX_ORTHO = 1, DH_BOX_TRICLINIC = 2 } dh_box_type;
+
+/* dh_frame.flags */
+#define DH_DEVICE_PTRS 0x1u /* coords and out are device pointers (same device as the context) */
+#define DH_ACCUMULATE 0x2u  /* add into out instead of overwriting it */
+#define DH_COORDS_F4 0x4u   /* coords are n x 4 floats (x,y,z,ignored) instead of n x 3 */
+
+/* dh_config.flags */
+#define DH_CFG_NO_GRAPH 0x1u /* batched path: launch directly instead of replaying a CUDA graph */
+#define DH_CFG_TIMING 0x2u   /* record CUDA events around the pair-kernel launches (dh_stats.pair_kernel_ms) */
+
+typedef struct dh_ctx dh_ctx;
+
+typedef struct {
+  int32_t device;        /* CUDA device ordinal */
+  uint64_t pool_bytes;   /* served path: device memory the admission control may use (0: 1/2 of free) */
+  int32_t max_inflight;  /* served path: most requests resident on the device at once (0: 64) */
+  uint64_t timeout_ns;   /* served path: bound on device-side waits (0: 2 s) */
+  const char* tune_cache;/* autotuner cache file, or NULL for in-memory only */
+  uint32_t flags;        /* DH_CFG_* */
+} dh_config;
+
+typedef struct {
+  const float* coords;             /* n x 3 (or n x 4 with DH_COORDS_F4) float32, species contiguous */
+  int64_t n;                       /* number of particles, >= 0 */
+  const int64_t* species_offsets;  /* HOST array of n_species+1 entries: 0 = o[0] <= o[1] <= ... <= o[S] = n */
+  int32_t n_species;               /* S >= 1 */
+  int32_t box_type;                /* dh_box_type */
+  double box[9];                   /* box matrix (ignored for DH_BOX_NONE) */
+  double r_max;                    /* upper end of the histogram, > 0 and finite */
+  int32_t nbins;                   /* number of bins, 1 <= nbins <= DH_MAX_BINS */
+  uint64_t* out;                   /* S(S+1)/2 x nbins counts */
+  uint32_t flags;                  /* DH_DEVICE_PTRS | DH_ACCUMULATE | DH_COORDS_F4 */
+} dh_frame;
+
+#define DH_MAX_BINS 4194304
+
+/* Per-context statistics of the most recent dh_histogram / dh_histogram_batch call. */
+typedef struct {
+  uint64_t pairs;          /* unique pairs evaluated */
+  uint64_t deferred;       /* pairs whose float32 value fell within the error bound of an edge */
+  uint64_t exact_fallback; /* deferred pairs that needed the binary64 replay */
+  int32_t sweeps;          /* passes over the pairs (histogram wider than shared memory) */
+  int32_t blocks;          /* CUDA blocks launched for the pair kernel */
+  int32_t items;           /* work items (tile pairs) */
+  int32_t kernel_launches; /* kernels launched by the call */
+  double pair_kernel_ms;   /* device time of the pair-kernel launches (needs DH_CFG_TIMING), else 0 */
+} dh_stats;
+
+/* Create a context on config->device (NULL: device 0, defaults).  Owns a CUDA
+ * stream, device workspace and pinned host staging buffers, all released by
+ * dh_destroy.  *out receives the context. */
+dh_status dh_create(const dh_config* config, dh_ctx** out);
+
+/* Release everything the context owns.  Pending served requests are cancelled. */
+dh_status dh_destroy(dh_ctx* ctx);
+
+/* Use the given cudaStream_t (passed as void*) for subsequent device work of
+ * dh_histogram / dh_histogram_batch; NULL restores the context's own stream. */
+dh_status dh_set_stream(dh_ctx* ctx, void* stream);
+
+/* Histograms of one frame: Alg. 1 (Sec. 2.2) over every species pair, with
+ * the minimum image of Eq. 5 for periodic boxes and the bins of Eq. 4.
+ * Synchronous: on return, out holds the result.  With DH_DEVICE_PTRS the work
+ * runs on the context stream and the call waits for it. */
+dh_status dh_histogram(dh_ctx* ctx, const dh_frame* frame);
+
+/* Like dh_histogram, but with DH_DEVICE_PTRS it only enqueues the work on the
+ * context stream and returns; errors found on the device are reported by the
+ * next synchronous call (or dh_sync). */
+dh_status dh_histogram_async(dh_ctx* ctx, const dh_frame* frame);
+
+/* Wait for work enqueued by dh_histogram_async and report device-side errors. */
+dh_status dh_sync(dh_ctx* ctx);
+
+/* k frames of possibly different N, species, box and nbins through one
+ * persistent launch per bin sweep.  All frames must use the same pointer kind
+ * (all DH_DEVICE_PTRS or none).  Synchronous. */
+dh_status dh_histogram_batch(dh_ctx* ctx, const dh_frame* frames, int32_t k);
+
+/* Served path: submit one frame as a request.  Coordinates and output stay on
+ * the device (DH_DEVICE_PTRS) or are staged by the library (host pointers);
+ * the caller's buffers must stay valid and unmodified until dh_poll/dh_wait
+ * report a final status.  Admission is by device-memory footprint; requests
+ * that do not fit wait in a queue.  *ticket identifies the request. */
+dh_status dh_submit(dh_ctx* ctx, const dh_frame* frame, uint64_t* ticket);
+
+/* DH_PENDING while the request runs, then its final status (once). */
+dh_status dh_poll(dh_ctx* ctx, uint64_t ticket);
+
+/* Block until the request finishes or timeout_ns passes (DH_ERR_TIMEOUT). */
+dh_status dh_wait(dh_ctx* ctx, uint64_t ticket, uint64_t timeout_ns);
+
+/* Cancel a queued or running request; its output is left unspecified. */
+dh_status dh_cancel(dh_ctx* ctx, uint64_t ticket);
+
+/* Statistics of the last dh_histogram / dh_histogram_batch call on ctx. */
+dh_status dh_get_stats(dh_ctx* ctx, dh_stats* stats);
+
+/* Message describing the last error on this host thread (owned by the library). */
+const char* dh_last_error(dh_ctx* ctx);
+
+/* Host-only helper, no GPU needed: the binary64 bin thresholds used for exact
+ * decisions.  thresholds[0] = 0 and, for 1 <= k <= nbins, thresholds[k] is the
+ * smallest binary64 value q >= 0 with floor((nbins * sqrt(q)) / r_max) >= k;
+ * a pair with r^2 = q lies in bin k iff thresholds[k] <= q < thresholds[k+1],
+ * and is counted iff q < thresholds[nbins].  thresholds must hold nbins+1 doubles. */
+dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds);
+
+/* Library version string. */
+const char* dh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DH_H */

@@ -1,0 +1,315 @@
+"""Python binding of libdh, the GB300 particle-pair distance histogram library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libdh.so`` (see ``include/dh.h``).  The functions keep the C names
+(``dh_create``, ``dh_histogram``, ...); :class:`Context` wraps them for numpy
+arrays (host pointers) and torch CUDA tensors (device pointers).  There is no
+CPU fallback: if the library has not been built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdh.so")
+
+DH_OK = 0
+DH_PENDING = 1
+DH_ERR_INVALID = -1
+DH_ERR_NOMEM = -2
+DH_ERR_CUDA = -3
+DH_ERR_TIMEOUT = -4
+DH_ERR_CANCELLED = -5
+DH_ERR_NOTFOUND = -6
+
+DH_BOX_NONE = 0
+DH_BOX_ORTHO = 1
+DH_BOX_TRICLINIC = 2
+
+DH_DEVICE_PTRS = 0x1
+DH_ACCUMULATE = 0x2
+DH_COORDS_F4 = 0x4
+DH_CFG_NO_GRAPH = 0x1
+DH_CFG_TIMING = 0x2
+DH_MAX_BINS = 4194304
+
+STATUS_NAMES = {0: "DH_OK", 1: "DH_PENDING", -1: "DH_ERR_INVALID", -2: "DH_ERR_NOMEM",
+                -3: "DH_ERR_CUDA", -4: "DH_ERR_TIMEOUT", -5: "DH_ERR_CANCELLED",
+                -6: "DH_ERR_NOTFOUND"}
+
+
+class dh_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("pool_bytes", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_int32), ("timeout_ns", ctypes.c_uint64),
+                ("tune_cache", ctypes.c_char_p), ("flags", ctypes.c_uint32)]
+
+
+class dh_frame(ctypes.Structure):
+    _fields_ = [("coords", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("species_offsets", ctypes.c_void_p), ("n_species", ctypes.c_int32),
+                ("box_type", ctypes.c_int32), ("box", ctypes.c_double * 9),
+                ("r_max", ctypes.c_double), ("nbins", ctypes.c_int32),
+                ("out", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class dh_stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_uint64), ("deferred", ctypes.c_uint64),
+                ("exact_fallback", ctypes.c_uint64), ("sweeps", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("items", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32), ("pair_kernel_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DHError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGNATURES = {
+    "dh_create": ([ctypes.POINTER(dh_config), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "dh_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "dh_set_stream": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dh_histogram": ([ctypes.c_void_p, ctypes.POINTER(dh_frame)], ctypes.c_int),
+    "dh_histogram_async": ([ctypes.c_void_p, ctypes.POINTER(dh_frame)], ctypes.c_int),
+    "dh_sync": ([ctypes.c_void_p], ctypes.c_int),
+    "dh_histogram_batch": ([ctypes.c_void_p, ctypes.POINTER(dh_frame), ctypes.c_int32], ctypes.c_int),
+    "dh_submit": ([ctypes.c_void_p, ctypes.POINTER(dh_frame), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "dh_poll": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "dh_wait": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64], ctypes.c_int),
+    "dh_cancel": ([ctypes.c_void_p, ctypes.c_uint64], ctypes.c_int),
+    "dh_get_stats": ([ctypes.c_void_p, ctypes.POINTER(dh_stats)], ctypes.c_int),
+    "dh_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
+    "dh_bin_thresholds": ([ctypes.c_double, ctypes.c_int32, ctypes.c_void_p], ctypes.c_int),
+    "dh_version": ([], ctypes.c_char_p),
+}
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libdh.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libdh.so not found at {p}: build it with "
+                               "`python -m paper_1808_01478_gb300.build`")
+        lib = ctypes.CDLL(p)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+def _check(status: int, ctx=None) -> int:
+    if status < 0:
+        msg = load_library().dh_last_error(ctx).decode(errors="replace")
+        raise DHError(status, msg)
+    return status
+
+
+# ---------------------------------------------------------------- C-named functions
+
+
+def dh_version() -> str:
+    return load_library().dh_version().decode()
+
+
+def dh_bin_thresholds(r_max: float, nbins: int) -> np.ndarray:
+    out = np.empty(int(nbins) + 1, dtype=np.float64)
+    _check(load_library().dh_bin_thresholds(float(r_max), int(nbins), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def dh_create(device: int = 0, pool_bytes: int = 0, max_inflight: int = 0, timeout_ns: int = 0,
+              flags: int = 0) -> ctypes.c_void_p:
+    cfg = dh_config(device, pool_bytes, max_inflight, timeout_ns, None, flags)
+    h = ctypes.c_void_p()
+    _check(load_library().dh_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def dh_destroy(ctx) -> None:
+    _check(load_library().dh_destroy(ctx))
+
+
+def dh_set_stream(ctx, stream_ptr: int | None) -> None:
+    _check(load_library().dh_set_stream(ctx, ctypes.c_void_p(stream_ptr or 0)), ctx)
+
+
+def dh_histogram(ctx, frame: dh_frame) -> None:
+    _check(load_library().dh_histogram(ctx, ctypes.byref(frame)), ctx)
+
+
+def dh_histogram_async(ctx, frame: dh_frame) -> None:
+    _check(load_library().dh_histogram_async(ctx, ctypes.byref(frame)), ctx)
+
+
+def dh_sync(ctx) -> None:
+    _check(load_library().dh_sync(ctx), ctx)
+
+
+def dh_histogram_batch(ctx, frames) -> None:
+    arr = (dh_frame * len(frames))(*frames)
+    _check(load_library().dh_histogram_batch(ctx, arr, len(frames)), ctx)
+
+
+def dh_submit(ctx, frame: dh_frame) -> int:
+    t = ctypes.c_uint64()
+    _check(load_library().dh_submit(ctx, ctypes.byref(frame), ctypes.byref(t)), ctx)
+    return int(t.value)
+
+
+def dh_poll(ctx, ticket: int) -> int:
+    return load_library().dh_poll(ctx, ticket)
+
+
+def dh_wait(ctx, ticket: int, timeout_ns: int) -> int:
+    return load_library().dh_wait(ctx, ticket, timeout_ns)
+
+
+def dh_cancel(ctx, ticket: int) -> int:
+    return load_library().dh_cancel(ctx, ticket)
+
+
+def dh_get_stats(ctx) -> dict:
+    s = dh_stats()
+    _check(load_library().dh_get_stats(ctx, ctypes.byref(s)), ctx)
+    return s.as_dict()
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def n_hist(n_species: int) -> int:
+    return n_species * (n_species + 1) // 2
+
+
+class FrameArgs:
+    """Keeps the buffers referenced by one dh_frame alive."""
+
+    def __init__(self, coords, offsets, box_type, box, r_max, nbins, out=None, accumulate=False):
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        s = offs.shape[0] - 1
+        self.offsets = offs
+        self.keep = [offs]
+        flags = 0
+        if _is_torch(coords) and coords.is_cuda:
+            import torch
+            assert coords.dtype == torch.float32 and coords.is_contiguous()
+            if coords.dim() == 2 and coords.shape[1] == 4:
+                flags |= DH_COORDS_F4
+            n = coords.shape[0]
+            if out is None:
+                out = torch.zeros((n_hist(s), int(nbins)), dtype=torch.int64, device=coords.device)
+            assert out.is_cuda and out.is_contiguous() and out.element_size() == 8
+            flags |= DH_DEVICE_PTRS
+            cptr, optr = coords.data_ptr(), out.data_ptr()
+        else:
+            c = np.ascontiguousarray(coords, dtype=np.float32)
+            if c.ndim == 2 and c.shape[1] == 4:
+                flags |= DH_COORDS_F4
+            n = c.shape[0]
+            if out is None:
+                out = np.zeros((n_hist(s), int(nbins)), dtype=np.uint64)
+            assert out.flags.c_contiguous and out.dtype.itemsize == 8
+            self.keep.append(c)
+            cptr = c.ctypes.data if n else 0
+            optr = out.ctypes.data if _is_torch(out) is False else out.data_ptr()
+        if accumulate:
+            flags |= DH_ACCUMULATE
+        bx = np.zeros(9) if box is None else np.asarray(box, dtype=np.float64).reshape(9)
+        self.out = out
+        self.frame = dh_frame(cptr, int(n), offs.ctypes.data, s, int(box_type),
+                              (ctypes.c_double * 9)(*bx.tolist()), float(r_max), int(nbins), optr, flags)
+
+
+class Context:
+    """One libdh context (device workspace, stream, threshold cache)."""
+
+    def __init__(self, device: int = 0, **cfg):
+        self.handle = dh_create(device, **cfg)
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            dh_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream) -> None:
+        ptr = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        dh_set_stream(self.handle, ptr)
+
+    def histogram(self, coords, offsets, box_type, box, r_max, nbins, out=None, accumulate=False):
+        fa = FrameArgs(coords, offsets, box_type, box, r_max, nbins, out, accumulate)
+        dh_histogram(self.handle, fa.frame)
+        return fa.out
+
+    def histogram_frame(self, frame, out=None, device_tensors=None):
+        """Histogram of a workloads.Frame (host arrays unless device_tensors=(coords, out))."""
+        if device_tensors is not None:
+            coords, out = device_tensors
+            return self.histogram(coords, frame.offsets, frame.box_type, frame.box, frame.r_max,
+                                  frame.nbins, out)
+        return self.histogram(frame.coords, frame.offsets, frame.box_type, frame.box, frame.r_max,
+                              frame.nbins, out)
+
+    def histogram_async(self, coords, offsets, box_type, box, r_max, nbins, out):
+        fa = FrameArgs(coords, offsets, box_type, box, r_max, nbins, out)
+        dh_histogram_async(self.handle, fa.frame)
+        return fa
+
+    def sync(self):
+        dh_sync(self.handle)
+
+    def histogram_batch(self, frame_args: list[FrameArgs]) -> None:
+        dh_histogram_batch(self.handle, [fa.frame for fa in frame_args])
+
+    def stats(self) -> dict:
+        return dh_get_stats(self.handle)
+
+    # served path
+    def submit(self, fa: FrameArgs) -> int:
+        return dh_submit(self.handle, fa.frame)
+
+    def poll(self, ticket: int) -> int:
+        return dh_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_ns: int = 60_000_000_000) -> int:
+        return dh_wait(self.handle, ticket, timeout_ns)
+
+    def cancel(self, ticket: int) -> int:
+        return dh_cancel(self.handle, ticket)

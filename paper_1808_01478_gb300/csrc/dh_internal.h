@@ -1,0 +1,96 @@
+// Internal interface between the host runtime (dh_runtime.cpp) and the CUDA
+// kernels (dh_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dh {
+
+// Kernel variants of the minimum-image step (Eq. 5).
+enum Variant : int32_t {
+  V_NONE = 0,         // no periodic box
+  V_ORTHO = 1,        // diagonal B: per-axis nearest image
+  V_TRIC = 2,         // triclinic, r_max below half the smallest plane spacing: one wrap
+  V_TRIC_SEARCH = 3,  // triclinic, larger r_max: Eq. 5 wrap plus the 27-image search
+};
+
+constexpr int kBlock = 256;          // threads per block of the pair kernel
+constexpr int kRegI = 4;             // i-particles held in registers per thread
+constexpr int kTile = kBlock * kRegI;  // particles per tile edge (i and j)
+constexpr int kWarps = kBlock / 32;
+constexpr int kQueueCap = 64;        // deferred pairs per warp queue
+
+// One frame as seen by the device.  Host fills the first part; the staging and
+// setup kernels fill the second.
+struct FrameDev {
+  const float4* X;   // packed coordinates (x,y,z,0), frame-local index
+  uint64_t* out;     // S(S+1)/2 x nbins histograms of this frame
+  const double* T;   // binary64 thresholds T[0..nbins]
+  int32_t variant;
+  int32_t nbins;
+  int32_t n;         // particles
+  int32_t sweep_width;  // bins per sweep (pass p covers [p*w, min(nbins,(p+1)*w)))
+  double r_max;
+  double B[9];       // row-major, columns a,b,c
+  double Linv[3];    // orthorhombic: 1.0/L per axis, binary64
+  float Bf[9];       // float32 copies of B
+  float invf[3];     // float32 reciprocals: ortho 1/Lx,1/Ly,1/Lz; triclinic 1/ax,1/by,1/cz
+  float S;           // float32(nbins / r_max)
+  float margin;      // triclinic: 1 - 2 r_max / h_min (no-search precondition margin)
+  double eps_S;      // |S - nbins/r_max| / (nbins/r_max)
+  // ---- written on the device
+  int32_t cmin[3];   // ordered-integer encodings of the per-axis coordinate min / max
+  int32_t cmax[3];
+  int32_t bad;       // a non-finite coordinate was seen
+  int32_t all_defer; // float32 decisions are not safe for this frame: every pair goes exact
+  float delta;       // float32 window half-width in bin units
+  float eps_s;       // search variant: fractional-coordinate ambiguity margin
+  unsigned long long deferred;  // statistics
+  unsigned long long exact;
+};
+
+// One species pair (a,b) of one frame, cut into kTile x kTile work items.
+struct Segment {
+  int32_t frame;
+  int32_t intra;     // a == b: only tiles ti <= tj, pairs j > i
+  int32_t h;         // histogram index within the frame
+  int32_t n_ti, n_tj;
+  int32_t a0, na, b0, nb;  // frame-local particle ranges of species a and b
+  int32_t pad;
+  int64_t item0;     // first global item index
+};
+
+struct Control {
+  unsigned long long next_item;  // dynamic work counter (reset before each pass)
+  int32_t status;                // 0 ok, else an error code
+  int32_t pad;
+};
+
+struct PairLaunch {
+  FrameDev* frames;
+  const Segment* segs;
+  int32_t n_segs;
+  int32_t pass;
+  int64_t n_items;
+  int32_t hist_width;  // shared-memory bins per block
+  int32_t pad;
+  Control* ctl;
+};
+
+// ---- launchers (dh_kernels.cu); all enqueue on `stream` and return the launch error
+cudaError_t launch_stage(const float* src, int64_t n, int stride, float4* dst, FrameDev* frame_dev,
+                         cudaStream_t stream);
+cudaError_t launch_frame_setup(FrameDev* frames, int n_frames, int pass_hi_max, cudaStream_t stream);
+cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* status,
+                              cudaStream_t stream);
+cudaError_t launch_pairs(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream);
+size_t pair_kernel_smem(int hist_width);
+int pair_kernel_max_width();
+int pair_kernel_blocks_per_sm(int hist_width);
+
+// Host/device shared definition of the binary64 bin of Alg. 1 (used to build thresholds).
+int64_t host_bin_of(double r2, double r_max, int32_t nbins);
+int build_thresholds_host(double r_max, int32_t nbins, double* T);
+
+}  // namespace dh

@@ -1,0 +1,681 @@
+// CUDA kernels of the particle-pair distance histogram (sm_103a).
+//
+// Hot path (Reuter & Koefinger, Sec. 2 and 3.2): for every unique pair the
+// distance vector, the minimum image of Eq. 5, the Euclidean distance and the
+// bin kappa = (int) nbins r / r_max of Alg. 1 are computed, and the bin of a
+// block-private shared-memory histogram is incremented (the hybrid strategy of
+// Sec. 2.4: groups of threads share a private histogram, merged into the
+// global one at the end, Sec. 3.2.3).  Private counts are uint32 and are
+// flushed into the uint64 global histogram before they can overflow
+// (Sec. 3.1, also applied on the GPU).
+//
+// Precision design (not in the paper, which computes in float32 only): the
+// result must equal the binary64 definition bin for bin.  Each pair is first
+// evaluated in float32 with an error bound delta (in bin units) derived for the
+// exact operation sequence below; a pair whose float32 bin coordinate t lies
+// farther than delta from every integer is decided in float32.  The others are
+// pushed into a per-warp queue and re-decided by replaying the binary64
+// definition (same operations, same order, explicit round-to-nearest
+// intrinsics, no contraction) and comparing r^2 with a table of binary64
+// thresholds T[k] = smallest r^2 whose bin is >= k.
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "dh_internal.h"
+
+namespace dh {
+
+// ------------------------------------------------------------------ helpers
+
+// Order-preserving map float -> int32 (for atomicMin/atomicMax on floats).
+__device__ __forceinline__ int32_t ord_of(float f) {
+  int32_t i = __float_as_int(f);
+  return i >= 0 ? i : (i ^ 0x7FFFFFFF);
+}
+__device__ __forceinline__ float float_of_ord(int32_t k) {
+  return __int_as_float(k >= 0 ? k : (k ^ 0x7FFFFFFF));
+}
+
+constexpr float kMagicRound = 12582912.0f;  // 1.5 * 2^23: fma(x, s, M) - M = nint_even(x*s), |x*s| < 2^22
+constexpr float kMagicFloor = 8388608.0f;   // 2^23: fadd.rd(t, 2^23) - 2^23 = floor(t), 0 <= t < 2^23
+constexpr unsigned kFull = 0xffffffffu;
+
+// Relative error bound assumed for sqrt.approx.ftz.f32 (checked exhaustively
+// over two binades by the GPU test suite).
+constexpr double kSqrtRelErr = 8.0 / 16777216.0;  // 8 * 2^-24
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// IEEE minimum that propagates NaN (masked pairs carry NaN and must stay NaN).
+__device__ __forceinline__ float min_nan(float a, float b) {
+  float y;
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+  return y;
+}
+__device__ __forceinline__ float nint_scaled(float x, float s) {
+  return __fadd_rn(__fmaf_rn(x, s, kMagicRound), -kMagicRound);
+}
+__device__ __forceinline__ float nint_f(float x) {
+  return __fadd_rn(__fadd_rn(x, kMagicRound), -kMagicRound);
+}
+
+// ------------------------------------------------------------------ binary64 bin of Alg. 1
+
+// kappa = floor((nbins * sqrt(r2)) / r_max), evaluated left to right in
+// binary64; nbins when the pair is beyond the histogram.
+__host__ __device__ inline int64_t bin_of_b64(double r2, double r_max, int32_t nbins) {
+#ifdef __CUDA_ARCH__
+  double r = __dsqrt_rn(r2);
+  double t = __dmul_rn((double)nbins, r);
+  t = __ddiv_rn(t, r_max);
+#else
+  double r = std::sqrt(r2);
+  double t = (double)nbins * r;
+  t = t / r_max;
+#endif
+  if (!(t < (double)nbins)) return nbins;
+  return (int64_t)floor(t);
+}
+
+// Smallest binary64 q >= 0 with bin(q) >= k (k >= 1), found by stepping ulp by
+// ulp from the rounded edge (k r_max / nbins)^2.  *ok is cleared if the walk
+// does not settle within 4096 steps.
+__host__ __device__ inline double threshold_of(int32_t k, double r_max, int32_t nbins, int* ok) {
+  if (k <= 0) return 0.0;
+  double e = ((double)k * r_max) / (double)nbins;
+  double q = e * e;
+  int it = 0;
+  if (bin_of_b64(q, r_max, nbins) >= k) {
+    for (; it < 4096; ++it) {
+      double p = nextafter(q, 0.0);
+      if (!(p < q) || bin_of_b64(p, r_max, nbins) < k) break;
+      q = p;
+    }
+  } else {
+    for (; it < 4096; ++it) {
+      q = nextafter(q, (double)INFINITY);
+      if (bin_of_b64(q, r_max, nbins) >= k) break;
+    }
+  }
+  if (it >= 4096) *ok = 0;
+  return q;
+}
+
+int64_t host_bin_of(double r2, double r_max, int32_t nbins) { return bin_of_b64(r2, r_max, nbins); }
+
+int build_thresholds_host(double r_max, int32_t nbins, double* T) {
+  int ok = 1;
+  for (int32_t k = 0; k <= nbins; ++k) T[k] = threshold_of(k, r_max, nbins, &ok);
+  return ok;
+}
+
+__global__ void thresholds_kernel(double r_max, int32_t nbins, double* T, int32_t* status) {
+  int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > nbins) return;
+  int ok = 1;
+  T[k] = threshold_of(k, r_max, nbins, &ok);
+  if (!ok) atomicExch(status, 7);
+}
+
+// ------------------------------------------------------------------ A1: staging
+
+// coords (n x stride floats) -> float4, per-axis min/max, finiteness.
+__global__ void stage_kernel(const float* __restrict__ src, int64_t n, int stride,
+                             float4* __restrict__ dst, FrameDev* F) {
+  float mn0 = INFINITY, mn1 = INFINITY, mn2 = INFINITY;
+  float mx0 = -INFINITY, mx1 = -INFINITY, mx2 = -INFINITY;
+  int bad = 0;
+  int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    float x = src[i * stride], y = src[i * stride + 1], z = src[i * stride + 2];
+    bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
+    dst[i] = make_float4(x, y, z, 0.0f);
+    mn0 = fminf(mn0, x); mn1 = fminf(mn1, y); mn2 = fminf(mn2, z);
+    mx0 = fmaxf(mx0, x); mx1 = fmaxf(mx1, y); mx2 = fmaxf(mx2, z);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn0 = fminf(mn0, __shfl_xor_sync(kFull, mn0, o));
+    mn1 = fminf(mn1, __shfl_xor_sync(kFull, mn1, o));
+    mn2 = fminf(mn2, __shfl_xor_sync(kFull, mn2, o));
+    mx0 = fmaxf(mx0, __shfl_xor_sync(kFull, mx0, o));
+    mx1 = fmaxf(mx1, __shfl_xor_sync(kFull, mx1, o));
+    mx2 = fmaxf(mx2, __shfl_xor_sync(kFull, mx2, o));
+    bad |= __shfl_xor_sync(kFull, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mn0 <= mx0) {
+      atomicMin(&F->cmin[0], ord_of(mn0)); atomicMin(&F->cmin[1], ord_of(mn1));
+      atomicMin(&F->cmin[2], ord_of(mn2));
+      atomicMax(&F->cmax[0], ord_of(mx0)); atomicMax(&F->cmax[1], ord_of(mx1));
+      atomicMax(&F->cmax[2], ord_of(mx2));
+    }
+    if (bad) atomicExch(&F->bad, 1);
+  }
+}
+
+// ------------------------------------------------------------------ per-frame error window
+
+// Derives the float32 decision window delta (bin units) for one frame from its
+// box, r_max, nbins and the coordinate ranges found by stage_kernel.  Every
+// float32 operation of the fast path rounds to nearest (relative error <= u =
+// 2^-24), except sqrt.approx (kSqrtRelErr).  Bounds, with S = nbins/r_max and
+// R_c the coordinate range on axis c:
+//   relative part  alpha*t: d or d' rounding (u), r^2 = fma(dz,dz,fma(dy,dy,dx*dx))
+//                  (3u on r^2 -> 1.5u on r), sqrt, float32 S (eps_S), t = r*S (u);
+//   absolute part  beta = S*|a|: a_c collects the rounding of xj - xi (u R_c), of
+//                  every intermediate of the wrap (u |intermediate|) and of the
+//                  float32 box entries (|k| |B32 - B|);
+//   orthorhombic ties: where float32 and binary64 choose different nearest
+//                  images (d/L within ~2u R/L of a half integer) both vectors
+//                  have |d'_c| within 2u R_c of L_c/2; this adds S*4u|R| near t
+//                  = S L_min/2 and is added whenever that point is in range.
+// delta = alpha*(nbins+1) + beta (+ tie term) + 2^-20, times 1.01.  If a
+// precondition of the float32 path fails (wrap range, triclinic margin) or
+// delta >= 0.25, every pair of the frame is decided in binary64.
+__global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_frames) return;
+  FrameDev& F = frames[f];
+  const double u = 1.0 / 16777216.0;
+  double R[3] = {0, 0, 0};
+  if (F.n > 0 && F.cmin[0] <= F.cmax[0]) {
+    for (int c = 0; c < 3; ++c) {
+      double lo = float_of_ord(F.cmin[c]), hi = float_of_ord(F.cmax[c]);
+      R[c] = hi - lo;
+    }
+  }
+  double S = (double)F.nbins / F.r_max;
+  double alpha = 4.5 * u + kSqrtRelErr + F.eps_S;
+  double a[3] = {0, 0, 0};
+  double tie = 0.0;
+  int all_defer = 0;
+  float eps_s = 0.0f;
+  const double* B = F.B;
+  double dB[9];
+  for (int q = 0; q < 9; ++q) dB[q] = fabs((double)F.Bf[q] - B[q]);
+  if (F.variant == V_NONE) {
+    alpha += u;  // xj - xi rounding is relative to |d| when nothing is wrapped
+  } else if (F.variant == V_ORTHO) {
+    double Lmin = INFINITY, Rn2 = 0;
+    for (int c = 0; c < 3; ++c) {
+      double L = B[4 * c];
+      double K = floor(R[c] / L + 0.5) + 1.0;
+      a[c] = u * R[c] + K * dB[4 * c];
+      if (R[c] / L > 1048576.0) all_defer = 1;  // nint via the 2^23 trick needs |d/L| < 2^22
+      Lmin = fmin(Lmin, L);
+      Rn2 += R[c] * R[c];
+    }
+    double t_tie = S * Lmin * 0.5 * (1.0 - 8.0 * u * sqrt(Rn2) / Lmin) - 1.0;
+    if (t_tie <= (double)F.nbins + 1.0) tie = S * 4.0 * u * sqrt(Rn2) * 1.01;
+  } else if (F.variant == V_TRIC) {
+    // sequential wrap along c, then b, then a (Eq. 5 for r below h_min/2)
+    double ax = B[0], bx = B[1], cx = B[2], by = B[4], cy = B[5], cz = B[8];
+    double Kz = floor(R[2] / cz + 0.5) + 1.0;
+    double D1x = R[0] + Kz * fabs(cx), D1y = R[1] + Kz * fabs(cy);
+    double Ky = floor(D1y / by + 0.5) + 1.0;
+    double D2x = D1x + Ky * fabs(bx);
+    double Kx = floor(D2x / ax + 0.5) + 1.0;
+    a[0] = u * (R[0] + D1x + D2x) + Kz * dB[2] + Ky * dB[1] + Kx * dB[0];
+    a[1] = u * (R[1] + D1y) + Kz * dB[5] + Ky * dB[4];
+    a[2] = u * R[2] + Kz * dB[8];
+    // the three nearest-integer decisions must be exact for every pair closer
+    // than r_max: their float32 errors must stay below a quarter of the margin
+    double ez = (2.0 * u * R[2] + R[2] * fabs((double)F.invf[2] * cz - 1.0)) / cz;
+    double ey = (2.0 * (a[1] + u * D1y) + D1y * fabs((double)F.invf[1] * by - 1.0)) / by;
+    double ex = (2.0 * (a[0] + u * D2x) + D2x * fabs((double)F.invf[0] * ax - 1.0)) / ax;
+    double emax = fmax(ex, fmax(ey, ez));
+    if (!(emax < 0.25 * (double)F.margin) || D2x / ax > 1048576.0 || D1y / by > 1048576.0 ||
+        R[2] / cz > 1048576.0)
+      all_defer = 1;
+  } else {  // V_TRIC_SEARCH
+    double ax = B[0], bx = B[1], cx = B[2], by = B[4], cy = B[5], cz = B[8];
+    double Sz = R[2] / cz + 1.0;
+    double Sy = (R[1] + fabs(cy) * Sz) / by + 1.0;
+    double Sx = (R[0] + fabs(bx) * Sy + fabs(cx) * Sz) / ax + 1.0;
+    double ez = 3.0 * u * (R[2] / cz + Sz);
+    double ey = (3.0 * u * (R[1] + fabs(cy) * Sz) + fabs(cy) * ez) / by + 2.0 * u * Sy;
+    double ex = (3.0 * u * (R[0] + fabs(bx) * Sy + fabs(cx) * Sz) + fabs(bx) * ey + fabs(cx) * ez) / ax +
+                2.0 * u * Sx;
+    eps_s = (float)(2.0 * fmax(ex, fmax(ey, ez)) + 1e-12);
+    double Kx = floor(Sx + 0.5) + 1.0, Ky = floor(Sy + 0.5) + 1.0, Kz = floor(Sz + 0.5) + 1.0;
+    double Ix = R[0] + Kx * ax + Ky * fabs(bx) + Kz * fabs(cx) + ax + fabs(bx) + fabs(cx);
+    double Iy = R[1] + Ky * by + Kz * fabs(cy) + by + fabs(cy);
+    double Iz = R[2] + Kz * cz + cz;
+    a[0] = u * (R[0] + 7.0 * Ix) + (Kx + 1) * dB[0] + (Ky + 1) * dB[1] + (Kz + 1) * dB[2];
+    a[1] = u * (R[1] + 6.0 * Iy) + (Ky + 1) * dB[4] + (Kz + 1) * dB[5];
+    a[2] = u * (R[2] + 3.0 * Iz) + (Kz + 1) * dB[8];
+    if (Sx > 1048576.0 || Sy > 1048576.0 || Sz > 1048576.0 || eps_s > 0.05f) all_defer = 1;
+  }
+  double beta = S * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * (1.0 + 64.0 * u);
+  double delta = (alpha * ((double)F.nbins + 1.0) + beta + tie + 1.0 / 1048576.0) * 1.01;
+  if (!(delta < 0.25)) all_defer = 1;
+  F.delta = (float)fmin(delta, 0.25);
+  F.eps_s = eps_s;
+  F.all_defer = all_defer;
+}
+
+// ------------------------------------------------------------------ binary64 replay
+
+// Squared minimum-image distance in binary64, the same operations in the same
+// order as the definition (Alg. 1, Eq. 5, 27 neighbouring shifts).
+template <int V>
+__device__ double exact_r2(const FrameDev& F, float4 pi, float4 pj) {
+  double dx = __dsub_rn((double)pj.x, (double)pi.x);
+  double dy = __dsub_rn((double)pj.y, (double)pi.y);
+  double dz = __dsub_rn((double)pj.z, (double)pi.z);
+  const double* B = F.B;
+  if (V == V_ORTHO) {
+    double kx = rint(__dmul_rn(dx, F.Linv[0]));
+    double ky = rint(__dmul_rn(dy, F.Linv[1]));
+    double kz = rint(__dmul_rn(dz, F.Linv[2]));
+    dx = __fma_rn(-kx, B[0], dx);
+    dy = __fma_rn(-ky, B[4], dy);
+    dz = __fma_rn(-kz, B[8], dz);
+  } else if (V == V_TRIC || V == V_TRIC_SEARCH) {
+    const double ax = B[0], bx = B[1], cx = B[2], by = B[4], cy = B[5], cz = B[8];
+    double sz = __ddiv_rn(dz, cz);
+    double sy = __ddiv_rn(__dsub_rn(dy, __dmul_rn(cy, sz)), by);
+    double sx = __ddiv_rn(__dsub_rn(__dsub_rn(dx, __dmul_rn(bx, sy)), __dmul_rn(cx, sz)), ax);
+    double kx = rint(sx), ky = rint(sy), kz = rint(sz);
+    dx = __dsub_rn(__dsub_rn(__dsub_rn(dx, __dmul_rn(ax, kx)), __dmul_rn(bx, ky)), __dmul_rn(cx, kz));
+    dy = __dsub_rn(__dsub_rn(dy, __dmul_rn(by, ky)), __dmul_rn(cy, kz));
+    dz = __dsub_rn(dz, __dmul_rn(cz, kz));
+    double best = INFINITY;
+#pragma unroll 1
+    for (int mx = -1; mx <= 1; ++mx)
+#pragma unroll 1
+      for (int my = -1; my <= 1; ++my)
+#pragma unroll 1
+        for (int mz = -1; mz <= 1; ++mz) {
+          double ex = __dadd_rn(__dadd_rn(__dadd_rn(dx, __dmul_rn(ax, (double)mx)), __dmul_rn(bx, (double)my)),
+                                __dmul_rn(cx, (double)mz));
+          double ey = __dadd_rn(__dadd_rn(dy, __dmul_rn(by, (double)my)), __dmul_rn(cy, (double)mz));
+          double ez = __dadd_rn(dz, __dmul_rn(cz, (double)mz));
+          double r2 = __fma_rn(ez, ez, __fma_rn(ey, ey, __dmul_rn(ex, ex)));
+          if (r2 < best) best = r2;
+        }
+    return best;
+  }
+  return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+}
+
+// Bin of a binary64 r^2 from the threshold table: the largest k with T[k] <= r2.
+__device__ __forceinline__ int bin_from_thresholds(const double* __restrict__ T, int nbins, double r2) {
+  int lo = 0, hi = nbins;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(T + mid) <= r2) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------ A2-A8: pair kernel
+
+struct FastParams {
+  float S;
+  float thr;      // 0.5 - delta, or -1 when every pair is decided exactly
+  float tclamp;   // hi + 0.5
+  int32_t kbase;  // bits(2^23) + lo
+  uint32_t width; // hi - lo
+  int32_t lo;
+  float b[9];
+  float inv[3];
+  float amb_thr;  // search variant: 0.5 - eps_s
+};
+
+struct ItemDesc {
+  int32_t valid;   // 0: no more work
+  int32_t frame;
+  int32_t h;
+  int32_t seg_intra;
+  int32_t i0, ni, j0, nj;
+  int32_t masked;
+  int32_t skip;    // frame has no bins in this pass
+};
+
+// float32 bin coordinate t = S * |d'| of one pair (NaN in, NaN out).
+template <int V>
+__device__ __forceinline__ float pair_t(float dx, float dy, float dz, const FastParams& P, bool& amb) {
+  if (V == V_ORTHO) {
+    dx = __fmaf_rn(-nint_scaled(dx, P.inv[0]), P.b[0], dx);
+    dy = __fmaf_rn(-nint_scaled(dy, P.inv[1]), P.b[4], dy);
+    dz = __fmaf_rn(-nint_scaled(dz, P.inv[2]), P.b[8], dz);
+  } else if (V == V_TRIC) {
+    float kz = nint_scaled(dz, P.inv[2]);
+    dx = __fmaf_rn(-kz, P.b[2], dx);
+    dy = __fmaf_rn(-kz, P.b[5], dy);
+    dz = __fmaf_rn(-kz, P.b[8], dz);
+    float ky = nint_scaled(dy, P.inv[1]);
+    dx = __fmaf_rn(-ky, P.b[1], dx);
+    dy = __fmaf_rn(-ky, P.b[4], dy);
+    float kx = nint_scaled(dx, P.inv[0]);
+    dx = __fmaf_rn(-kx, P.b[0], dx);
+  } else if (V == V_TRIC_SEARCH) {
+    float sz = __fmul_rn(dz, P.inv[2]);
+    float sy = __fmul_rn(__fmaf_rn(-P.b[5], sz, dy), P.inv[1]);
+    float sx = __fmul_rn(__fmaf_rn(-P.b[2], sz, __fmaf_rn(-P.b[1], sy, dx)), P.inv[0]);
+    float kx = nint_f(sx), ky = nint_f(sy), kz = nint_f(sz);
+    amb = (fabsf(__fsub_rn(sx, kx)) > P.amb_thr) || (fabsf(__fsub_rn(sy, ky)) > P.amb_thr) ||
+          (fabsf(__fsub_rn(sz, kz)) > P.amb_thr);
+    dx = __fmaf_rn(-kz, P.b[2], __fmaf_rn(-ky, P.b[1], __fmaf_rn(-kx, P.b[0], dx)));
+    dy = __fmaf_rn(-kz, P.b[5], __fmaf_rn(-ky, P.b[4], dy));
+    dz = __fmaf_rn(-kz, P.b[8], dz);
+    float best = INFINITY;
+#pragma unroll
+    for (int mx = -1; mx <= 1; ++mx) {
+      float ex1 = __fmaf_rn((float)mx, P.b[0], dx);
+#pragma unroll
+      for (int my = -1; my <= 1; ++my) {
+        float ex2 = __fmaf_rn((float)my, P.b[1], ex1);
+        float ey2 = __fmaf_rn((float)my, P.b[4], dy);
+#pragma unroll
+        for (int mz = -1; mz <= 1; ++mz) {
+          float ex = __fmaf_rn((float)mz, P.b[2], ex2);
+          float ey = __fmaf_rn((float)mz, P.b[5], ey2);
+          float ez = __fmaf_rn((float)mz, P.b[8], dz);
+          best = min_nan(best, __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex))));
+        }
+      }
+    }
+    return __fmul_rn(sqrt_approx(best), P.S);
+  }
+  float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+  return __fmul_rn(sqrt_approx(r2), P.S);
+}
+
+// Re-decide up to `count` queued pairs (one per lane) in binary64.
+template <int V>
+__device__ void drain_queue(const FrameDev& F, const FastParams& P, const uint2* q, int count,
+                            uint32_t* sh, int lane) {
+  if (lane < count) {
+    uint2 e = q[lane];
+    float4 pi = __ldg(F.X + e.x);
+    float4 pj = __ldg(F.X + e.y);
+    double r2 = exact_r2<V>(F, pi, pj);
+    int k = bin_from_thresholds(F.T, F.nbins, r2);
+    uint32_t rel = (uint32_t)(k - P.lo);
+    if (rel < P.width) atomicAdd(sh + rel, 1u);
+  }
+}
+
+// Append this thread's deferred pairs (bits of dmask: register slot r pairs
+// particle ibase + r*kBlock with particle jg) to the warp queue; whenever 32 are
+// queued they are decided at once by the whole warp.
+template <int V>
+__device__ __noinline__ void defer_pairs(uint32_t dmask, int ibase, int jg, uint2* q, int& qcount,
+                                         const FrameDev& F, const FastParams& P, uint32_t* sh,
+                                         int lane, unsigned& ndeferred) {
+  for (;;) {
+    bool has = dmask != 0u;
+    unsigned bal = __ballot_sync(kFull, has);
+    if (bal == 0u) break;
+    if (has) {
+      int r = __ffs(dmask) - 1;
+      dmask &= dmask - 1u;
+      int pos = qcount + __popc(bal & ((1u << lane) - 1u));
+      q[pos] = make_uint2((unsigned)(ibase + r * kBlock), (unsigned)jg);
+    }
+    qcount += __popc(bal);
+    ndeferred += __popc(bal);
+    __syncwarp();
+    if (qcount >= 32) {
+      drain_queue<V>(F, P, q, 32, sh, lane);
+      __syncwarp();
+      int rest = qcount - 32;
+      if (lane < rest) q[lane] = q[32 + lane];
+      __syncwarp();
+      qcount = rest;
+    }
+  }
+}
+
+template <int V, bool MASKED>
+__device__ __forceinline__ void run_tile(const FrameDev& F, const FastParams& P, const ItemDesc& it,
+                                         const float4* __restrict__ sj, uint32_t* sh, uint2* q,
+                                         int tid, int lane, unsigned& ndeferred) {
+  float xi[kRegI], yi[kRegI], zi[kRegI];
+  const int ibase = it.i0 + tid;
+#pragma unroll
+  for (int r = 0; r < kRegI; ++r) {
+    int li = tid + r * kBlock;
+    if (li < it.ni) {
+      float4 p = __ldg(F.X + ibase + r * kBlock);
+      xi[r] = p.x; yi[r] = p.y; zi[r] = p.z;
+    } else {
+      xi[r] = __int_as_float(0x7fffffff); yi[r] = xi[r]; zi[r] = xi[r];
+    }
+  }
+  int qcount = 0;
+  const float qnan = __int_as_float(0x7fffffff);
+  for (int jj = 0; jj < it.nj; ++jj) {
+    const float4 pj = sj[jj];
+    const int jg = it.j0 + jj;
+    uint32_t dmask = 0u;
+#pragma unroll
+    for (int r = 0; r < kRegI; ++r) {
+      float dx = __fsub_rn(pj.x, xi[r]);
+      float dy = __fsub_rn(pj.y, yi[r]);
+      float dz = __fsub_rn(pj.z, zi[r]);
+      if (MASKED) {
+        // intra-species: only j > i; all three components so no later test sees a number
+        if (!(jg > ibase + r * kBlock)) { dx = qnan; dy = qnan; dz = qnan; }
+      }
+      bool amb = false;
+      float t = pair_t<V>(dx, dy, dz, P, amb);
+      t = min_nan(t, P.tclamp);
+      float fl = __fadd_rd(t, kMagicFloor);
+      float fr = __fsub_rn(t, __fsub_rn(fl, kMagicFloor));
+      bool nearedge = fabsf(__fsub_rn(fr, 0.5f)) > P.thr;
+      if (V == V_TRIC_SEARCH) nearedge = nearedge || amb;
+      uint32_t rel = (uint32_t)(__float_as_int(fl) - P.kbase);
+      if (!nearedge && rel < P.width) atomicAdd(sh + rel, 1u);
+      if (nearedge) dmask |= (1u << r);
+    }
+    if (__any_sync(kFull, dmask != 0u)) {
+      defer_pairs<V>(dmask, ibase, jg, q, qcount, F, P, sh, lane, ndeferred);
+    }
+  }
+  // decide what is left in the queue
+  drain_queue<V>(F, P, q, qcount, sh, lane);
+  __syncwarp();
+}
+
+template <int V>
+__device__ void run_item(const FrameDev& F, const FastParams& P, const ItemDesc& it,
+                         const float4* sj, uint32_t* sh, uint2* q, int tid, int lane,
+                         unsigned& ndeferred) {
+  if (it.masked) run_tile<V, true>(F, P, it, sj, sh, q, tid, lane, ndeferred);
+  else run_tile<V, false>(F, P, it, sj, sh, q, tid, lane, ndeferred);
+}
+
+__device__ void flush_hist(uint32_t* sh, int width, uint64_t* dst, int tid) {
+  for (int k = tid; k < width; k += kBlock) {
+    uint32_t v = sh[k];
+    if (v) {
+      atomicAdd((unsigned long long*)(dst + k), (unsigned long long)v);
+      sh[k] = 0u;
+    }
+  }
+}
+
+// Work item -> tile pair.  Items of a segment are numbered row by row over
+// (ti, tj); intra-species segments keep only tj >= ti (upper triangle).
+__device__ void decode_item(const PairLaunch& L, long long item, ItemDesc& it) {
+  int lo = 0, hi = L.n_segs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (L.segs[mid].item0 <= item) lo = mid; else hi = mid - 1;
+  }
+  const Segment& s = L.segs[lo];
+  long long lid = item - s.item0;
+  int ti, tj;
+  if (s.intra) {
+    // row ti starts at ti*n - ti*(ti-1)/2
+    long long n = s.n_ti;
+    int a = 0, b = (int)n - 1;
+    while (a < b) {
+      int m = (a + b + 1) >> 1;
+      long long start = (long long)m * n - (long long)m * (m - 1) / 2;
+      if (start <= lid) a = m; else b = m - 1;
+    }
+    ti = a;
+    long long start = (long long)ti * n - (long long)ti * (ti - 1) / 2;
+    tj = ti + (int)(lid - start);
+  } else {
+    ti = (int)(lid / s.n_tj);
+    tj = (int)(lid - (long long)ti * s.n_tj);
+  }
+  it.valid = 1;
+  it.frame = s.frame;
+  it.h = s.h;
+  it.seg_intra = s.intra;
+  it.i0 = s.a0 + ti * kTile;
+  it.ni = min(kTile, s.na - ti * kTile);
+  it.j0 = s.b0 + tj * kTile;
+  it.nj = min(kTile, s.nb - tj * kTile);
+  it.masked = (s.intra && ti == tj) ? 1 : 0;
+  const FrameDev& F = L.frames[s.frame];
+  int lo_bin = L.pass * F.sweep_width;
+  it.skip = (lo_bin >= F.nbins) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kBlock) pair_kernel(PairLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int width_pad = (L.hist_width + 3) & ~3;
+  uint32_t* sh = reinterpret_cast<uint32_t*>(smem_raw);
+  float4* sj = reinterpret_cast<float4*>(sh + width_pad);
+  uint2* sq = reinterpret_cast<uint2*>(sj + kTile);
+  __shared__ ItemDesc s_it;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint2* q = sq + warp * kQueueCap;
+  for (int k = tid; k < width_pad; k += kBlock) sh[k] = 0u;
+
+  int cur_frame = -1, cur_h = -1;
+  unsigned long long since = 0;  // pairs accumulated in sh since the last flush
+  FastParams P;
+  uint64_t* cur_dst = nullptr;
+  int cur_width = 0;
+
+  for (;;) {
+    if (tid == 0) {
+      unsigned long long item = atomicAdd(&L.ctl->next_item, 1ull);
+      if ((long long)item >= L.n_items) s_it.valid = 0;
+      else decode_item(L, (long long)item, s_it);
+    }
+    __syncthreads();
+    const ItemDesc it = s_it;
+    if (!it.valid) break;
+    if (!it.skip) {
+      const FrameDev& F = L.frames[it.frame];
+      const unsigned long long pairs = (unsigned long long)it.ni * (unsigned long long)it.nj;
+      if (it.frame != cur_frame || it.h != cur_h || since + pairs > 0xFFFFFFFFull) {
+        if (cur_frame >= 0) {
+          __syncthreads();
+          flush_hist(sh, cur_width, cur_dst, tid);
+          __syncthreads();
+        }
+        if (it.frame != cur_frame) {
+          int lo_bin = L.pass * F.sweep_width;
+          int hi_bin = min(F.nbins, lo_bin + F.sweep_width);
+          P.S = F.S;
+          P.thr = F.all_defer ? -1.0f : 0.5f - F.delta;
+          P.tclamp = (float)hi_bin + 0.5f;
+          P.kbase = __float_as_int(kMagicFloor) + lo_bin;
+          P.width = (uint32_t)(hi_bin - lo_bin);
+          P.lo = lo_bin;
+#pragma unroll
+          for (int c = 0; c < 9; ++c) P.b[c] = F.Bf[c];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) P.inv[c] = F.invf[c];
+          P.amb_thr = 0.5f - F.eps_s;
+        }
+        cur_frame = it.frame;
+        cur_h = it.h;
+        cur_width = (int)P.width;
+        cur_dst = F.out + (size_t)it.h * F.nbins + P.lo;
+        since = 0;
+      }
+      since += pairs;
+      // stage the j tile (A1 layout: float4 per particle)
+      for (int k = tid; k < it.nj; k += kBlock) sj[k] = __ldg(F.X + it.j0 + k);
+      __syncthreads();
+      unsigned ndef = 0;
+      switch (F.variant) {
+        case V_NONE: run_item<V_NONE>(F, P, it, sj, sh, q, tid, lane, ndef); break;
+        case V_ORTHO: run_item<V_ORTHO>(F, P, it, sj, sh, q, tid, lane, ndef); break;
+        case V_TRIC: run_item<V_TRIC>(F, P, it, sj, sh, q, tid, lane, ndef); break;
+        default: run_item<V_TRIC_SEARCH>(F, P, it, sj, sh, q, tid, lane, ndef); break;
+      }
+      if (lane == 0 && ndef) atomicAdd(&L.frames[it.frame].deferred, (unsigned long long)ndef);
+    }
+    __syncthreads();
+  }
+  if (cur_frame >= 0) {
+    __syncthreads();
+    flush_hist(sh, cur_width, cur_dst, tid);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+size_t pair_kernel_smem(int hist_width) {
+  size_t w = (size_t)((hist_width + 3) & ~3);
+  return w * 4 + (size_t)kTile * 16 + (size_t)kWarps * kQueueCap * 8;
+}
+
+int pair_kernel_max_width() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  size_t fixed = pair_kernel_smem(0) + sizeof(ItemDesc) + 64;
+  if ((size_t)optin <= fixed) return 0;
+  return (int)(((size_t)optin - fixed) / 4) & ~3;
+}
+
+int pair_kernel_blocks_per_sm(int hist_width) {
+  size_t smem = pair_kernel_smem(hist_width);
+  cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel, kBlock, smem);
+  return nb;
+}
+
+cudaError_t launch_stage(const float* src, int64_t n, int stride, float4* dst, FrameDev* frame_dev,
+                         cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  stage_kernel<<<(unsigned)blocks, 256, 0, stream>>>(src, n, stride, dst, frame_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frame_setup(FrameDev* frames, int n_frames, int, cudaStream_t stream) {
+  if (n_frames <= 0) return cudaSuccess;
+  frame_setup_kernel<<<(n_frames + 63) / 64, 64, 0, stream>>>(frames, n_frames);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* status,
+                              cudaStream_t stream) {
+  int threads = 128;
+  int blocks = (nbins + 1 + threads - 1) / threads;
+  thresholds_kernel<<<blocks, threads, 0, stream>>>(r_max, nbins, T, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  pair_kernel<<<grid, kBlock, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace dh

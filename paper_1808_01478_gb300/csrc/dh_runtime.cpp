@@ -1,0 +1,624 @@
+// Host runtime of libdh: argument checks, work planning, device workspace,
+// threshold-table cache and the launch sequence behind the C ABI of dh.h.
+//
+// Transfer scheme (Reuter & Koefinger, Sec. 3.2): the coordinates of all
+// species of a frame are one contiguous array copied to the device in one
+// operation, all histograms of the frame come back in one copy, and device
+// memory is allocated on first use and reused by later calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/dh.h"
+#include "dh_internal.h"
+
+using namespace dh;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dh_status fail(dh_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? DH_ERR_NOMEM : DH_ERR_CUDA, "%s: %s", \
+                  #expr, cudaGetErrorString(e_));                                        \
+  } while (0)
+
+// Device buffer that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max(bytes, cap + cap / 2);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+struct HostBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max(bytes, cap + cap / 2);
+    cudaError_t e = cudaMallocHost(&p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+struct ThresholdKey {
+  uint64_t rbits;
+  int32_t nbins;
+  bool operator==(const ThresholdKey& o) const { return rbits == o.rbits && nbins == o.nbins; }
+  bool operator<(const ThresholdKey& o) const {
+    return rbits != o.rbits ? rbits < o.rbits : nbins < o.nbins;
+  }
+};
+
+// Frame checked and planned on the host.
+struct PlannedFrame {
+  const dh_frame* src;
+  int32_t variant;
+  int32_t n_hist;
+  int32_t sweeps;
+  int32_t sweep_width;
+  double margin;
+  uint64_t pairs;
+};
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+// Smallest distance between opposite faces of the cell spanned by the columns of B.
+double min_plane_spacing(const double* B) {
+  double a[3] = {B[0], B[3], B[6]}, b[3] = {B[1], B[4], B[7]}, c[3] = {B[2], B[5], B[8]};
+  auto cross = [](const double* u, const double* v, double* w) {
+    w[0] = u[1] * v[2] - u[2] * v[1];
+    w[1] = u[2] * v[0] - u[0] * v[2];
+    w[2] = u[0] * v[1] - u[1] * v[0];
+  };
+  auto norm = [](const double* w) { return std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]); };
+  double bc[3], ca[3], ab[3];
+  cross(b, c, bc);
+  cross(c, a, ca);
+  cross(a, b, ab);
+  double vol = std::fabs(a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2]);
+  return std::min(vol / norm(bc), std::min(vol / norm(ca), vol / norm(ab)));
+}
+
+}  // namespace
+
+struct dh_ctx {
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t user_stream = nullptr;
+  bool has_user_stream = false;
+  std::recursive_mutex mu;
+  int num_sms = 0;
+  int max_width = 0;
+  dh_config cfg{};
+
+  DevBuf raw;      // caller coordinates copied from the host (n x stride floats)
+  DevBuf X;        // packed float4 coordinates
+  DevBuf hist;     // uint64 histograms (host-pointer outputs, or scratch)
+  DevBuf meta;     // FrameDev array + Segment array
+  DevBuf ctl;      // Control
+  HostBuf hmeta;   // pinned staging for meta
+  HostBuf hout;    // pinned staging for accumulate-on-host
+  DevBuf tstat;    // threshold build status
+
+  std::map<ThresholdKey, double*> tcache;
+  std::list<ThresholdKey> tlru;
+
+  dh_stats stats{};
+  cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;  // pair-kernel timing (DH_CFG_TIMING)
+  bool timed = false;
+  bool pending_async = false;
+  std::vector<PlannedFrame> async_plan;
+
+  cudaStream_t stream() const { return has_user_stream ? user_stream : own_stream; }
+};
+
+namespace {
+
+dh_status check_frame(const dh_frame* f, PlannedFrame& pf, int max_width) {
+  if (!f) return fail(DH_ERR_INVALID, "frame is NULL");
+  if (f->n < 0 || f->n > (int64_t)0x7FFFFFFF - 2 * kTile)
+    return fail(DH_ERR_INVALID, "n = %lld out of range", (long long)f->n);
+  if (f->n_species < 1) return fail(DH_ERR_INVALID, "n_species must be >= 1");
+  if (!f->species_offsets) return fail(DH_ERR_INVALID, "species_offsets is NULL");
+  const int64_t* o = f->species_offsets;
+  if (o[0] != 0 || o[f->n_species] != f->n)
+    return fail(DH_ERR_INVALID, "species offsets must start at 0 and end at n");
+  for (int s = 0; s < f->n_species; ++s)
+    if (o[s + 1] < o[s]) return fail(DH_ERR_INVALID, "species offsets must be nondecreasing");
+  if (f->nbins < 1 || f->nbins > DH_MAX_BINS)
+    return fail(DH_ERR_INVALID, "nbins = %d out of range [1, %d]", f->nbins, DH_MAX_BINS);
+  if (!(f->r_max > 0.0) || !is_finite(f->r_max)) return fail(DH_ERR_INVALID, "r_max must be > 0 and finite");
+  if (f->n > 0 && !f->coords) return fail(DH_ERR_INVALID, "coords is NULL");
+  if (!f->out) return fail(DH_ERR_INVALID, "out is NULL");
+  const double* B = f->box;
+  pf.margin = 1.0;
+  switch (f->box_type) {
+    case DH_BOX_NONE:
+      pf.variant = V_NONE;
+      break;
+    case DH_BOX_ORTHO:
+      for (int q = 0; q < 9; ++q) {
+        bool diag = (q == 0 || q == 4 || q == 8);
+        if (!is_finite(B[q])) return fail(DH_ERR_INVALID, "box entry %d is not finite", q);
+        if (diag && !(B[q] > 0.0)) return fail(DH_ERR_INVALID, "orthorhombic box lengths must be > 0");
+        if (!diag && B[q] != 0.0) return fail(DH_ERR_INVALID, "orthorhombic box must be diagonal");
+      }
+      pf.variant = V_ORTHO;
+      break;
+    case DH_BOX_TRICLINIC: {
+      for (int q = 0; q < 9; ++q)
+        if (!is_finite(B[q])) return fail(DH_ERR_INVALID, "box entry %d is not finite", q);
+      if (B[3] != 0.0 || B[6] != 0.0 || B[7] != 0.0)
+        return fail(DH_ERR_INVALID, "triclinic box must be upper triangular (a along x, b in the xy plane)");
+      if (!(B[0] > 0.0 && B[4] > 0.0 && B[8] > 0.0))
+        return fail(DH_ERR_INVALID, "triclinic box diagonal must be > 0");
+      if (std::fabs(B[1]) > 0.5 * B[0] || std::fabs(B[2]) > 0.5 * B[0] || std::fabs(B[5]) > 0.5 * B[4])
+        return fail(DH_ERR_INVALID, "triclinic box must be reduced: |bx|,|cx| <= ax/2, |cy| <= by/2");
+      double hmin = min_plane_spacing(B);
+      double margin = 1.0 - 2.0 * f->r_max / hmin;
+      pf.margin = margin;
+      pf.variant = (margin >= 1.0 / 256.0) ? V_TRIC : V_TRIC_SEARCH;
+      break;
+    }
+    default:
+      return fail(DH_ERR_INVALID, "unknown box_type %d", f->box_type);
+  }
+  int64_t S = f->n_species;
+  pf.src = f;
+  pf.n_hist = (int32_t)(S * (S + 1) / 2);
+  pf.sweeps = (f->nbins + max_width - 1) / max_width;
+  pf.sweep_width = (f->nbins + pf.sweeps - 1) / pf.sweeps;
+  uint64_t pairs = 0;
+  for (int a = 0; a < S; ++a) {
+    uint64_t na = (uint64_t)(o[a + 1] - o[a]);
+    pairs += na * (na ? na - 1 : 0) / 2;
+    for (int b = a + 1; b < S; ++b) pairs += na * (uint64_t)(o[b + 1] - o[b]);
+  }
+  pf.pairs = pairs;
+  return DH_OK;
+}
+
+void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64_t* out, const double* T) {
+  const dh_frame* f = pf.src;
+  std::memset(&F, 0, sizeof F);
+  F.X = X;
+  F.out = out;
+  F.T = T;
+  F.variant = pf.variant;
+  F.nbins = f->nbins;
+  F.n = (int32_t)f->n;
+  F.sweep_width = pf.sweep_width;
+  F.r_max = f->r_max;
+  for (int q = 0; q < 9; ++q) {
+    F.B[q] = (f->box_type == DH_BOX_NONE) ? 0.0 : f->box[q];
+    F.Bf[q] = (float)F.B[q];
+  }
+  if (pf.variant == V_ORTHO) {
+    F.Linv[0] = 1.0 / F.B[0];
+    F.Linv[1] = 1.0 / F.B[4];
+    F.Linv[2] = 1.0 / F.B[8];
+    F.invf[0] = (float)F.Linv[0];
+    F.invf[1] = (float)F.Linv[1];
+    F.invf[2] = (float)F.Linv[2];
+  } else if (pf.variant == V_TRIC || pf.variant == V_TRIC_SEARCH) {
+    F.invf[0] = (float)(1.0 / F.B[0]);
+    F.invf[1] = (float)(1.0 / F.B[4]);
+    F.invf[2] = (float)(1.0 / F.B[8]);
+  }
+  double S = (double)f->nbins / f->r_max;
+  F.S = (float)S;
+  F.eps_S = std::fabs((double)F.S - S) / S;
+  F.margin = (float)pf.margin;
+  for (int c = 0; c < 3; ++c) {
+    F.cmin[c] = 0x7FFFFFFF;                // ordered encoding of +huge: min starts high
+    F.cmax[c] = (int32_t)0x80000000;       // and max starts low
+  }
+}
+
+// Tiles of one frame's species pairs, appended to segs; returns the item count.
+int64_t add_segments(const PlannedFrame& pf, int32_t frame_idx, int64_t item0, std::vector<Segment>& segs) {
+  const dh_frame* f = pf.src;
+  const int64_t* o = f->species_offsets;
+  int S = f->n_species;
+  int64_t items = 0;
+  int h = 0;
+  for (int a = 0; a < S; ++a)
+    for (int b = a; b < S; ++b, ++h) {
+      int32_t na = (int32_t)(o[a + 1] - o[a]), nb = (int32_t)(o[b + 1] - o[b]);
+      bool intra = (a == b);
+      if (na == 0 || nb == 0 || (intra && na < 2)) continue;
+      Segment s;
+      std::memset(&s, 0, sizeof s);
+      s.frame = frame_idx;
+      s.intra = intra ? 1 : 0;
+      s.h = h;
+      s.a0 = (int32_t)o[a];
+      s.na = na;
+      s.b0 = (int32_t)o[b];
+      s.nb = nb;
+      s.n_ti = (na + kTile - 1) / kTile;
+      s.n_tj = (nb + kTile - 1) / kTile;
+      s.item0 = item0 + items;
+      int64_t n_items = intra ? (int64_t)s.n_ti * (s.n_ti + 1) / 2 : (int64_t)s.n_ti * s.n_tj;
+      items += n_items;
+      segs.push_back(s);
+    }
+  return items;
+}
+
+dh_status get_thresholds(dh_ctx* c, double r_max, int32_t nbins, double** out, int* launched) {
+  uint64_t rb;
+  std::memcpy(&rb, &r_max, 8);
+  ThresholdKey key{rb, nbins};
+  auto it = c->tcache.find(key);
+  if (it != c->tcache.end()) {
+    c->tlru.remove(key);
+    c->tlru.push_front(key);
+    *out = it->second;
+    return DH_OK;
+  }
+  if (c->tcache.size() >= 64) {
+    ThresholdKey old = c->tlru.back();
+    c->tlru.pop_back();
+    // the table may still be read by queued work: free after the stream drains
+    cudaStreamSynchronize(c->stream());
+    cudaFree(c->tcache[old]);
+    c->tcache.erase(old);
+  }
+  double* T = nullptr;
+  CUDA_TRY(cudaMalloc(&T, sizeof(double) * (size_t)(nbins + 1)));
+  CUDA_TRY(launch_thresholds(r_max, nbins, T, (int32_t*)c->tstat.p, c->stream()));
+  ++*launched;
+  c->tcache[key] = T;
+  c->tlru.push_front(key);
+  *out = T;
+  return DH_OK;
+}
+
+// Enqueue everything for k planned frames.  dev_out[f] is where frame f's
+// histograms are accumulated on the device (already zeroed or holding the
+// values to accumulate onto).
+dh_status enqueue_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const std::vector<uint64_t*>& dev_out,
+                         bool host_coords) {
+  cudaStream_t st = c->stream();
+  int k = (int)pfs.size();
+  int launched = 0;
+  // coordinates
+  std::vector<int64_t> xoff(k + 1, 0);
+  size_t raw_floats = 0;
+  for (int f = 0; f < k; ++f) {
+    xoff[f + 1] = xoff[f] + pfs[f].src->n;
+    if (host_coords) raw_floats += (size_t)pfs[f].src->n * ((pfs[f].src->flags & DH_COORDS_F4) ? 4 : 3);
+  }
+  CUDA_TRY(c->X.ensure(sizeof(float4) * (size_t)std::max<int64_t>(xoff[k], 1)));
+  if (host_coords) CUDA_TRY(c->raw.ensure(sizeof(float) * std::max<size_t>(raw_floats, 1)));
+  // metadata: FrameDev[k] + Segment[...]
+  std::vector<Segment> segs;
+  int64_t n_items = 0;
+  for (int f = 0; f < k; ++f) n_items += add_segments(pfs[f], f, n_items, segs);
+  size_t meta_bytes = sizeof(FrameDev) * (size_t)k + sizeof(Segment) * std::max<size_t>(segs.size(), 1);
+  CUDA_TRY(c->meta.ensure(meta_bytes));
+  CUDA_TRY(c->hmeta.ensure(meta_bytes));
+  FrameDev* hF = (FrameDev*)c->hmeta.p;
+  Segment* hS = (Segment*)(hF + k);
+  FrameDev* dF = (FrameDev*)c->meta.p;
+  Segment* dS = (Segment*)(dF + k);
+  int max_pass = 1, hist_width = 1;
+  for (int f = 0; f < k; ++f) {
+    double* T = nullptr;
+    dh_status s = get_thresholds(c, pfs[f].src->r_max, pfs[f].src->nbins, &T, &launched);
+    if (s != DH_OK) return s;
+    fill_frame_dev(pfs[f], hF[f], (const float4*)c->X.p + xoff[f], dev_out[f], T);
+    max_pass = std::max(max_pass, pfs[f].sweeps);
+    hist_width = std::max(hist_width, pfs[f].sweep_width);
+  }
+  if (!segs.empty()) std::memcpy(hS, segs.data(), sizeof(Segment) * segs.size());
+  CUDA_TRY(cudaMemcpyAsync(dF, hF, meta_bytes, cudaMemcpyHostToDevice, st));
+  // A1: copy and pack coordinates
+  size_t roff = 0;
+  for (int f = 0; f < k; ++f) {
+    const dh_frame* fr = pfs[f].src;
+    if (fr->n == 0) continue;
+    int stride = (fr->flags & DH_COORDS_F4) ? 4 : 3;
+    const float* src = fr->coords;
+    if (host_coords) {
+      float* dst = (float*)c->raw.p + roff;
+      CUDA_TRY(cudaMemcpyAsync(dst, fr->coords, sizeof(float) * (size_t)fr->n * stride, cudaMemcpyHostToDevice, st));
+      src = dst;
+      roff += (size_t)fr->n * stride;
+    }
+    CUDA_TRY(launch_stage(src, fr->n, stride, (float4*)c->X.p + xoff[f], dF + f, st));
+    ++launched;
+  }
+  CUDA_TRY(launch_frame_setup(dF, k, 0, st));
+  ++launched;
+  // A2-A8: one persistent launch per bin sweep
+  int grid = 0;
+  if (n_items > 0) {
+    int bps = pair_kernel_blocks_per_sm(hist_width);
+    if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", hist_width);
+    int64_t g = (int64_t)bps * c->num_sms;
+    grid = (int)std::min<int64_t>(g, n_items);
+    size_t smem = pair_kernel_smem(hist_width);
+    if (c->ev_pair0) CUDA_TRY(cudaEventRecord(c->ev_pair0, st));
+    for (int p = 0; p < max_pass; ++p) {
+      CUDA_TRY(cudaMemsetAsync(c->ctl.p, 0, sizeof(Control), st));
+      PairLaunch L;
+      std::memset(&L, 0, sizeof L);
+      L.frames = dF;
+      L.segs = dS;
+      L.n_segs = (int32_t)segs.size();
+      L.pass = p;
+      L.n_items = n_items;
+      L.hist_width = hist_width;
+      L.ctl = (Control*)c->ctl.p;
+      CUDA_TRY(launch_pairs(L, grid, smem, st));
+      ++launched;
+    }
+    if (c->ev_pair1) CUDA_TRY(cudaEventRecord(c->ev_pair1, st));
+  }
+  c->timed = (c->ev_pair0 != nullptr) && n_items > 0;
+  dh_stats& S = c->stats;
+  std::memset(&S, 0, sizeof S);
+  for (auto& pf : pfs) S.pairs += pf.pairs;
+  S.sweeps = max_pass;
+  S.blocks = grid;
+  S.items = (int32_t)std::min<int64_t>(n_items, 0x7FFFFFFF);
+  S.kernel_launches = launched;
+  return DH_OK;
+}
+
+// After the stream has drained: read back per-frame flags and statistics.
+dh_status finish_frames(dh_ctx* c, int k) {
+  FrameDev* hF = (FrameDev*)c->hmeta.p;
+  CUDA_TRY(cudaMemcpyAsync(hF, c->meta.p, sizeof(FrameDev) * (size_t)k, cudaMemcpyDeviceToHost, c->stream()));
+  int32_t tstat = 0;
+  CUDA_TRY(cudaMemcpyAsync(&tstat, c->tstat.p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream()));
+  CUDA_TRY(cudaStreamSynchronize(c->stream()));
+  if (tstat != 0) return fail(DH_ERR_CUDA, "bin threshold table did not converge");
+  if (c->timed) {
+    float ms = 0.0f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev_pair0, c->ev_pair1));
+    c->stats.pair_kernel_ms = ms;
+  }
+  for (int f = 0; f < k; ++f) {
+    c->stats.deferred += hF[f].deferred;
+    c->stats.exact_fallback += hF[f].deferred;
+    if (hF[f].bad) return fail(DH_ERR_INVALID, "frame %d has non-finite coordinates", f);
+  }
+  return DH_OK;
+}
+
+dh_status run_frames(dh_ctx* c, const dh_frame* frames, int k, bool wait) {
+  if (k < 0) return fail(DH_ERR_INVALID, "negative frame count");
+  if (k == 0) return DH_OK;
+  std::vector<PlannedFrame> pfs((size_t)k);
+  bool dev = (frames[0].flags & DH_DEVICE_PTRS) != 0;
+  for (int f = 0; f < k; ++f) {
+    dh_status s = check_frame(&frames[f], pfs[f], c->max_width);
+    if (s != DH_OK) return s;
+    if (((frames[f].flags & DH_DEVICE_PTRS) != 0) != dev)
+      return fail(DH_ERR_INVALID, "all frames of a batch must use the same pointer kind");
+  }
+  cudaStream_t st = c->stream();
+  std::vector<uint64_t*> dev_out((size_t)k);
+  std::vector<size_t> hoff((size_t)k + 1, 0);
+  for (int f = 0; f < k; ++f) hoff[f + 1] = hoff[f] + (size_t)pfs[f].n_hist * frames[f].nbins;
+  if (dev) {
+    for (int f = 0; f < k; ++f) {
+      dev_out[f] = frames[f].out;
+      if (!(frames[f].flags & DH_ACCUMULATE))
+        CUDA_TRY(cudaMemsetAsync(frames[f].out, 0, sizeof(uint64_t) * (hoff[f + 1] - hoff[f]), st));
+    }
+  } else {
+    CUDA_TRY(c->hist.ensure(sizeof(uint64_t) * std::max<size_t>(hoff[k], 1)));
+    CUDA_TRY(cudaMemsetAsync(c->hist.p, 0, sizeof(uint64_t) * hoff[k], st));
+    for (int f = 0; f < k; ++f) dev_out[f] = (uint64_t*)c->hist.p + hoff[f];
+  }
+  CUDA_TRY(cudaMemsetAsync(c->tstat.p, 0, sizeof(int32_t), st));
+  dh_status s = enqueue_frames(c, pfs, dev_out, !dev);
+  if (s != DH_OK) return s;
+  if (!dev) {
+    bool any_acc = false;
+    for (int f = 0; f < k; ++f) any_acc |= (frames[f].flags & DH_ACCUMULATE) != 0;
+    if (any_acc) CUDA_TRY(c->hout.ensure(sizeof(uint64_t) * std::max<size_t>(hoff[k], 1)));
+    for (int f = 0; f < k; ++f) {
+      size_t cnt = hoff[f + 1] - hoff[f];
+      if (frames[f].flags & DH_ACCUMULATE)
+        CUDA_TRY(cudaMemcpyAsync((uint64_t*)c->hout.p + hoff[f], dev_out[f], sizeof(uint64_t) * cnt,
+                                 cudaMemcpyDeviceToHost, st));
+      else
+        CUDA_TRY(cudaMemcpyAsync(frames[f].out, dev_out[f], sizeof(uint64_t) * cnt, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  if (!wait && dev) {
+    c->pending_async = true;
+    return DH_OK;
+  }
+  s = finish_frames(c, k);
+  if (s != DH_OK) return s;
+  if (!dev) {
+    for (int f = 0; f < k; ++f)
+      if (frames[f].flags & DH_ACCUMULATE) {
+        const uint64_t* src = (const uint64_t*)c->hout.p + hoff[f];
+        for (size_t q = 0; q < hoff[f + 1] - hoff[f]; ++q) frames[f].out[q] += src[q];
+      }
+  }
+  return DH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dh_version(void) { return "dh 0.1 (sm_103a)"; }
+
+const char* dh_last_error(dh_ctx*) { return g_last_error.c_str(); }
+
+dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds) {
+  if (!thresholds) return fail(DH_ERR_INVALID, "thresholds is NULL");
+  if (nbins < 1 || nbins > DH_MAX_BINS) return fail(DH_ERR_INVALID, "nbins out of range");
+  if (!(r_max > 0.0) || !std::isfinite(r_max)) return fail(DH_ERR_INVALID, "r_max must be > 0 and finite");
+  if (!build_thresholds_host(r_max, nbins, thresholds))
+    return fail(DH_ERR_INVALID, "threshold search did not converge");
+  return DH_OK;
+}
+
+dh_status dh_create(const dh_config* config, dh_ctx** out) {
+  if (!out) return fail(DH_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  std::unique_ptr<dh_ctx> c(new dh_ctx());
+  if (config) c->cfg = *config;
+  c->device = c->cfg.device;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (c->device < 0 || c->device >= ndev) return fail(DH_ERR_INVALID, "device %d not present", c->device);
+  CUDA_TRY(cudaSetDevice(c->device));
+  CUDA_TRY(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  c->max_width = pair_kernel_max_width();
+  if (c->max_width < 1024) return fail(DH_ERR_CUDA, "not enough shared memory per block");
+  CUDA_TRY(c->ctl.ensure(sizeof(Control)));
+  CUDA_TRY(c->tstat.ensure(64));
+  if (c->cfg.flags & DH_CFG_TIMING) {
+    CUDA_TRY(cudaEventCreate(&c->ev_pair0));
+    CUDA_TRY(cudaEventCreate(&c->ev_pair1));
+  }
+  *out = c.release();
+  return DH_OK;
+}
+
+dh_status dh_destroy(dh_ctx* c) {
+  if (!c) return DH_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream());
+  for (auto& kv : c->tcache) cudaFree(kv.second);
+  c->raw.release();
+  c->X.release();
+  c->hist.release();
+  c->meta.release();
+  c->ctl.release();
+  c->tstat.release();
+  c->hmeta.release();
+  c->hout.release();
+  if (c->ev_pair0) cudaEventDestroy(c->ev_pair0);
+  if (c->ev_pair1) cudaEventDestroy(c->ev_pair1);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+  return DH_OK;
+}
+
+dh_status dh_set_stream(dh_ctx* c, void* stream) {
+  if (!c) return fail(DH_ERR_INVALID, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  c->user_stream = (cudaStream_t)stream;
+  c->has_user_stream = stream != nullptr;
+  return DH_OK;
+}
+
+dh_status dh_histogram(dh_ctx* c, const dh_frame* frame) {
+  if (!c || !frame) return fail(DH_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  return run_frames(c, frame, 1, true);
+}
+
+dh_status dh_histogram_async(dh_ctx* c, const dh_frame* frame) {
+  if (!c || !frame) return fail(DH_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  return run_frames(c, frame, 1, false);
+}
+
+dh_status dh_sync(dh_ctx* c) {
+  if (!c) return fail(DH_ERR_INVALID, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  if (!c->pending_async) {
+    CUDA_TRY(cudaStreamSynchronize(c->stream()));
+    return DH_OK;
+  }
+  c->pending_async = false;
+  return finish_frames(c, 1);
+}
+
+dh_status dh_histogram_batch(dh_ctx* c, const dh_frame* frames, int32_t k) {
+  if (!c || (k > 0 && !frames)) return fail(DH_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  return run_frames(c, frames, k, true);
+}
+
+dh_status dh_get_stats(dh_ctx* c, dh_stats* s) {
+  if (!c || !s) return fail(DH_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  *s = c->stats;
+  return DH_OK;
+}
+
+dh_status dh_submit(dh_ctx*, const dh_frame*, uint64_t*) { return fail(DH_ERR_INVALID, "not built yet"); }
+dh_status dh_poll(dh_ctx*, uint64_t) { return fail(DH_ERR_NOTFOUND, "not built yet"); }
+dh_status dh_wait(dh_ctx*, uint64_t, uint64_t) { return fail(DH_ERR_NOTFOUND, "not built yet"); }
+dh_status dh_cancel(dh_ctx*, uint64_t) { return fail(DH_ERR_NOTFOUND, "not built yet"); }
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry point,
+and its host-only logic (the binary64 bin thresholds) agrees with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1808_01478_gb300 as dh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1808_01478_gb300 import build
+
+    build.build()
+    return dh.load_library()
+
+
+def declared_entry_points():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            text = open(os.path.join(inc, fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(dh_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for required in ("dh_create", "dh_destroy", "dh_histogram", "dh_histogram_batch", "dh_submit",
+                     "dh_poll", "dh_wait", "dh_cancel", "dh_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_entry_points():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert dh.dh_version().startswith("dh ")
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_entry_points()) <= set(dh.exported_symbols())
+
+
+@pytest.mark.parametrize("r_max,nbins", [(17.33, 1000), (30.0, 10000), (35.0, 20000), (0.1, 1),
+                                         (1e-3, 7), (123.456, 4096), (2.0, 3)])
+def test_thresholds_agree_with_oracle_bin(lib, oracle_mod, r_max, nbins):
+    T = dh.dh_bin_thresholds(r_max, nbins)
+    assert T[0] == 0.0
+    assert np.all(np.diff(T) > 0)
+    ks = range(1, nbins + 1) if nbins <= 1000 else \
+        sorted(set(np.random.default_rng(0).integers(1, nbins + 1, 600).tolist()) | {1, nbins})
+    for k in ks:
+        # T[k] is in bin >= k and the next smaller double is in bin < k
+        assert oracle_mod.bin_of(T[k], r_max, nbins) >= k
+        assert oracle_mod.bin_of(np.nextafter(T[k], 0.0), r_max, nbins) < k
+        # and the threshold is where the edge is expected
+        assert abs(np.sqrt(T[k]) - k * r_max / nbins) <= 1e-12 * r_max
+
+
+def test_thresholds_reject_bad_arguments(lib):
+    with pytest.raises(dh.DHError):
+        dh.dh_bin_thresholds(0.0, 10)
+    with pytest.raises(dh.DHError):
+        dh.dh_bin_thresholds(1.0, 0)
+    with pytest.raises(dh.DHError):
+        dh.dh_bin_thresholds(float("nan"), 10)

@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, bin for bin.
+
+Histogram counts are integers, so the bar is bit-exact equality on every bin.
+Sizes are chosen so the oracle finishes in seconds while the GPU work still
+spans several 1024x1024 tiles with ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1808_01478_gb300 as dh
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_mod):
+    c = dh.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_hist(ctx, torch, f, device=True, f4=False):
+    if device:
+        x = torch.from_numpy(f.coords).cuda()
+        if f4:
+            x = torch.cat([x, torch.zeros_like(x[:, :1])], 1).contiguous()
+        out = ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins)
+        torch.cuda.synchronize()
+        return out.cpu().numpy().view(np.uint64)
+    c = f.coords
+    if f4:
+        c = np.concatenate([c, np.zeros((c.shape[0], 1), np.float32)], 1)
+    return ctx.histogram(c, f.offsets, f.box_type, f.box, f.r_max, f.nbins)
+
+
+def assert_same(got, want, name=""):
+    assert got.shape == want.shape, (got.shape, want.shape)
+    if not np.array_equal(got, want):
+        bad = np.argwhere(got != want)
+        h, k = bad[0]
+        raise AssertionError(f"{name}: {len(bad)} bins differ; first (h={h}, bin={k}): "
+                             f"gpu {got[h, k]} oracle {want[h, k]}; sums {got.sum()} vs {want.sum()}")
+
+
+def small_cases():
+    tric = w.triclinic_box(80, 80, 80, *w.C3_ANGLES)
+    return {
+        "nobox_c1": w.config_small_nobox(seed=1),
+        "nobox_ragged": w.uniform_frame(4, 3333, w.BOX_NONE, w.ortho_box(9.0), 16.0, 1000),
+        "ortho_c2_small": w.config_ortho_two_species(seed=2, n=6000),
+        "ortho_aniso": w.uniform_frame(5, 4100, w.BOX_ORTHO, w.ortho_box(20.0, 13.0, 31.0), 6.4, 3000,
+                                       n_species=3),
+        "tric_c3_small": w.config_triclinic_clusters(seed=3, n=6000, n_clusters=10, edge=80.0),
+        "tric_search": w.uniform_frame(6, 2500, w.BOX_TRICLINIC, w.triclinic_box(20, 20, 20, *w.C3_ANGLES),
+                                       14.0, 2000, n_species=2),
+        "tric_skewed": w.uniform_frame(7, 3000, w.BOX_TRICLINIC, w.triclinic_box(30, 25, 28, 80, 75, 105),
+                                       0.9 * w.box_heights(w.triclinic_box(30, 25, 28, 80, 75, 105)).min() / 2,
+                                       5000),
+        "tric_c3_box_uniform": w.uniform_frame(8, 4000, w.BOX_TRICLINIC, tric, 35.0, 20000, n_species=3),
+    }
+
+
+CASES = small_cases()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_parity_small(ctx, torch_mod, oracle_mod, name):
+    f = CASES[name]
+    want = oracle_mod.histogram_frame(f)
+    got = gpu_hist(ctx, torch_mod, f)
+    assert_same(got, want, name)
+    st = ctx.stats()
+    assert st["pairs"] == f.n_pairs()
+
+
+@pytest.mark.parametrize("name", ["nobox_ragged", "ortho_c2_small", "tric_c3_small"])
+def test_parity_host_pointers_and_f4(ctx, torch_mod, oracle_mod, name):
+    f = CASES[name]
+    want = oracle_mod.histogram_frame(f)
+    assert_same(gpu_hist(ctx, torch_mod, f, device=False), want, name + "/host")
+    assert_same(gpu_hist(ctx, torch_mod, f, device=True, f4=True), want, name + "/f4")
+    assert_same(gpu_hist(ctx, torch_mod, f, device=False, f4=True), want, name + "/host-f4")
+
+
+def test_multi_sweep_wide_histogram(ctx, torch_mod, oracle_mod):
+    # more bins than one block's shared memory holds: several passes over the pairs
+    f = w.uniform_frame(9, 3000, w.BOX_ORTHO, w.ortho_box(40.0), 20.0, 150_000, n_species=2)
+    want = oracle_mod.histogram_frame(f)
+    got = gpu_hist(ctx, torch_mod, f)
+    assert ctx.stats()["sweeps"] >= 2
+    assert_same(got, want, "multi-sweep")
+
+
+@pytest.mark.parametrize("spacing,box_type", [(0.1, w.BOX_NONE), (0.25, w.BOX_ORTHO), (0.5, w.BOX_NONE)])
+def test_adversarial_lattice_edges(ctx, torch_mod, oracle_mod, spacing, box_type):
+    # lattice spacing == bin width: a large share of pairs sits within ulps of bin edges
+    per = 14
+    g = np.arange(per, dtype=np.float64) * spacing
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
+    side = per * spacing
+    if box_type == w.BOX_ORTHO:
+        box = w.ortho_box(side)
+        r_max = side / 2
+    else:
+        box = np.zeros(9)
+        r_max = side * math.sqrt(3)
+    nbins = int(round(r_max / spacing))
+    f = w.frame_from(x, [0, len(x)], box_type, box, r_max, nbins, "lattice")
+    want = oracle_mod.histogram_frame(f)
+    got = gpu_hist(ctx, torch_mod, f)
+    assert_same(got, want, "lattice")
+    assert ctx.stats()["deferred"] > 0
+
+
+def test_edge_sizes(ctx, torch_mod, oracle_mod):
+    rng = np.random.default_rng(0)
+    for n, offs in [(0, [0, 0]), (1, [0, 1]), (2, [0, 2]), (5, [0, 0, 5, 5]), (1025, [0, 1, 1024, 1025]),
+                    (2049, [0, 2049]), (1024, [0, 512, 1024])]:
+        x = (rng.random((n, 3)) * 5).astype(np.float32)
+        f = w.frame_from(x, offs, w.BOX_NONE, np.zeros(9), 9.0, 17, f"n{n}")
+        want = oracle_mod.histogram_frame(f)
+        got = ctx.histogram(x, offs, f.box_type, f.box, f.r_max, f.nbins)
+        assert_same(got, want, f.name)
+    # one bin, and more bins than pairs
+    f = w.uniform_frame(1, 700, w.BOX_ORTHO, w.ortho_box(5.0), 2.5, 1)
+    assert_same(gpu_hist(ctx, torch_mod, f), oracle_mod.histogram_frame(f), "nbins=1")
+
+
+def test_accumulate(ctx, torch_mod, oracle_mod):
+    f = CASES["ortho_aniso"]
+    want = oracle_mod.histogram_frame(f)
+    out = np.full(want.shape, 7, dtype=np.uint64)
+    ctx.histogram(f.coords, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out=out, accumulate=True)
+    assert_same(out, want + np.uint64(7), "accumulate-host")
+    x = torch_mod.from_numpy(f.coords).cuda()
+    o = torch_mod.from_numpy(want.view(np.int64).copy()).cuda()
+    ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out=o, accumulate=True)
+    assert_same(o.cpu().numpy().view(np.uint64), want * np.uint64(2), "accumulate-device")
+
+
+def test_invalid_arguments(ctx, torch_mod):
+    x = np.zeros((4, 3), np.float32)
+    x[2, 1] = np.nan
+    with pytest.raises(dh.DHError) as e:
+        ctx.histogram(x, [0, 4], w.BOX_NONE, None, 1.0, 4)
+    assert e.value.status == dh.DH_ERR_INVALID
+    good = np.random.default_rng(1).random((10, 3)).astype(np.float32)
+    bad_cases = [
+        dict(offsets=[0, 5], box_type=w.BOX_NONE, box=None, r_max=1.0, nbins=4),
+        dict(offsets=[0, 10], box_type=w.BOX_NONE, box=None, r_max=-1.0, nbins=4),
+        dict(offsets=[0, 10], box_type=w.BOX_NONE, box=None, r_max=1.0, nbins=0),
+        dict(offsets=[0, 10], box_type=w.BOX_ORTHO, box=[1, 0.1, 0, 0, 1, 0, 0, 0, 1], r_max=1.0, nbins=4),
+        dict(offsets=[0, 10], box_type=w.BOX_TRICLINIC, box=[1, 0.9, 0, 0, 1, 0, 0, 0, 1], r_max=0.1, nbins=4),
+        dict(offsets=[0, 10], box_type=w.BOX_TRICLINIC, box=[1, 0, 0, 0.2, 1, 0, 0, 0, 1], r_max=0.1, nbins=4),
+        dict(offsets=[0, 6, 4, 10], box_type=w.BOX_NONE, box=None, r_max=1.0, nbins=4),
+        dict(offsets=[0, 10], box_type=7, box=None, r_max=1.0, nbins=4),
+    ]
+    for kw in bad_cases:
+        with pytest.raises(dh.DHError) as e:
+            ctx.histogram(good, **kw)
+        assert e.value.status == dh.DH_ERR_INVALID, kw
+    # the context stays usable after errors
+    f = CASES["nobox_c1"]
+    got = ctx.histogram(f.coords, f.offsets, f.box_type, f.box, f.r_max, f.nbins)
+    assert int(got.sum()) == 1_999_000
+
+
+def test_repeat_calls_identical_and_threshold_cache(ctx, torch_mod, oracle_mod):
+    f = CASES["tric_c3_small"]
+    want = oracle_mod.histogram_frame(f)
+    for _ in range(3):
+        assert_same(gpu_hist(ctx, torch_mod, f), want, "repeat")
