@@ -171,6 +171,22 @@ const char* dh_last_error(dh_ctx* ctx);
  * and is counted iff q < thresholds[nbins].  thresholds must hold nbins+1 doubles. */
 dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds);
 
+/* Diagnostics of the float32 decision rule (not part of the histogram).
+ *  what = DH_CHECK_SQRT: out[0] = largest relative error of the float32 square
+ *    root of the fast path over every float in [1, 4), against the correctly
+ *    rounded value; the window derivation assumes at most 2^-21.
+ *  what = DH_CHECK_WINDOW: stages `frame` (as dh_histogram would) and evaluates
+ *    n_samples pairs (i, j) drawn with splitmix64 from `seed`: out[0] = largest
+ *    |t32 - t64| / delta, where t = nbins * r / r_max in float32 (fast path) and
+ *    binary64 (definition) and delta is the frame's decision window (must be
+ *    < 1); out[1] = sampled pairs the float32 path would decide whose bin differs
+ *    from the binary64 bin (must be 0); out[2] = pairs compared; out[3] = delta.
+ * out must hold 4 doubles.  Synchronous. */
+#define DH_CHECK_SQRT 0
+#define DH_CHECK_WINDOW 1
+dh_status dh_selfcheck(dh_ctx* ctx, int32_t what, const dh_frame* frame, uint64_t n_samples, uint64_t seed,
+                       double* out);
+
 /* Library version string. */
 const char* dh_version(void);
 

@@ -91,7 +91,12 @@ _SIGNATURES = {
     "dh_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "dh_bin_thresholds": ([ctypes.c_double, ctypes.c_int32, ctypes.c_void_p], ctypes.c_int),
     "dh_version": ([], ctypes.c_char_p),
+    "dh_selfcheck": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                      ctypes.c_void_p], ctypes.c_int),
 }
+
+DH_CHECK_SQRT = 0
+DH_CHECK_WINDOW = 1
 
 
 def load_library(path: str | None = None) -> ctypes.CDLL:
@@ -187,6 +192,14 @@ def dh_wait(ctx, ticket: int, timeout_ns: int) -> int:
 
 def dh_cancel(ctx, ticket: int) -> int:
     return load_library().dh_cancel(ctx, ticket)
+
+
+def dh_selfcheck(ctx, what: int, frame: dh_frame | None = None, n_samples: int = 0, seed: int = 0) -> np.ndarray:
+    out = np.zeros(4, dtype=np.float64)
+    fp = ctypes.byref(frame) if frame is not None else None
+    _check(load_library().dh_selfcheck(ctx, int(what), fp, int(n_samples), int(seed),
+                                       out.ctypes.data_as(ctypes.c_void_p)), ctx)
+    return out
 
 
 def dh_get_stats(ctx) -> dict:
@@ -300,6 +313,15 @@ class Context:
 
     def stats(self) -> dict:
         return dh_get_stats(self.handle)
+
+    def check_sqrt(self) -> float:
+        return float(dh_selfcheck(self.handle, DH_CHECK_SQRT)[0])
+
+    def check_window(self, coords, offsets, box_type, box, r_max, nbins, n_samples=1 << 22, seed=1) -> dict:
+        fa = FrameArgs(coords, offsets, box_type, box, r_max, nbins)
+        out = dh_selfcheck(self.handle, DH_CHECK_WINDOW, fa.frame, n_samples, seed)
+        return {"max_ratio": float(out[0]), "violations": int(out[1]), "checked": int(out[2]),
+                "delta": float(out[3])}
 
     # served path
     def submit(self, fa: FrameArgs) -> int:

@@ -50,41 +50,57 @@ struct FrameDev {
   unsigned long long exact;
 };
 
-// One species pair (a,b) of one frame, cut into kTile x kTile work items.
+// One species pair (a,b) of one frame and one bin sweep, cut into kTile x kTile
+// work items numbered row by row over (ti, tj) (intra-species: tj >= ti only).
+// A launch may carry only part of a segment's items: launch items
+// [item0, item0 + count) are the segment's items [item_base, item_base + count).
 struct Segment {
-  int32_t frame;
+  FrameDev* fd;
   int32_t intra;     // a == b: only tiles ti <= tj, pairs j > i
   int32_t h;         // histogram index within the frame
+  int32_t pass;      // bin sweep: bins [pass*w, min(nbins, (pass+1)*w)), w = fd->sweep_width
   int32_t n_ti, n_tj;
   int32_t a0, na, b0, nb;  // frame-local particle ranges of species a and b
   int32_t pad;
-  int64_t item0;     // first global item index
+  int64_t item0;     // first launch item of this segment
+  int64_t item_base; // segment-local index of that item
 };
 
+// Staging job: one frame's coordinates (n x stride floats) -> float4.
+struct StageJob {
+  const float* src;
+  float4* dst;
+  FrameDev* fd;
+  int64_t n;
+  int32_t stride;
+  int32_t pad;
+  int64_t chunk0;    // first staging chunk of this job
+};
+constexpr int kStageChunk = 8192;
+
 struct Control {
-  unsigned long long next_item;  // dynamic work counter (reset before each pass)
+  unsigned long long next_item;  // dynamic work counter (reset before each launch)
   int32_t status;                // 0 ok, else an error code
   int32_t pad;
 };
 
 struct PairLaunch {
-  FrameDev* frames;
   const Segment* segs;
   int32_t n_segs;
-  int32_t pass;
-  int64_t n_items;
   int32_t hist_width;  // shared-memory bins per block
-  int32_t pad;
+  int64_t n_items;
   Control* ctl;
 };
 
 // ---- launchers (dh_kernels.cu); all enqueue on `stream` and return the launch error
-cudaError_t launch_stage(const float* src, int64_t n, int stride, float4* dst, FrameDev* frame_dev,
-                         cudaStream_t stream);
+cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cudaStream_t stream);
 cudaError_t launch_frame_setup(FrameDev* frames, int n_frames, int pass_hi_max, cudaStream_t stream);
 cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* status,
                               cudaStream_t stream);
 cudaError_t launch_pairs(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream);
+cudaError_t launch_check_sqrt(unsigned long long* out, cudaStream_t stream);
+cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t seed, unsigned long long* out,
+                                cudaStream_t stream);
 size_t pair_kernel_smem(int hist_width);
 int pair_kernel_max_width();
 int pair_kernel_blocks_per_sm(int hist_width);

@@ -125,17 +125,28 @@ __global__ void thresholds_kernel(double r_max, int32_t nbins, double* T, int32_
 
 // ------------------------------------------------------------------ A1: staging
 
-// coords (n x stride floats) -> float4, per-axis min/max, finiteness.
-__global__ void stage_kernel(const float* __restrict__ src, int64_t n, int stride,
-                             float4* __restrict__ dst, FrameDev* F) {
+// Staging of several frames at once: block b handles chunk b of the job whose
+// chunk range contains it; coords (n x stride floats) -> float4, per-axis
+// min/max (for the error window) and finiteness.
+__global__ void stage_kernel(const StageJob* __restrict__ jobs, int n_jobs) {
+  const long long chunk = blockIdx.x;
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].chunk0 <= chunk) lo = mid; else hi = mid - 1;
+  }
+  const StageJob J = jobs[lo];
+  const int64_t i0 = (chunk - J.chunk0) * (int64_t)kStageChunk;
+  const int64_t i1 = min(J.n, i0 + (int64_t)kStageChunk);
   float mn0 = INFINITY, mn1 = INFINITY, mn2 = INFINITY;
   float mx0 = -INFINITY, mx1 = -INFINITY, mx2 = -INFINITY;
   int bad = 0;
-  int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+  const float* __restrict__ src = J.src;
+  const int stride = J.stride;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     float x = src[i * stride], y = src[i * stride + 1], z = src[i * stride + 2];
     bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
-    dst[i] = make_float4(x, y, z, 0.0f);
+    J.dst[i] = make_float4(x, y, z, 0.0f);
     mn0 = fminf(mn0, x); mn1 = fminf(mn1, y); mn2 = fminf(mn2, z);
     mx0 = fmaxf(mx0, x); mx1 = fmaxf(mx1, y); mx2 = fmaxf(mx2, z);
   }
@@ -149,6 +160,7 @@ __global__ void stage_kernel(const float* __restrict__ src, int64_t n, int strid
     bad |= __shfl_xor_sync(kFull, bad, o);
   }
   if ((threadIdx.x & 31) == 0) {
+    FrameDev* F = J.fd;
     if (mn0 <= mx0) {
       atomicMin(&F->cmin[0], ord_of(mn0)); atomicMin(&F->cmin[1], ord_of(mn1));
       atomicMin(&F->cmin[2], ord_of(mn2));
@@ -330,10 +342,10 @@ struct FastParams {
 };
 
 struct ItemDesc {
+  FrameDev* fd;
   int32_t valid;   // 0: no more work
-  int32_t frame;
   int32_t h;
-  int32_t seg_intra;
+  int32_t pass;
   int32_t i0, ni, j0, nj;
   int32_t masked;
   int32_t skip;    // frame has no bins in this pass
@@ -513,7 +525,7 @@ __device__ void decode_item(const PairLaunch& L, long long item, ItemDesc& it) {
     if (L.segs[mid].item0 <= item) lo = mid; else hi = mid - 1;
   }
   const Segment& s = L.segs[lo];
-  long long lid = item - s.item0;
+  long long lid = item - s.item0 + s.item_base;
   int ti, tj;
   if (s.intra) {
     // row ti starts at ti*n - ti*(ti-1)/2
@@ -532,17 +544,16 @@ __device__ void decode_item(const PairLaunch& L, long long item, ItemDesc& it) {
     tj = (int)(lid - (long long)ti * s.n_tj);
   }
   it.valid = 1;
-  it.frame = s.frame;
+  it.fd = s.fd;
   it.h = s.h;
-  it.seg_intra = s.intra;
+  it.pass = s.pass;
   it.i0 = s.a0 + ti * kTile;
   it.ni = min(kTile, s.na - ti * kTile);
   it.j0 = s.b0 + tj * kTile;
   it.nj = min(kTile, s.nb - tj * kTile);
   it.masked = (s.intra && ti == tj) ? 1 : 0;
-  const FrameDev& F = L.frames[s.frame];
-  int lo_bin = L.pass * F.sweep_width;
-  it.skip = (lo_bin >= F.nbins) ? 1 : 0;
+  int lo_bin = s.pass * s.fd->sweep_width;
+  it.skip = (lo_bin >= s.fd->nbins) ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(kBlock) pair_kernel(PairLaunch L) {
@@ -557,32 +568,44 @@ __global__ void __launch_bounds__(kBlock) pair_kernel(PairLaunch L) {
   uint2* q = sq + warp * kQueueCap;
   for (int k = tid; k < width_pad; k += kBlock) sh[k] = 0u;
 
-  int cur_frame = -1, cur_h = -1;
+  const FrameDev* cur_fd = nullptr;
+  int cur_h = -1, cur_pass = -1;
   unsigned long long since = 0;  // pairs accumulated in sh since the last flush
   FastParams P;
   uint64_t* cur_dst = nullptr;
   int cur_width = 0;
 
+  // Guided self-scheduling: thread 0 claims runs of consecutive items whose
+  // length shrinks with the work left (at most 64, at least 1), so a block
+  // mostly stays on one segment (few histogram flushes) and the tail stays fine.
+  long long run_next = 0, run_end = 0;
   for (;;) {
     if (tid == 0) {
-      unsigned long long item = atomicAdd(&L.ctl->next_item, 1ull);
-      if ((long long)item >= L.n_items) s_it.valid = 0;
-      else decode_item(L, (long long)item, s_it);
+      if (run_next >= run_end) {
+        long long cur = (long long)*(volatile unsigned long long*)&L.ctl->next_item;
+        long long ch = (L.n_items - cur) / (4LL * gridDim.x);
+        ch = ch < 1 ? 1 : (ch > 64 ? 64 : ch);
+        run_next = (long long)atomicAdd(&L.ctl->next_item, (unsigned long long)ch);
+        run_end = run_next + ch < (long long)L.n_items ? run_next + ch : (long long)L.n_items;
+      }
+      long long item = run_next++;
+      if (item >= L.n_items) s_it.valid = 0;
+      else decode_item(L, item, s_it);
     }
     __syncthreads();
     const ItemDesc it = s_it;
     if (!it.valid) break;
     if (!it.skip) {
-      const FrameDev& F = L.frames[it.frame];
+      const FrameDev& F = *it.fd;
       const unsigned long long pairs = (unsigned long long)it.ni * (unsigned long long)it.nj;
-      if (it.frame != cur_frame || it.h != cur_h || since + pairs > 0xFFFFFFFFull) {
-        if (cur_frame >= 0) {
+      if (it.fd != cur_fd || it.h != cur_h || it.pass != cur_pass || since + pairs > 0xFFFFFFFFull) {
+        if (cur_fd) {
           __syncthreads();
           flush_hist(sh, cur_width, cur_dst, tid);
           __syncthreads();
         }
-        if (it.frame != cur_frame) {
-          int lo_bin = L.pass * F.sweep_width;
+        if (it.fd != cur_fd || it.pass != cur_pass) {
+          int lo_bin = it.pass * F.sweep_width;
           int hi_bin = min(F.nbins, lo_bin + F.sweep_width);
           P.S = F.S;
           P.thr = F.all_defer ? -1.0f : 0.5f - F.delta;
@@ -596,14 +619,15 @@ __global__ void __launch_bounds__(kBlock) pair_kernel(PairLaunch L) {
           for (int c = 0; c < 3; ++c) P.inv[c] = F.invf[c];
           P.amb_thr = 0.5f - F.eps_s;
         }
-        cur_frame = it.frame;
+        cur_fd = it.fd;
         cur_h = it.h;
+        cur_pass = it.pass;
         cur_width = (int)P.width;
         cur_dst = F.out + (size_t)it.h * F.nbins + P.lo;
         since = 0;
       }
       since += pairs;
-      // stage the j tile (A1 layout: float4 per particle)
+      // stage the j tile (float4 per particle)
       for (int k = tid; k < it.nj; k += kBlock) sj[k] = __ldg(F.X + it.j0 + k);
       __syncthreads();
       unsigned ndef = 0;
@@ -613,14 +637,121 @@ __global__ void __launch_bounds__(kBlock) pair_kernel(PairLaunch L) {
         case V_TRIC: run_item<V_TRIC>(F, P, it, sj, sh, q, tid, lane, ndef); break;
         default: run_item<V_TRIC_SEARCH>(F, P, it, sj, sh, q, tid, lane, ndef); break;
       }
-      if (lane == 0 && ndef) atomicAdd(&L.frames[it.frame].deferred, (unsigned long long)ndef);
+      if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();
   }
-  if (cur_frame >= 0) {
+  if (cur_fd) {
     __syncthreads();
     flush_hist(sh, cur_width, cur_dst, tid);
   }
+}
+
+// ------------------------------------------------------------------ self checks
+
+// Largest relative error of sqrt.approx.ftz.f32 over every float in [1, 4)
+// (two binades: the relative error pattern repeats with the exponent's parity),
+// against the correctly rounded binary64 square root.
+__global__ void check_sqrt_kernel(unsigned long long* max_err_bits) {
+  const uint32_t base = 0x3F800000u;  // 1.0f
+  const uint32_t count = 2u << 23;    // [1, 4)
+  double worst = 0.0;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    float x = __uint_as_float(base + k);
+    double ref = __dsqrt_rn((double)x);
+    double e = fabs((double)sqrt_approx(x) - ref) / ref;
+    worst = fmax(worst, e);
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(kFull, worst, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(max_err_bits, (unsigned long long)__double_as_longlong(worst));
+}
+
+// splitmix64: a counter-based generator for the sampled pairs
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// For sampled pairs of one frame: the float32 bin coordinate t32 of the fast
+// path against t64 = nbins*sqrt(r2_64)/r_max from the binary64 definition.
+// out[0]: max |t32 - t64| / delta over pairs with t64 < nbins + 1 (bits of a
+// double); out[1]: pairs the fast path would decide (not near an edge) whose
+// float32 bin differs from the binary64 bin -- must be 0; out[2]: pairs checked.
+template <int V>
+__device__ void check_window_pair(const FrameDev& F, const FastParams& P, int i, int j,
+                                  double* worst, unsigned long long* viol, unsigned long long* checked) {
+  float4 pi = F.X[i], pj = F.X[j];
+  bool amb = false;
+  float t = pair_t<V>(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z), P, amb);
+  double r2 = exact_r2<V>(F, pi, pj);
+  double t64 = __ddiv_rn(__dmul_rn((double)F.nbins, __dsqrt_rn(r2)), F.r_max);
+  int k64 = bin_from_thresholds(F.T, F.nbins, r2);
+  float tc = min_nan(t, P.tclamp);
+  float fl = __fadd_rd(tc, kMagicFloor);
+  float fr = __fsub_rn(tc, __fsub_rn(fl, kMagicFloor));
+  bool nearedge = fabsf(__fsub_rn(fr, 0.5f)) > P.thr || amb;
+  int k32 = __float_as_int(fl) - __float_as_int(kMagicFloor);
+  if (t64 < (double)F.nbins + 1.0 && !amb) {
+    *worst = fmax(*worst, fabs((double)t - t64) / (double)F.delta);
+    ++*checked;
+  }
+  int k32c = k32 < F.nbins ? k32 : F.nbins;
+  if (!nearedge && k32c != k64) ++*viol;
+}
+
+__global__ void check_window_kernel(const FrameDev* Fp, uint64_t n_samples, uint64_t seed,
+                                    unsigned long long* out) {
+  const FrameDev& F = *Fp;
+  FastParams P;
+  P.S = F.S;
+  P.thr = F.all_defer ? -1.0f : 0.5f - F.delta;
+  P.tclamp = (float)F.nbins + 0.5f;
+  P.kbase = __float_as_int(kMagicFloor);
+  P.width = (uint32_t)F.nbins;
+  P.lo = 0;
+  for (int c = 0; c < 9; ++c) P.b[c] = F.Bf[c];
+  for (int c = 0; c < 3; ++c) P.inv[c] = F.invf[c];
+  P.amb_thr = 0.5f - F.eps_s;
+  double worst = 0.0;
+  unsigned long long viol = 0, checked = 0;
+  if (F.n >= 2) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_samples;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+      uint64_t h = mix64(seed ^ mix64(s));
+      int i = (int)(h % (uint64_t)F.n);
+      int j = (int)((h >> 32) % (uint64_t)F.n);
+      if (i == j) continue;
+      switch (F.variant) {
+        case V_NONE: check_window_pair<V_NONE>(F, P, i, j, &worst, &viol, &checked); break;
+        case V_ORTHO: check_window_pair<V_ORTHO>(F, P, i, j, &worst, &viol, &checked); break;
+        case V_TRIC: check_window_pair<V_TRIC>(F, P, i, j, &worst, &viol, &checked); break;
+        default: check_window_pair<V_TRIC_SEARCH>(F, P, i, j, &worst, &viol, &checked); break;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    worst = fmax(worst, __shfl_xor_sync(kFull, worst, o));
+    viol += __shfl_xor_sync(kFull, viol, o);
+    checked += __shfl_xor_sync(kFull, checked, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, (unsigned long long)__double_as_longlong(worst));
+    atomicAdd(out + 1, viol);
+    atomicAdd(out + 2, checked);
+  }
+}
+
+cudaError_t launch_check_sqrt(unsigned long long* out, cudaStream_t stream) {
+  check_sqrt_kernel<<<1024, 256, 0, stream>>>(out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t seed, unsigned long long* out,
+                                cudaStream_t stream) {
+  check_window_kernel<<<1024, 256, 0, stream>>>(F, n_samples, seed, out);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launchers
@@ -648,12 +779,9 @@ int pair_kernel_blocks_per_sm(int hist_width) {
   return nb;
 }
 
-cudaError_t launch_stage(const float* src, int64_t n, int stride, float4* dst, FrameDev* frame_dev,
-                         cudaStream_t stream) {
-  if (n <= 0) return cudaSuccess;
-  int64_t blocks = (n + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  stage_kernel<<<(unsigned)blocks, 256, 0, stream>>>(src, n, stride, dst, frame_dev);
+cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cudaStream_t stream) {
+  if (n_jobs <= 0 || n_chunks <= 0) return cudaSuccess;
+  stage_kernel<<<(unsigned)n_chunks, 256, 0, stream>>>(jobs, n_jobs);
   return cudaGetLastError();
 }
 

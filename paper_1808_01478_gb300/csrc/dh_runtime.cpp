@@ -8,118 +8,20 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <chrono>
 #include <cmath>
-#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <deque>
-#include <list>
-#include <map>
 #include <memory>
-#include <mutex>
 #include <string>
-#include <thread>
-#include <unordered_map>
 #include <vector>
 
-#include "../../include/dh.h"
-#include "dh_internal.h"
+#include "dh_runtime.h"
 
-using namespace dh;
+namespace dh {
 
 namespace {
-
 thread_local std::string g_last_error;
-
-dh_status fail(dh_status s, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
-  va_end(ap);
-  g_last_error = buf;
-  return s;
-}
-
-#define CUDA_TRY(expr)                                                                   \
-  do {                                                                                   \
-    cudaError_t e_ = (expr);                                                             \
-    if (e_ != cudaSuccess)                                                               \
-      return fail(e_ == cudaErrorMemoryAllocation ? DH_ERR_NOMEM : DH_ERR_CUDA, "%s: %s", \
-                  #expr, cudaGetErrorString(e_));                                        \
-  } while (0)
-
-// Device buffer that only grows.
-struct DevBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= cap) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    size_t want = std::max(bytes, cap + cap / 2);
-    cudaError_t e = cudaMalloc(&p, want);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return e;
-    }
-    cap = want;
-    return cudaSuccess;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-};
-
-struct HostBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= cap) return cudaSuccess;
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    cap = 0;
-    size_t want = std::max(bytes, cap + cap / 2);
-    cudaError_t e = cudaMallocHost(&p, want);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return e;
-    }
-    cap = want;
-    return cudaSuccess;
-  }
-  void release() {
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    cap = 0;
-  }
-};
-
-struct ThresholdKey {
-  uint64_t rbits;
-  int32_t nbins;
-  bool operator==(const ThresholdKey& o) const { return rbits == o.rbits && nbins == o.nbins; }
-  bool operator<(const ThresholdKey& o) const {
-    return rbits != o.rbits ? rbits < o.rbits : nbins < o.nbins;
-  }
-};
-
-// Frame checked and planned on the host.
-struct PlannedFrame {
-  const dh_frame* src;
-  int32_t variant;
-  int32_t n_hist;
-  int32_t sweeps;
-  int32_t sweep_width;
-  double margin;
-  uint64_t pairs;
-};
-
 bool is_finite(double v) { return std::isfinite(v); }
 
 // Smallest distance between opposite faces of the cell spanned by the columns of B.
@@ -141,38 +43,112 @@ double min_plane_spacing(const double* B) {
 
 }  // namespace
 
-struct dh_ctx {
-  int device = 0;
-  cudaStream_t own_stream = nullptr;
-  cudaStream_t user_stream = nullptr;
-  bool has_user_stream = false;
-  std::recursive_mutex mu;
-  int num_sms = 0;
-  int max_width = 0;
-  dh_config cfg{};
+dh_status fail(dh_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
 
-  DevBuf raw;      // caller coordinates copied from the host (n x stride floats)
-  DevBuf X;        // packed float4 coordinates
-  DevBuf hist;     // uint64 histograms (host-pointer outputs, or scratch)
-  DevBuf meta;     // FrameDev array + Segment array
-  DevBuf ctl;      // Control
-  HostBuf hmeta;   // pinned staging for meta
-  HostBuf hout;    // pinned staging for accumulate-on-host
-  DevBuf tstat;    // threshold build status
+const char* last_error_message() { return g_last_error.c_str(); }
 
-  std::map<ThresholdKey, double*> tcache;
-  std::list<ThresholdKey> tlru;
+cudaError_t DevBuf::ensure(size_t bytes) {
+  if (bytes <= cap) return cudaSuccess;
+  size_t want = std::max(bytes, cap + cap / 2);
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  cap = want;
+  return cudaSuccess;
+}
 
-  dh_stats stats{};
-  cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;  // pair-kernel timing (DH_CFG_TIMING)
-  bool timed = false;
-  bool pending_async = false;
-  std::vector<PlannedFrame> async_plan;
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+}
 
-  cudaStream_t stream() const { return has_user_stream ? user_stream : own_stream; }
-};
+cudaError_t HostBuf::ensure(size_t bytes) {
+  if (bytes <= cap) return cudaSuccess;
+  size_t want = std::max(bytes, cap + cap / 2);
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMallocHost(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  cap = want;
+  return cudaSuccess;
+}
 
-namespace {
+void HostBuf::release() {
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  cap = 0;
+}
+
+dh_status ThresholdCache::acquire(double r_max, int32_t nbins, cudaStream_t st, int32_t* status_dev,
+                                  double** T, int* launched) {
+  std::lock_guard<std::mutex> g(mu_);
+  Key key;
+  std::memcpy(&key.rbits, &r_max, 8);
+  key.nbins = nbins;
+  auto it = map_.find(key);
+  if (it != map_.end()) {
+    it->second.refs++;
+    it->second.last = ++tick_;
+    *T = it->second.T;
+    return DH_OK;
+  }
+  // evict least recently used tables nobody holds (stream-ordered free)
+  while (map_.size() >= cap_) {
+    auto victim = map_.end();
+    for (auto e = map_.begin(); e != map_.end(); ++e)
+      if (e->second.refs == 0 && (victim == map_.end() || e->second.last < victim->second.last)) victim = e;
+    if (victim == map_.end()) break;
+    cudaFreeAsync(victim->second.T, st);
+    rev_.erase(victim->second.T);
+    map_.erase(victim);
+  }
+  double* t = nullptr;
+  DH_CUDA_TRY(cudaMallocAsync((void**)&t, sizeof(double) * (size_t)(nbins + 1), st));
+  DH_CUDA_TRY(launch_thresholds(r_max, nbins, t, status_dev, st));
+  if (launched) ++*launched;
+  map_[key] = Entry{t, 1, ++tick_};
+  rev_[t] = key;
+  *T = t;
+  return DH_OK;
+}
+
+void ThresholdCache::release(const double* T) {
+  std::lock_guard<std::mutex> g(mu_);
+  auto r = rev_.find(T);
+  if (r == rev_.end()) return;
+  auto it = map_.find(r->second);
+  if (it != map_.end() && it->second.refs > 0) it->second.refs--;
+}
+
+void ThresholdCache::clear(cudaStream_t st) {
+  std::lock_guard<std::mutex> g(mu_);
+  for (auto& kv : map_) cudaFreeAsync(kv.second.T, st);
+  map_.clear();
+  rev_.clear();
+}
+
+int pair_grid(int num_sms, int bps, int64_t n_items) {
+  int64_t g = (int64_t)std::max(bps, 1) * num_sms;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, n_items));
+}
 
 dh_status check_frame(const dh_frame* f, PlannedFrame& pf, int max_width) {
   if (!f) return fail(DH_ERR_INVALID, "frame is NULL");
@@ -275,107 +251,99 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   }
 }
 
-// Tiles of one frame's species pairs, appended to segs; returns the item count.
-int64_t add_segments(const PlannedFrame& pf, int32_t frame_idx, int64_t item0, std::vector<Segment>& segs) {
+// Tiles of one frame's species pairs for every bin sweep, appended to segs
+// (fd: the frame's device descriptor); returns the item count.
+int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::vector<Segment>& segs) {
   const dh_frame* f = pf.src;
   const int64_t* o = f->species_offsets;
   int S = f->n_species;
   int64_t items = 0;
-  int h = 0;
-  for (int a = 0; a < S; ++a)
-    for (int b = a; b < S; ++b, ++h) {
-      int32_t na = (int32_t)(o[a + 1] - o[a]), nb = (int32_t)(o[b + 1] - o[b]);
-      bool intra = (a == b);
-      if (na == 0 || nb == 0 || (intra && na < 2)) continue;
-      Segment s;
-      std::memset(&s, 0, sizeof s);
-      s.frame = frame_idx;
-      s.intra = intra ? 1 : 0;
-      s.h = h;
-      s.a0 = (int32_t)o[a];
-      s.na = na;
-      s.b0 = (int32_t)o[b];
-      s.nb = nb;
-      s.n_ti = (na + kTile - 1) / kTile;
-      s.n_tj = (nb + kTile - 1) / kTile;
-      s.item0 = item0 + items;
-      int64_t n_items = intra ? (int64_t)s.n_ti * (s.n_ti + 1) / 2 : (int64_t)s.n_ti * s.n_tj;
-      items += n_items;
-      segs.push_back(s);
-    }
+  for (int pass = 0; pass < pf.sweeps; ++pass) {
+    int h = 0;
+    for (int a = 0; a < S; ++a)
+      for (int b = a; b < S; ++b, ++h) {
+        int32_t na = (int32_t)(o[a + 1] - o[a]), nb = (int32_t)(o[b + 1] - o[b]);
+        bool intra = (a == b);
+        if (na == 0 || nb == 0 || (intra && na < 2)) continue;
+        Segment s;
+        std::memset(&s, 0, sizeof s);
+        s.fd = fd;
+        s.intra = intra ? 1 : 0;
+        s.h = h;
+        s.pass = pass;
+        s.a0 = (int32_t)o[a];
+        s.na = na;
+        s.b0 = (int32_t)o[b];
+        s.nb = nb;
+        s.n_ti = (na + kTile - 1) / kTile;
+        s.n_tj = (nb + kTile - 1) / kTile;
+        s.item0 = item0 + items;
+        s.item_base = 0;
+        items += intra ? (int64_t)s.n_ti * (s.n_ti + 1) / 2 : (int64_t)s.n_ti * s.n_tj;
+        segs.push_back(s);
+      }
+  }
   return items;
 }
 
-dh_status get_thresholds(dh_ctx* c, double r_max, int32_t nbins, double** out, int* launched) {
-  uint64_t rb;
-  std::memcpy(&rb, &r_max, 8);
-  ThresholdKey key{rb, nbins};
-  auto it = c->tcache.find(key);
-  if (it != c->tcache.end()) {
-    c->tlru.remove(key);
-    c->tlru.push_front(key);
-    *out = it->second;
-    return DH_OK;
-  }
-  if (c->tcache.size() >= 64) {
-    ThresholdKey old = c->tlru.back();
-    c->tlru.pop_back();
-    // the table may still be read by queued work: free after the stream drains
-    cudaStreamSynchronize(c->stream());
-    cudaFree(c->tcache[old]);
-    c->tcache.erase(old);
-  }
-  double* T = nullptr;
-  CUDA_TRY(cudaMalloc(&T, sizeof(double) * (size_t)(nbins + 1)));
-  CUDA_TRY(launch_thresholds(r_max, nbins, T, (int32_t*)c->tstat.p, c->stream()));
-  ++*launched;
-  c->tcache[key] = T;
-  c->tlru.push_front(key);
-  *out = T;
-  return DH_OK;
+namespace {
+
+void release_held(dh_ctx* c) {
+  for (const double* T : c->held_tables) c->tcache.release(T);
+  c->held_tables.clear();
 }
 
 // Enqueue everything for k planned frames.  dev_out[f] is where frame f's
 // histograms are accumulated on the device (already zeroed or holding the
-// values to accumulate onto).
+// values to accumulate onto).  Launches: one staging kernel for all frames,
+// one setup kernel, threshold tables not yet cached, one pair kernel.
 dh_status enqueue_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const std::vector<uint64_t*>& dev_out,
-                         bool host_coords) {
+                         bool host_coords, bool with_pairs = true) {
   cudaStream_t st = c->stream();
   int k = (int)pfs.size();
   int launched = 0;
-  // coordinates
   std::vector<int64_t> xoff(k + 1, 0);
   size_t raw_floats = 0;
   for (int f = 0; f < k; ++f) {
     xoff[f + 1] = xoff[f] + pfs[f].src->n;
     if (host_coords) raw_floats += (size_t)pfs[f].src->n * ((pfs[f].src->flags & DH_COORDS_F4) ? 4 : 3);
   }
-  CUDA_TRY(c->X.ensure(sizeof(float4) * (size_t)std::max<int64_t>(xoff[k], 1)));
-  if (host_coords) CUDA_TRY(c->raw.ensure(sizeof(float) * std::max<size_t>(raw_floats, 1)));
-  // metadata: FrameDev[k] + Segment[...]
+  DH_CUDA_TRY(c->X.ensure(sizeof(float4) * (size_t)std::max<int64_t>(xoff[k], 1)));
+  if (host_coords) DH_CUDA_TRY(c->raw.ensure(sizeof(float) * std::max<size_t>(raw_floats, 1)));
+  // device metadata: FrameDev[k] | StageJob[k] | Segment[m], uploaded in one copy
+  DH_CUDA_TRY(c->meta.ensure(sizeof(FrameDev) * (size_t)k + sizeof(StageJob) * (size_t)k));
+  FrameDev* dF = (FrameDev*)c->meta.p;
   std::vector<Segment> segs;
   int64_t n_items = 0;
-  for (int f = 0; f < k; ++f) n_items += add_segments(pfs[f], f, n_items, segs);
-  size_t meta_bytes = sizeof(FrameDev) * (size_t)k + sizeof(Segment) * std::max<size_t>(segs.size(), 1);
-  CUDA_TRY(c->meta.ensure(meta_bytes));
-  CUDA_TRY(c->hmeta.ensure(meta_bytes));
+  for (int f = 0; f < k; ++f) n_items += add_segments(pfs[f], dF + f, n_items, segs);
+  size_t meta_bytes = sizeof(FrameDev) * (size_t)k + sizeof(StageJob) * (size_t)k +
+                      sizeof(Segment) * std::max<size_t>(segs.size(), 1);
+  DH_CUDA_TRY(c->meta.ensure(meta_bytes));
+  DH_CUDA_TRY(c->hmeta.ensure(meta_bytes));
+  if ((FrameDev*)c->meta.p != dF) {  // buffer moved: segments must point into the new one
+    dF = (FrameDev*)c->meta.p;
+    segs.clear();
+    n_items = 0;
+    for (int f = 0; f < k; ++f) n_items += add_segments(pfs[f], dF + f, n_items, segs);
+  }
   FrameDev* hF = (FrameDev*)c->hmeta.p;
-  Segment* hS = (Segment*)(hF + k);
-  FrameDev* dF = (FrameDev*)c->meta.p;
-  Segment* dS = (Segment*)(dF + k);
-  int max_pass = 1, hist_width = 1;
+  StageJob* hJ = (StageJob*)(hF + k);
+  Segment* hS = (Segment*)(hJ + k);
+  StageJob* dJ = (StageJob*)(dF + k);
+  Segment* dS = (Segment*)(dJ + k);
+  int hist_width = 1;
   for (int f = 0; f < k; ++f) {
     double* T = nullptr;
-    dh_status s = get_thresholds(c, pfs[f].src->r_max, pfs[f].src->nbins, &T, &launched);
+    dh_status s = c->tcache.acquire(pfs[f].src->r_max, pfs[f].src->nbins, st, (int32_t*)c->tstat.p, &T, &launched);
     if (s != DH_OK) return s;
+    c->held_tables.push_back(T);
     fill_frame_dev(pfs[f], hF[f], (const float4*)c->X.p + xoff[f], dev_out[f], T);
-    max_pass = std::max(max_pass, pfs[f].sweeps);
     hist_width = std::max(hist_width, pfs[f].sweep_width);
   }
-  if (!segs.empty()) std::memcpy(hS, segs.data(), sizeof(Segment) * segs.size());
-  CUDA_TRY(cudaMemcpyAsync(dF, hF, meta_bytes, cudaMemcpyHostToDevice, st));
-  // A1: copy and pack coordinates
+  // A1: coordinates to the device and packed to float4
   size_t roff = 0;
+  int n_jobs = 0;
+  int64_t n_chunks = 0;
   for (int f = 0; f < k; ++f) {
     const dh_frame* fr = pfs[f].src;
     if (fr->n == 0) continue;
@@ -383,41 +351,51 @@ dh_status enqueue_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
     const float* src = fr->coords;
     if (host_coords) {
       float* dst = (float*)c->raw.p + roff;
-      CUDA_TRY(cudaMemcpyAsync(dst, fr->coords, sizeof(float) * (size_t)fr->n * stride, cudaMemcpyHostToDevice, st));
+      DH_CUDA_TRY(cudaMemcpyAsync(dst, fr->coords, sizeof(float) * (size_t)fr->n * stride, cudaMemcpyHostToDevice, st));
       src = dst;
       roff += (size_t)fr->n * stride;
     }
-    CUDA_TRY(launch_stage(src, fr->n, stride, (float4*)c->X.p + xoff[f], dF + f, st));
+    StageJob& J = hJ[n_jobs++];
+    std::memset(&J, 0, sizeof J);
+    J.src = src;
+    J.dst = (float4*)c->X.p + xoff[f];
+    J.fd = dF + f;
+    J.n = fr->n;
+    J.stride = stride;
+    J.chunk0 = n_chunks;
+    n_chunks += (fr->n + kStageChunk - 1) / kStageChunk;
+  }
+  if (!segs.empty()) std::memcpy(hS, segs.data(), sizeof(Segment) * segs.size());
+  DH_CUDA_TRY(cudaMemcpyAsync(dF, hF, meta_bytes, cudaMemcpyHostToDevice, st));
+  if (n_jobs > 0) {
+    DH_CUDA_TRY(launch_stage(dJ, n_jobs, n_chunks, st));
     ++launched;
   }
-  CUDA_TRY(launch_frame_setup(dF, k, 0, st));
+  DH_CUDA_TRY(launch_frame_setup(dF, k, 0, st));
   ++launched;
-  // A2-A8: one persistent launch per bin sweep
+  // A2-A8: one persistent launch over every frame, species pair and bin sweep
   int grid = 0;
-  if (n_items > 0) {
+  int max_pass = 1;
+  for (auto& pf : pfs) max_pass = std::max(max_pass, pf.sweeps);
+  if (n_items > 0 && with_pairs) {
     int bps = pair_kernel_blocks_per_sm(hist_width);
     if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", hist_width);
-    int64_t g = (int64_t)bps * c->num_sms;
-    grid = (int)std::min<int64_t>(g, n_items);
+    grid = pair_grid(c->num_sms, bps, n_items);
     size_t smem = pair_kernel_smem(hist_width);
-    if (c->ev_pair0) CUDA_TRY(cudaEventRecord(c->ev_pair0, st));
-    for (int p = 0; p < max_pass; ++p) {
-      CUDA_TRY(cudaMemsetAsync(c->ctl.p, 0, sizeof(Control), st));
-      PairLaunch L;
-      std::memset(&L, 0, sizeof L);
-      L.frames = dF;
-      L.segs = dS;
-      L.n_segs = (int32_t)segs.size();
-      L.pass = p;
-      L.n_items = n_items;
-      L.hist_width = hist_width;
-      L.ctl = (Control*)c->ctl.p;
-      CUDA_TRY(launch_pairs(L, grid, smem, st));
-      ++launched;
-    }
-    if (c->ev_pair1) CUDA_TRY(cudaEventRecord(c->ev_pair1, st));
+    DH_CUDA_TRY(cudaMemsetAsync(c->ctl.p, 0, sizeof(Control), st));
+    if (c->ev_pair0) DH_CUDA_TRY(cudaEventRecord(c->ev_pair0, st));
+    PairLaunch L;
+    std::memset(&L, 0, sizeof L);
+    L.segs = dS;
+    L.n_segs = (int32_t)segs.size();
+    L.n_items = n_items;
+    L.hist_width = hist_width;
+    L.ctl = (Control*)c->ctl.p;
+    DH_CUDA_TRY(launch_pairs(L, grid, smem, st));
+    ++launched;
+    if (c->ev_pair1) DH_CUDA_TRY(cudaEventRecord(c->ev_pair1, st));
   }
-  c->timed = (c->ev_pair0 != nullptr) && n_items > 0;
+  c->timed = (c->ev_pair0 != nullptr) && n_items > 0 && with_pairs;
   dh_stats& S = c->stats;
   std::memset(&S, 0, sizeof S);
   for (auto& pf : pfs) S.pairs += pf.pairs;
@@ -431,14 +409,16 @@ dh_status enqueue_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
 // After the stream has drained: read back per-frame flags and statistics.
 dh_status finish_frames(dh_ctx* c, int k) {
   FrameDev* hF = (FrameDev*)c->hmeta.p;
-  CUDA_TRY(cudaMemcpyAsync(hF, c->meta.p, sizeof(FrameDev) * (size_t)k, cudaMemcpyDeviceToHost, c->stream()));
+  DH_CUDA_TRY(cudaMemcpyAsync(hF, c->meta.p, sizeof(FrameDev) * (size_t)k, cudaMemcpyDeviceToHost, c->stream()));
   int32_t tstat = 0;
-  CUDA_TRY(cudaMemcpyAsync(&tstat, c->tstat.p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream()));
-  CUDA_TRY(cudaStreamSynchronize(c->stream()));
+  DH_CUDA_TRY(cudaMemcpyAsync(&tstat, c->tstat.p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream()));
+  cudaError_t e = cudaStreamSynchronize(c->stream());
+  release_held(c);
+  DH_CUDA_TRY(e);
   if (tstat != 0) return fail(DH_ERR_CUDA, "bin threshold table did not converge");
   if (c->timed) {
     float ms = 0.0f;
-    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev_pair0, c->ev_pair1));
+    DH_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev_pair0, c->ev_pair1));
     c->stats.pair_kernel_ms = ms;
   }
   for (int f = 0; f < k; ++f) {
@@ -468,27 +448,31 @@ dh_status run_frames(dh_ctx* c, const dh_frame* frames, int k, bool wait) {
     for (int f = 0; f < k; ++f) {
       dev_out[f] = frames[f].out;
       if (!(frames[f].flags & DH_ACCUMULATE))
-        CUDA_TRY(cudaMemsetAsync(frames[f].out, 0, sizeof(uint64_t) * (hoff[f + 1] - hoff[f]), st));
+        DH_CUDA_TRY(cudaMemsetAsync(frames[f].out, 0, sizeof(uint64_t) * (hoff[f + 1] - hoff[f]), st));
     }
   } else {
-    CUDA_TRY(c->hist.ensure(sizeof(uint64_t) * std::max<size_t>(hoff[k], 1)));
-    CUDA_TRY(cudaMemsetAsync(c->hist.p, 0, sizeof(uint64_t) * hoff[k], st));
+    DH_CUDA_TRY(c->hist.ensure(sizeof(uint64_t) * std::max<size_t>(hoff[k], 1)));
+    DH_CUDA_TRY(cudaMemsetAsync(c->hist.p, 0, sizeof(uint64_t) * hoff[k], st));
     for (int f = 0; f < k; ++f) dev_out[f] = (uint64_t*)c->hist.p + hoff[f];
   }
-  CUDA_TRY(cudaMemsetAsync(c->tstat.p, 0, sizeof(int32_t), st));
+  DH_CUDA_TRY(cudaMemsetAsync(c->tstat.p, 0, sizeof(int32_t), st));
   dh_status s = enqueue_frames(c, pfs, dev_out, !dev);
-  if (s != DH_OK) return s;
+  if (s != DH_OK) {
+    cudaStreamSynchronize(st);
+    release_held(c);
+    return s;
+  }
   if (!dev) {
     bool any_acc = false;
     for (int f = 0; f < k; ++f) any_acc |= (frames[f].flags & DH_ACCUMULATE) != 0;
-    if (any_acc) CUDA_TRY(c->hout.ensure(sizeof(uint64_t) * std::max<size_t>(hoff[k], 1)));
+    if (any_acc) DH_CUDA_TRY(c->hout.ensure(sizeof(uint64_t) * std::max<size_t>(hoff[k], 1)));
     for (int f = 0; f < k; ++f) {
       size_t cnt = hoff[f + 1] - hoff[f];
       if (frames[f].flags & DH_ACCUMULATE)
-        CUDA_TRY(cudaMemcpyAsync((uint64_t*)c->hout.p + hoff[f], dev_out[f], sizeof(uint64_t) * cnt,
+        DH_CUDA_TRY(cudaMemcpyAsync((uint64_t*)c->hout.p + hoff[f], dev_out[f], sizeof(uint64_t) * cnt,
                                  cudaMemcpyDeviceToHost, st));
       else
-        CUDA_TRY(cudaMemcpyAsync(frames[f].out, dev_out[f], sizeof(uint64_t) * cnt, cudaMemcpyDeviceToHost, st));
+        DH_CUDA_TRY(cudaMemcpyAsync(frames[f].out, dev_out[f], sizeof(uint64_t) * cnt, cudaMemcpyDeviceToHost, st));
     }
   }
   if (!wait && dev) {
@@ -507,13 +491,63 @@ dh_status run_frames(dh_ctx* c, const dh_frame* frames, int k, bool wait) {
   return DH_OK;
 }
 
+dh_status selfcheck(dh_ctx* c, int32_t what, const dh_frame* frame, uint64_t n_samples, uint64_t seed, double* out) {
+  cudaStream_t st = c->stream();
+  DevBuf res;
+  DH_CUDA_TRY(res.ensure(4 * sizeof(unsigned long long)));
+  DH_CUDA_TRY(cudaMemsetAsync(res.p, 0, 4 * sizeof(unsigned long long), st));
+  unsigned long long h[4] = {0, 0, 0, 0};
+  for (int q = 0; q < 4; ++q) out[q] = 0.0;
+  if (what == DH_CHECK_SQRT) {
+    DH_CUDA_TRY(launch_check_sqrt((unsigned long long*)res.p, st));
+    DH_CUDA_TRY(cudaMemcpyAsync(h, res.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    DH_CUDA_TRY(cudaStreamSynchronize(st));
+    res.release();
+    std::memcpy(&out[0], &h[0], 8);
+    return DH_OK;
+  }
+  if (what != DH_CHECK_WINDOW || !frame) return fail(DH_ERR_INVALID, "unknown self check %d", what);
+  std::vector<PlannedFrame> pfs(1);
+  dh_status s = check_frame(frame, pfs[0], c->max_width);
+  if (s != DH_OK) return s;
+  bool dev = (frame->flags & DH_DEVICE_PTRS) != 0;
+  std::vector<uint64_t*> dev_out(1);
+  DH_CUDA_TRY(c->hist.ensure(sizeof(uint64_t) * (size_t)pfs[0].n_hist * frame->nbins));
+  dev_out[0] = (uint64_t*)c->hist.p;
+  DH_CUDA_TRY(cudaMemsetAsync(c->tstat.p, 0, sizeof(int32_t), st));
+  s = enqueue_frames(c, pfs, dev_out, !dev, false);
+  if (s == DH_OK) {
+    cudaError_t e = launch_check_window((const FrameDev*)c->meta.p, n_samples, seed, (unsigned long long*)res.p, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, res.p, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = fail(DH_ERR_CUDA, "self check: %s", cudaGetErrorString(e));
+  }
+  if (s == DH_OK) {
+    s = finish_frames(c, 1);
+  } else {
+    cudaStreamSynchronize(st);
+    release_held(c);
+  }
+  res.release();
+  if (s != DH_OK) return s;
+  double worst;
+  std::memcpy(&worst, &h[0], 8);
+  out[0] = worst;
+  out[1] = (double)h[1];
+  out[2] = (double)h[2];
+  out[3] = (double)((FrameDev*)c->hmeta.p)->delta;
+  return DH_OK;
+}
+
 }  // namespace
+}  // namespace dh
+
+using namespace dh;
 
 extern "C" {
 
 const char* dh_version(void) { return "dh 0.1 (sm_103a)"; }
 
-const char* dh_last_error(dh_ctx*) { return g_last_error.c_str(); }
+const char* dh_last_error(dh_ctx*) { return last_error_message(); }
 
 dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds) {
   if (!thresholds) return fail(DH_ERR_INVALID, "thresholds is NULL");
@@ -531,18 +565,18 @@ dh_status dh_create(const dh_config* config, dh_ctx** out) {
   if (config) c->cfg = *config;
   c->device = c->cfg.device;
   int ndev = 0;
-  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  DH_CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (c->device < 0 || c->device >= ndev) return fail(DH_ERR_INVALID, "device %d not present", c->device);
-  CUDA_TRY(cudaSetDevice(c->device));
-  CUDA_TRY(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
-  CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  DH_CUDA_TRY(cudaSetDevice(c->device));
+  DH_CUDA_TRY(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+  DH_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   c->max_width = pair_kernel_max_width();
   if (c->max_width < 1024) return fail(DH_ERR_CUDA, "not enough shared memory per block");
-  CUDA_TRY(c->ctl.ensure(sizeof(Control)));
-  CUDA_TRY(c->tstat.ensure(64));
+  DH_CUDA_TRY(c->ctl.ensure(sizeof(Control)));
+  DH_CUDA_TRY(c->tstat.ensure(64));
   if (c->cfg.flags & DH_CFG_TIMING) {
-    CUDA_TRY(cudaEventCreate(&c->ev_pair0));
-    CUDA_TRY(cudaEventCreate(&c->ev_pair1));
+    DH_CUDA_TRY(cudaEventCreate(&c->ev_pair0));
+    DH_CUDA_TRY(cudaEventCreate(&c->ev_pair1));
   }
   *out = c.release();
   return DH_OK;
@@ -552,7 +586,13 @@ dh_status dh_destroy(dh_ctx* c) {
   if (!c) return DH_OK;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream());
-  for (auto& kv : c->tcache) cudaFree(kv.second);
+  {
+    std::lock_guard<std::mutex> g(c->server_mu);
+    if (c->server) server_destroy(c->server);
+    c->server = nullptr;
+  }
+  c->tcache.clear(c->stream());
+  cudaStreamSynchronize(c->stream());
   c->raw.release();
   c->X.release();
   c->hist.release();
@@ -595,7 +635,7 @@ dh_status dh_sync(dh_ctx* c) {
   std::lock_guard<std::recursive_mutex> g(c->mu);
   cudaSetDevice(c->device);
   if (!c->pending_async) {
-    CUDA_TRY(cudaStreamSynchronize(c->stream()));
+    DH_CUDA_TRY(cudaStreamSynchronize(c->stream()));
     return DH_OK;
   }
   c->pending_async = false;
@@ -609,6 +649,14 @@ dh_status dh_histogram_batch(dh_ctx* c, const dh_frame* frames, int32_t k) {
   return run_frames(c, frames, k, true);
 }
 
+dh_status dh_selfcheck(dh_ctx* c, int32_t what, const dh_frame* frame, uint64_t n_samples, uint64_t seed,
+                       double* out) {
+  if (!c || !out) return fail(DH_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::recursive_mutex> g(c->mu);
+  cudaSetDevice(c->device);
+  return selfcheck(c, what, frame, n_samples, seed, out);
+}
+
 dh_status dh_get_stats(dh_ctx* c, dh_stats* s) {
   if (!c || !s) return fail(DH_ERR_INVALID, "NULL argument");
   std::lock_guard<std::recursive_mutex> g(c->mu);
@@ -616,9 +664,45 @@ dh_status dh_get_stats(dh_ctx* c, dh_stats* s) {
   return DH_OK;
 }
 
-dh_status dh_submit(dh_ctx*, const dh_frame*, uint64_t*) { return fail(DH_ERR_INVALID, "not built yet"); }
-dh_status dh_poll(dh_ctx*, uint64_t) { return fail(DH_ERR_NOTFOUND, "not built yet"); }
-dh_status dh_wait(dh_ctx*, uint64_t, uint64_t) { return fail(DH_ERR_NOTFOUND, "not built yet"); }
-dh_status dh_cancel(dh_ctx*, uint64_t) { return fail(DH_ERR_NOTFOUND, "not built yet"); }
+namespace {
+dh::Server* get_server(dh_ctx* c, dh_status* st) {
+  std::lock_guard<std::mutex> g(c->server_mu);
+  *st = DH_OK;
+  if (!c->server) c->server = server_create(c, st);
+  return c->server;
+}
+}  // namespace
+
+dh_status dh_submit(dh_ctx* c, const dh_frame* frame, uint64_t* ticket) {
+  if (!c || !frame || !ticket) return fail(DH_ERR_INVALID, "NULL argument");
+  dh_status st;
+  dh::Server* s = get_server(c, &st);
+  if (!s) return st;
+  return server_submit(s, frame, ticket);
+}
+
+dh_status dh_poll(dh_ctx* c, uint64_t ticket) {
+  if (!c) return fail(DH_ERR_INVALID, "ctx is NULL");
+  dh_status st;
+  dh::Server* s = get_server(c, &st);
+  if (!s) return st;
+  return server_poll(s, ticket);
+}
+
+dh_status dh_wait(dh_ctx* c, uint64_t ticket, uint64_t timeout_ns) {
+  if (!c) return fail(DH_ERR_INVALID, "ctx is NULL");
+  dh_status st;
+  dh::Server* s = get_server(c, &st);
+  if (!s) return st;
+  return server_wait(s, ticket, timeout_ns);
+}
+
+dh_status dh_cancel(dh_ctx* c, uint64_t ticket) {
+  if (!c) return fail(DH_ERR_INVALID, "ctx is NULL");
+  dh_status st;
+  dh::Server* s = get_server(c, &st);
+  if (!s) return st;
+  return server_cancel(s, ticket);
+}
 
 }  // extern "C"
