@@ -187,6 +187,33 @@ dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds);
 dh_status dh_selfcheck(dh_ctx* ctx, int32_t what, const dh_frame* frame, uint64_t n_samples, uint64_t seed,
                        double* out);
 
+/* Allocation-free histogram (the paper has no counterpart of this entry point).
+ *
+ * For callers that must not allocate device memory: code that runs while a
+ * CUDA graph is being captured, frameworks whose device memory belongs to
+ * their own allocator, processes with a fixed memory budget.  Every other
+ * entry point keeps its workspace in memory the context obtains with
+ * cudaMalloc; this one needs no context and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  It computes exactly what dh_histogram computes.
+ *
+ * frame->flags must contain DH_DEVICE_PTRS: coords and out are device
+ * pointers on the current device (species_offsets stays a host array); the
+ * work runs on `stream` (a cudaStream_t, NULL for the default stream) and the
+ * call returns when it has finished.  Scratch memory is one file-scope device
+ * array of DH_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits; limits: n <= DH_NOALLOC_MAX_N, nbins <=
+ * DH_NOALLOC_MAX_BINS, at most 256 species-pair work segments (n_species <= 15
+ * when one bin sweep suffices).  Larger frames return DH_ERR_INVALID.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array: each call clears what must start at
+ * zero, and calls whose GPU work overlaps (other streams, host threads) race
+ * on it and must be serialised by the caller. */
+#define DH_NOALLOC_MAX_N 131072
+#define DH_NOALLOC_MAX_BINS 65536
+#define DH_NOALLOC_SCRATCH_BYTES 2639104
+dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream);
+
 /* Library version string. */
 const char* dh_version(void);
 

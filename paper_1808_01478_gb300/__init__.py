@@ -93,7 +93,11 @@ _SIGNATURES = {
     "dh_version": ([], ctypes.c_char_p),
     "dh_selfcheck": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                       ctypes.c_void_p], ctypes.c_int),
+    "dh_histogram_noalloc": ([ctypes.POINTER(dh_frame), ctypes.c_void_p], ctypes.c_int),
 }
+
+DH_NOALLOC_MAX_N = 131072
+DH_NOALLOC_MAX_BINS = 65536
 
 DH_CHECK_SQRT = 0
 DH_CHECK_WINDOW = 1
@@ -200,6 +204,11 @@ def dh_selfcheck(ctx, what: int, frame: dh_frame | None = None, n_samples: int =
     _check(load_library().dh_selfcheck(ctx, int(what), fp, int(n_samples), int(seed),
                                        out.ctypes.data_as(ctypes.c_void_p)), ctx)
     return out
+
+
+def dh_histogram_noalloc(frame: dh_frame, stream_ptr: int | None = None) -> None:
+    """Allocation-free histogram of one frame with device pointers (no context needed)."""
+    _check(load_library().dh_histogram_noalloc(ctypes.byref(frame), ctypes.c_void_p(stream_ptr or 0)))
 
 
 def dh_get_stats(ctx) -> dict:
