@@ -20,6 +20,7 @@ constexpr int kRegI = 4;             // i-particles held in registers per thread
 constexpr int kTile = kBlock * kRegI;  // particles per tile edge (i and j)
 constexpr int kWarps = kBlock / 32;
 constexpr int kQueueCap = 64;        // deferred pairs per warp queue
+constexpr int kNumVariants = 4;
 
 // One frame as seen by the device.  Host fills the first part; the staging and
 // setup kernels fill the second.
@@ -27,6 +28,7 @@ struct FrameDev {
   const float4* X;   // packed coordinates (x,y,z,0), frame-local index
   uint64_t* out;     // S(S+1)/2 x nbins histograms of this frame
   const double* T;   // binary64 thresholds T[0..nbins]
+  const float2* Tf;  // the same thresholds as float pairs (hi, lo), hi + lo = T to ~2^-48
   int32_t variant;
   int32_t nbins;
   int32_t n;         // particles
@@ -35,19 +37,26 @@ struct FrameDev {
   double B[9];       // row-major, columns a,b,c
   double Linv[3];    // orthorhombic: 1.0/L per axis, binary64
   float Bf[9];       // float32 copies of B
+  float Bl[9];       // float32(B - Bf): B as double-float (Bf + Bl)
   float invf[3];     // float32 reciprocals: ortho 1/Lx,1/Ly,1/Lz; triclinic 1/ax,1/by,1/cz
   float S;           // float32(nbins / r_max)
+  float S2;          // float32((nbins / r_max)^2)
   float margin;      // triclinic: 1 - 2 r_max / h_min (no-search precondition margin)
   double eps_S;      // |S - nbins/r_max| / (nbins/r_max)
+  double eps_S2;     // |S2 - (nbins/r_max)^2| / (nbins/r_max)^2
   // ---- written on the device
   int32_t cmin[3];   // ordered-integer encodings of the per-axis coordinate min / max
   int32_t cmax[3];
   int32_t bad;       // a non-finite coordinate was seen
-  int32_t all_defer; // float32 decisions are not safe for this frame: every pair goes exact
-  float delta;       // float32 window half-width in bin units
+  int32_t all_defer; // float32 decisions are not safe for this frame: every pair is deferred
+  float qc2, qc1, qc0;  // near-edge test: |q - n^2| <= qc2*q + qc1*s + qc0 (q = t^2, s ~ t)
+  float mid2, mid1;  // double-float tier: |r2 - T[n]| <= mid2*r2 + mid1*s decides nothing
+  float tie_eps;     // orthorhombic: | |d'_c| - L_c/2 | <= tie_eps is re-decided in binary64
+  float delta;       // float32 window half-width in bin units at t = nbins (reported)
+  float alpha_t, beta_t;  // the t-space bound alpha*t + beta behind the q-space test
   float eps_s;       // search variant: fractional-coordinate ambiguity margin
-  unsigned long long deferred;  // statistics
-  unsigned long long exact;
+  unsigned long long deferred;  // statistics: pairs queued for the double-float tier
+  unsigned long long exact;     // pairs that also needed the binary64 replay
 };
 
 // One species pair (a,b) of one frame and one bin sweep, cut into kTile x kTile
@@ -97,13 +106,14 @@ cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cud
 cudaError_t launch_frame_setup(FrameDev* frames, int n_frames, int pass_hi_max, cudaStream_t stream);
 cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* status,
                               cudaStream_t stream);
-cudaError_t launch_pairs(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream);
+// One pair-kernel launch over segments whose frames all have minimum-image variant `variant`.
+cudaError_t launch_pairs(const PairLaunch& p, int variant, int grid, size_t smem, cudaStream_t stream);
 cudaError_t launch_check_sqrt(unsigned long long* out, cudaStream_t stream);
 cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t seed, unsigned long long* out,
                                 cudaStream_t stream);
 size_t pair_kernel_smem(int hist_width);
 int pair_kernel_max_width();
-int pair_kernel_blocks_per_sm(int hist_width);
+int pair_kernel_blocks_per_sm(int variant, int hist_width);
 
 // Host/device shared definition of the binary64 bin of Alg. 1 (used to build thresholds).
 int64_t host_bin_of(double r2, double r_max, int32_t nbins);

@@ -115,11 +115,17 @@ int build_thresholds_host(double r_max, int32_t nbins, double* T) {
   return ok;
 }
 
+// T[k] for k = 0..nbins, followed by the same values as float pairs (hi, lo)
+// at (float2*)(T + nbins + 1) for the double-float tier.
 __global__ void thresholds_kernel(double r_max, int32_t nbins, double* T, int32_t* status) {
   int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > nbins) return;
   int ok = 1;
-  T[k] = threshold_of(k, r_max, nbins, &ok);
+  double t = threshold_of(k, r_max, nbins, &ok);
+  T[k] = t;
+  float hi = __double2float_rn(t);
+  float lo = __double2float_rn(t - (double)hi);
+  reinterpret_cast<float2*>(T + nbins + 1)[k] = make_float2(hi, lo);
   if (!ok) atomicExch(status, 7);
 }
 
@@ -173,23 +179,29 @@ __global__ void stage_kernel(const StageJob* __restrict__ jobs, int n_jobs) {
 
 // ------------------------------------------------------------------ per-frame error window
 
-// Derives the float32 decision window delta (bin units) for one frame from its
-// box, r_max, nbins and the coordinate ranges found by stage_kernel.  Every
-// float32 operation of the fast path rounds to nearest (relative error <= u =
-// 2^-24), except sqrt.approx (kSqrtRelErr).  Bounds, with S = nbins/r_max and
-// R_c the coordinate range on axis c:
-//   relative part  alpha*t: d or d' rounding (u), r^2 = fma(dz,dz,fma(dy,dy,dx*dx))
-//                  (3u on r^2 -> 1.5u on r), sqrt, float32 S (eps_S), t = r*S (u);
-//   absolute part  beta = S*|a|: a_c collects the rounding of xj - xi (u R_c), of
-//                  every intermediate of the wrap (u |intermediate|) and of the
-//                  float32 box entries (|k| |B32 - B|);
-//   orthorhombic ties: where float32 and binary64 choose different nearest
-//                  images (d/L within ~2u R/L of a half integer) both vectors
-//                  have |d'_c| within 2u R_c of L_c/2; this adds S*4u|R| near t
-//                  = S L_min/2 and is added whenever that point is in range.
-// delta = alpha*(nbins+1) + beta (+ tie term) + 2^-20, times 1.01.  If a
-// precondition of the float32 path fails (wrap range, triclinic margin) or
-// delta >= 0.25, every pair of the frame is decided in binary64.
+// Derives, for one frame, the bound of the float32 decision and of the
+// double-float tier from its box, r_max, nbins and the coordinate ranges found
+// by stage_kernel.  Every float32 operation rounds to nearest (relative error
+// <= u = 2^-24); S = nbins/r_max, t = S r, q = t^2, R_c = coordinate range.
+//  t-space bound |t' - t| <= alpha*t + beta for t' = sqrt(q32) (the exact root
+//  of the computed q):
+//   alpha: rounding of d (none) or of the final wrapped d' (u), the
+//          r^2 = fma(dz,dz,fma(dy,dy,dx*dx)) chain (3u on r^2 -> 1.5u),
+//          float32 S^2 and the product q = r^2 S^2 ((eps_S2 + u)/2);
+//   beta:  S*|a|, a_c the absolute error of d'_c: rounding of xj - xi (u R_c),
+//          of each wrap intermediate (u |intermediate|) and the float32 box
+//          entries (|k| |B32 - B|); for orthorhombic boxes, where float32 and
+//          binary64 may round d/L to different images near a half integer
+//          (both then have |d'_c| within 2u R_c of L_c/2), a further S*4u|R|
+//          when t can reach S L_min/2 inside the histogram.
+//  q-space test: with n the integer nearest to sqrt(q32), floor(t) is decided
+//  when |q32 - n^2| > (alpha t' + beta)(2 t' + 1) = 2 alpha q + (alpha + 2 beta) t' + beta,
+//  with t' <= s (1 + 2^-18) for s = sqrt.approx(q32).
+//  double-float tier: |r2_df - r2_64| <= 2^-38 r2 + 2 r |a_mid| with |a_mid|
+//  from 2^-40 times the wrap magnitudes (binary64 oracle rounding and the
+//  float pair arithmetic, both far below it).
+// If a precondition of the float32 path fails (nearest-integer range,
+// triclinic margin) or the t-space bound reaches 1/4, every pair is deferred.
 __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= n_frames) return;
@@ -203,30 +215,32 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     }
   }
   double S = (double)F.nbins / F.r_max;
-  double alpha = 4.5 * u + kSqrtRelErr + F.eps_S;
+  double alpha = 3.0 * u + 0.5 * F.eps_S2;
   double a[3] = {0, 0, 0};
-  double tie = 0.0;
+  double I[3] = {R[0], R[1], R[2]};  // magnitudes of the wrap intermediates (for the double-float tier)
+  double tie = 0.0, tie_eps = 0.0;
   int all_defer = 0;
   float eps_s = 0.0f;
   const double* B = F.B;
   double dB[9];
   for (int q = 0; q < 9; ++q) dB[q] = fabs((double)F.Bf[q] - B[q]);
-  if (F.variant == V_NONE) {
-    alpha += u;  // xj - xi rounding is relative to |d| when nothing is wrapped
-  } else if (F.variant == V_ORTHO) {
-    double Lmin = INFINITY, Rn2 = 0;
+  if (F.variant == V_ORTHO) {
+    double Lmin = INFINITY, Rn2 = 0, Rmax = 0;
     for (int c = 0; c < 3; ++c) {
       double L = B[4 * c];
       double K = floor(R[c] / L + 0.5) + 1.0;
       a[c] = u * R[c] + K * dB[4 * c];
-      if (R[c] / L > 1048576.0) all_defer = 1;  // nint via the 2^23 trick needs |d/L| < 2^22
+      I[c] = R[c] + K * L;
+      if (R[c] / L > 1048576.0) all_defer = 1;  // nearest integer via the 1.5*2^23 trick needs |d/L| < 2^22
       Lmin = fmin(Lmin, L);
       Rn2 += R[c] * R[c];
+      Rmax = fmax(Rmax, R[c]);
     }
     double t_tie = S * Lmin * 0.5 * (1.0 - 8.0 * u * sqrt(Rn2) / Lmin) - 1.0;
     if (t_tie <= (double)F.nbins + 1.0) tie = S * 4.0 * u * sqrt(Rn2) * 1.01;
+    tie_eps = 8.0 * u * Rmax + 1e-12 * Lmin;
   } else if (F.variant == V_TRIC) {
-    // sequential wrap along c, then b, then a (Eq. 5 for r below h_min/2)
+    // sequential wrap along c, then b, then a (Eq. 5 below half the plane spacing)
     double ax = B[0], bx = B[1], cx = B[2], by = B[4], cy = B[5], cz = B[8];
     double Kz = floor(R[2] / cz + 0.5) + 1.0;
     double D1x = R[0] + Kz * fabs(cx), D1y = R[1] + Kz * fabs(cy);
@@ -236,6 +250,9 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     a[0] = u * (R[0] + D1x + D2x) + Kz * dB[2] + Ky * dB[1] + Kx * dB[0];
     a[1] = u * (R[1] + D1y) + Kz * dB[5] + Ky * dB[4];
     a[2] = u * R[2] + Kz * dB[8];
+    I[0] = D2x + Kx * ax;
+    I[1] = D1y + Ky * by;
+    I[2] = R[2] + Kz * cz;
     // the three nearest-integer decisions must be exact for every pair closer
     // than r_max: their float32 errors must stay below a quarter of the margin
     double ez = (2.0 * u * R[2] + R[2] * fabs((double)F.invf[2] * cz - 1.0)) / cz;
@@ -245,7 +262,7 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     if (!(emax < 0.25 * (double)F.margin) || D2x / ax > 1048576.0 || D1y / by > 1048576.0 ||
         R[2] / cz > 1048576.0)
       all_defer = 1;
-  } else {  // V_TRIC_SEARCH
+  } else if (F.variant == V_TRIC_SEARCH) {
     double ax = B[0], bx = B[1], cx = B[2], by = B[4], cy = B[5], cz = B[8];
     double Sz = R[2] / cz + 1.0;
     double Sy = (R[1] + fabs(cy) * Sz) / by + 1.0;
@@ -262,17 +279,212 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     a[0] = u * (R[0] + 7.0 * Ix) + (Kx + 1) * dB[0] + (Ky + 1) * dB[1] + (Kz + 1) * dB[2];
     a[1] = u * (R[1] + 6.0 * Iy) + (Ky + 1) * dB[4] + (Kz + 1) * dB[5];
     a[2] = u * (R[2] + 3.0 * Iz) + (Kz + 1) * dB[8];
+    I[0] = Ix; I[1] = Iy; I[2] = Iz;
     if (Sx > 1048576.0 || Sy > 1048576.0 || Sz > 1048576.0 || eps_s > 0.05f) all_defer = 1;
   }
-  double beta = S * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * (1.0 + 64.0 * u);
-  double delta = (alpha * ((double)F.nbins + 1.0) + beta + tie + 1.0 / 1048576.0) * 1.01;
+  double beta = S * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * (1.0 + 64.0 * u) + tie + 1.0 / 1048576.0;
+  alpha = alpha * (1.0 + 1.0 / 1024.0) + 1e-12;
+  double delta = alpha * ((double)F.nbins + 1.0) + beta;
   if (!(delta < 0.25)) all_defer = 1;
-  F.delta = (float)fmin(delta, 0.25);
+  const double slack = 1.0 + 1.0 / 1024.0;
+  if (all_defer) {
+    F.qc2 = F.qc1 = F.qc0 = 1e30f;
+  } else {
+    F.qc2 = (float)(2.0 * alpha * slack);
+    F.qc1 = (float)((alpha + 2.0 * beta) * (1.0 + 1.0 / 262144.0) * slack);
+    F.qc0 = (float)(beta * slack);
+  }
+  double Imax = fmax(I[0], fmax(I[1], I[2]));
+  double amid = 1.7320508075688772 * (R[0] + R[1] + R[2] + 4.0 * Imax) / 1099511627776.0;  // 2^-40
+  F.mid2 = (float)(1.0 / 274877906944.0);                                                   // 2^-38
+  F.mid1 = (float)(2.0 * amid / S * 1.01);
+  F.tie_eps = (float)tie_eps;
+  F.delta = (float)fmin(delta, 1.0);
+  F.alpha_t = (float)alpha;
+  F.beta_t = (float)beta;
   F.eps_s = eps_s;
   F.all_defer = all_defer;
 }
 
-// ------------------------------------------------------------------ binary64 replay
+// ------------------------------------------------------------------ A2-A8: pair kernel
+
+constexpr int kJU = 4;  // j particles per deferral-mask group (mask bit = u * kRegI + r)
+
+struct FastParams {
+  float S2;
+  float qc2, qc1, qc0;  // near-edge bound in q = t^2 space
+  int32_t kbase;        // bits(kMagicRound) + lo
+  uint32_t width;       // hi - lo
+  int32_t lo;
+  float b[9];
+  float inv[3];
+  float amb_thr;        // search variant: 0.5 - eps_s
+};
+
+struct ItemDesc {
+  FrameDev* fd;
+  int32_t valid;   // 0: no more work
+  int32_t h;
+  int32_t pass;
+  int32_t i0, ni, j0, nj;
+  int32_t masked;
+  int32_t skip;    // frame has no bins in this pass
+};
+
+// float32 |d'|^2 after the minimum image of the variant (NaN in, NaN out).
+template <int V>
+__device__ __forceinline__ float wrap_r2(float dx, float dy, float dz, const FastParams& P, bool& amb) {
+  if (V == V_ORTHO) {
+    dx = __fmaf_rn(-nint_scaled(dx, P.inv[0]), P.b[0], dx);
+    dy = __fmaf_rn(-nint_scaled(dy, P.inv[1]), P.b[4], dy);
+    dz = __fmaf_rn(-nint_scaled(dz, P.inv[2]), P.b[8], dz);
+  } else if (V == V_TRIC) {
+    // sequential wrap along c, b, a: the unique image inside the box-aligned brick
+    float kz = nint_scaled(dz, P.inv[2]);
+    dx = __fmaf_rn(-kz, P.b[2], dx);
+    dy = __fmaf_rn(-kz, P.b[5], dy);
+    dz = __fmaf_rn(-kz, P.b[8], dz);
+    float ky = nint_scaled(dy, P.inv[1]);
+    dx = __fmaf_rn(-ky, P.b[1], dx);
+    dy = __fmaf_rn(-ky, P.b[4], dy);
+    float kx = nint_scaled(dx, P.inv[0]);
+    dx = __fmaf_rn(-kx, P.b[0], dx);
+  } else if (V == V_TRIC_SEARCH) {
+    // Eq. 5 wrap via back substitution, then the 27 neighbouring shifts
+    float sz = __fmul_rn(dz, P.inv[2]);
+    float sy = __fmul_rn(__fmaf_rn(-P.b[5], sz, dy), P.inv[1]);
+    float sx = __fmul_rn(__fmaf_rn(-P.b[2], sz, __fmaf_rn(-P.b[1], sy, dx)), P.inv[0]);
+    float kx = nint_f(sx), ky = nint_f(sy), kz = nint_f(sz);
+    amb = (fabsf(__fsub_rn(sx, kx)) > P.amb_thr) || (fabsf(__fsub_rn(sy, ky)) > P.amb_thr) ||
+          (fabsf(__fsub_rn(sz, kz)) > P.amb_thr);
+    dx = __fmaf_rn(-kz, P.b[2], __fmaf_rn(-ky, P.b[1], __fmaf_rn(-kx, P.b[0], dx)));
+    dy = __fmaf_rn(-kz, P.b[5], __fmaf_rn(-ky, P.b[4], dy));
+    dz = __fmaf_rn(-kz, P.b[8], dz);
+    float best = INFINITY;
+#pragma unroll
+    for (int mx = -1; mx <= 1; ++mx) {
+      float ex1 = __fmaf_rn((float)mx, P.b[0], dx);
+#pragma unroll
+      for (int my = -1; my <= 1; ++my) {
+        float ex2 = __fmaf_rn((float)my, P.b[1], ex1);
+        float ey2 = __fmaf_rn((float)my, P.b[4], dy);
+#pragma unroll
+        for (int mz = -1; mz <= 1; ++mz) {
+          float ex = __fmaf_rn((float)mz, P.b[2], ex2);
+          float ey = __fmaf_rn((float)mz, P.b[5], ey2);
+          float ez = __fmaf_rn((float)mz, P.b[8], dz);
+          best = min_nan(best, __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex))));
+        }
+      }
+    }
+    return best;
+  }
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// The float32 decision of one pair.  With q = r^2 * S^2 (= t^2) and n the
+// integer nearest to sqrt(q), the residual e = q - n^2 is rounded once (fma),
+// so its sign gives floor(t) = n or n-1 and |e| is compared with the bound
+// derived in frame_setup_kernel; within it the pair is deferred.
+// rel = floor(t) - lo (valid when !nearedge).  NaN pairs are never deferred
+// and never counted.
+template <int V>
+__device__ __forceinline__ void fast_decide(float dx, float dy, float dz, const FastParams& P, bool& nearedge,
+                                            uint32_t& rel, float& q_out) {
+  bool amb = false;
+  float r2 = wrap_r2<V>(dx, dy, dz, P, amb);
+  float q = __fmul_rn(r2, P.S2);
+  float s = sqrt_approx(q);
+  float sm = __fadd_rn(s, kMagicRound);
+  float n = __fsub_rn(sm, kMagicRound);
+  float e = __fmaf_rn(-n, n, q);
+  float bound = __fmaf_rn(P.qc2, q, __fmaf_rn(P.qc1, s, P.qc0));
+  nearedge = fabsf(e) <= bound;
+  if (V == V_TRIC_SEARCH) nearedge = nearedge || amb;
+  int k = __float_as_int(sm) - P.kbase;
+  if (e < 0.0f) k -= 1;
+  rel = (uint32_t)k;
+  q_out = q;
+}
+
+// ---- double-float middle tier
+
+struct DF {
+  float h, l;  // unevaluated sum h + l
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+// v - k (bh + bl) for a small integer k
+__device__ __forceinline__ DF df_sub_kb(DF v, float k, float bh, float bl) {
+  DF p = two_prod(k, bh);
+  DF s = two_sum(v.h, -p.h);
+  float low = __fmaf_rn(-k, bl, __fsub_rn(__fadd_rn(v.l, s.l), p.l));
+  return {s.h, low};
+}
+__device__ __forceinline__ DF df_norm2(DF x, DF y, DF z) {
+  DF ax = two_prod(x.h, x.h), ay = two_prod(y.h, y.h), az = two_prod(z.h, z.h);
+  DF s1 = two_sum(ax.h, ay.h);
+  DF s2 = two_sum(s1.h, az.h);
+  float low = __fadd_rn(__fadd_rn(__fadd_rn(ax.l, ay.l), __fadd_rn(az.l, s1.l)), s2.l);
+  low = __fmaf_rn(__fadd_rn(x.h, x.h), x.l, low);
+  low = __fmaf_rn(__fadd_rn(y.h, y.h), y.l, low);
+  low = __fmaf_rn(__fadd_rn(z.h, z.h), z.l, low);
+  low = __fmaf_rn(x.l, x.l, __fmaf_rn(y.l, y.l, __fmaf_rn(z.l, z.l, low)));
+  return {s2.h, low};
+}
+
+// Bin of a deferred pair from r^2 evaluated in double-float arithmetic (about
+// 44 bits, with the exact coordinate differences and the same nearest images
+// as the float32 path), compared with the split binary64 threshold of the
+// nearest edge.  Returns -1 when even this is too close to call.
+template <int V>
+__device__ int mid_bin(const FrameDev& F, float4 pi, float4 pj) {
+  if (V == V_TRIC_SEARCH) return -1;
+  DF dx = two_sum(pj.x, -pi.x), dy = two_sum(pj.y, -pi.y), dz = two_sum(pj.z, -pi.z);
+  if (V == V_ORTHO) {
+    float kx = nint_scaled(dx.h, F.invf[0]), ky = nint_scaled(dy.h, F.invf[1]), kz = nint_scaled(dz.h, F.invf[2]);
+    dx = df_sub_kb(dx, kx, F.Bf[0], F.Bl[0]);
+    dy = df_sub_kb(dy, ky, F.Bf[4], F.Bl[4]);
+    dz = df_sub_kb(dz, kz, F.Bf[8], F.Bl[8]);
+    // float32 and binary64 may pick different images near |d'_c| = L_c/2
+    if (fabsf(fabsf(dx.h) - 0.5f * F.Bf[0]) <= F.tie_eps || fabsf(fabsf(dy.h) - 0.5f * F.Bf[4]) <= F.tie_eps ||
+        fabsf(fabsf(dz.h) - 0.5f * F.Bf[8]) <= F.tie_eps)
+      return -1;
+  } else if (V == V_TRIC) {
+    // the nearest-image integers of the float32 path, replayed exactly
+    float kz = nint_scaled(dz.h, F.invf[2]);
+    float fx1 = __fmaf_rn(-kz, F.Bf[2], dx.h);
+    float fy1 = __fmaf_rn(-kz, F.Bf[5], dy.h);
+    float ky = nint_scaled(fy1, F.invf[1]);
+    float fx2 = __fmaf_rn(-ky, F.Bf[1], fx1);
+    float kx = nint_scaled(fx2, F.invf[0]);
+    dx = df_sub_kb(df_sub_kb(df_sub_kb(dx, kz, F.Bf[2], F.Bl[2]), ky, F.Bf[1], F.Bl[1]), kx, F.Bf[0], F.Bl[0]);
+    dy = df_sub_kb(df_sub_kb(dy, kz, F.Bf[5], F.Bl[5]), ky, F.Bf[4], F.Bl[4]);
+    dz = df_sub_kb(dz, kz, F.Bf[8], F.Bl[8]);
+  }
+  DF r2 = df_norm2(dx, dy, dz);
+  float s = sqrt_approx(__fmul_rn(r2.h, F.S2));
+  float n = nint_f(s);
+  if (!(n >= 0.5f)) return 0;  // t below 1/2: bin 0
+  if (n > (float)F.nbins) return F.nbins;
+  int ni = (int)n;
+  float2 T = __ldg(F.Tf + ni);
+  float diff = __fadd_rn(__fsub_rn(r2.h, T.x), __fsub_rn(r2.l, T.y));
+  float bound = __fmaf_rn(F.mid2, r2.h, __fmul_rn(F.mid1, s));
+  if (!(fabsf(diff) > bound)) return -1;
+  return diff >= 0.0f ? ni : ni - 1;
+}
+
+// ---- binary64 last resort
 
 // Squared minimum-image distance in binary64, the same operations in the same
 // order as the definition (Alg. 1, Eq. 5, 27 neighbouring shifts).
@@ -327,128 +539,43 @@ __device__ __forceinline__ int bin_from_thresholds(const double* __restrict__ T,
   return lo;
 }
 
-// ------------------------------------------------------------------ A2-A8: pair kernel
-
-struct FastParams {
-  float S;
-  float thr;      // 0.5 - delta, or -1 when every pair is decided exactly
-  float tclamp;   // hi + 0.5
-  int32_t kbase;  // bits(2^23) + lo
-  uint32_t width; // hi - lo
-  int32_t lo;
-  float b[9];
-  float inv[3];
-  float amb_thr;  // search variant: 0.5 - eps_s
-};
-
-struct ItemDesc {
-  FrameDev* fd;
-  int32_t valid;   // 0: no more work
-  int32_t h;
-  int32_t pass;
-  int32_t i0, ni, j0, nj;
-  int32_t masked;
-  int32_t skip;    // frame has no bins in this pass
-};
-
-// float32 bin coordinate t = S * |d'| of one pair (NaN in, NaN out).
+// Exact bin of one deferred pair: double-float tier, then binary64 replay.
 template <int V>
-__device__ __forceinline__ float pair_t(float dx, float dy, float dz, const FastParams& P, bool& amb) {
-  if (V == V_ORTHO) {
-    dx = __fmaf_rn(-nint_scaled(dx, P.inv[0]), P.b[0], dx);
-    dy = __fmaf_rn(-nint_scaled(dy, P.inv[1]), P.b[4], dy);
-    dz = __fmaf_rn(-nint_scaled(dz, P.inv[2]), P.b[8], dz);
-  } else if (V == V_TRIC) {
-    float kz = nint_scaled(dz, P.inv[2]);
-    dx = __fmaf_rn(-kz, P.b[2], dx);
-    dy = __fmaf_rn(-kz, P.b[5], dy);
-    dz = __fmaf_rn(-kz, P.b[8], dz);
-    float ky = nint_scaled(dy, P.inv[1]);
-    dx = __fmaf_rn(-ky, P.b[1], dx);
-    dy = __fmaf_rn(-ky, P.b[4], dy);
-    float kx = nint_scaled(dx, P.inv[0]);
-    dx = __fmaf_rn(-kx, P.b[0], dx);
-  } else if (V == V_TRIC_SEARCH) {
-    float sz = __fmul_rn(dz, P.inv[2]);
-    float sy = __fmul_rn(__fmaf_rn(-P.b[5], sz, dy), P.inv[1]);
-    float sx = __fmul_rn(__fmaf_rn(-P.b[2], sz, __fmaf_rn(-P.b[1], sy, dx)), P.inv[0]);
-    float kx = nint_f(sx), ky = nint_f(sy), kz = nint_f(sz);
-    amb = (fabsf(__fsub_rn(sx, kx)) > P.amb_thr) || (fabsf(__fsub_rn(sy, ky)) > P.amb_thr) ||
-          (fabsf(__fsub_rn(sz, kz)) > P.amb_thr);
-    dx = __fmaf_rn(-kz, P.b[2], __fmaf_rn(-ky, P.b[1], __fmaf_rn(-kx, P.b[0], dx)));
-    dy = __fmaf_rn(-kz, P.b[5], __fmaf_rn(-ky, P.b[4], dy));
-    dz = __fmaf_rn(-kz, P.b[8], dz);
-    float best = INFINITY;
-#pragma unroll
-    for (int mx = -1; mx <= 1; ++mx) {
-      float ex1 = __fmaf_rn((float)mx, P.b[0], dx);
-#pragma unroll
-      for (int my = -1; my <= 1; ++my) {
-        float ex2 = __fmaf_rn((float)my, P.b[1], ex1);
-        float ey2 = __fmaf_rn((float)my, P.b[4], dy);
-#pragma unroll
-        for (int mz = -1; mz <= 1; ++mz) {
-          float ex = __fmaf_rn((float)mz, P.b[2], ex2);
-          float ey = __fmaf_rn((float)mz, P.b[5], ey2);
-          float ez = __fmaf_rn((float)mz, P.b[8], dz);
-          best = min_nan(best, __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex))));
-        }
-      }
-    }
-    return __fmul_rn(sqrt_approx(best), P.S);
+__device__ __forceinline__ int deferred_bin(const FrameDev& F, float4 pi, float4 pj, unsigned& nexact) {
+  int k = mid_bin<V>(F, pi, pj);
+  if (k < 0) {
+    k = bin_from_thresholds(F.T, F.nbins, exact_r2<V>(F, pi, pj));
+    ++nexact;
   }
-  float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-  return __fmul_rn(sqrt_approx(r2), P.S);
+  return k;
 }
 
-// Re-decide up to `count` queued pairs (one per lane) in binary64.
+// Decide the first `count` (<= 32) queued pairs, one per lane, and shift the
+// rest of the queue down.  Out of line so the hot loop keeps its registers.
 template <int V>
-__device__ void drain_queue(const FrameDev& F, const FastParams& P, const uint2* q, int count,
-                            uint32_t* sh, int lane) {
+__device__ __noinline__ int drain_queue(const FrameDev* F, int lo, uint32_t width, uint2* q, int qcount,
+                                        uint32_t* sh, int lane) {
+  const int count = qcount < 32 ? qcount : 32;
+  unsigned nexact = 0;
   if (lane < count) {
     uint2 e = q[lane];
-    float4 pi = __ldg(F.X + e.x);
-    float4 pj = __ldg(F.X + e.y);
-    double r2 = exact_r2<V>(F, pi, pj);
-    int k = bin_from_thresholds(F.T, F.nbins, r2);
-    uint32_t rel = (uint32_t)(k - P.lo);
-    if (rel < P.width) atomicAdd(sh + rel, 1u);
+    float4 pi = __ldg(F->X + e.x);
+    float4 pj = __ldg(F->X + e.y);
+    int k = deferred_bin<V>(*F, pi, pj, nexact);
+    uint32_t rel = (uint32_t)(k - lo);
+    if (rel < width) atomicAdd(sh + rel, 1u);
   }
-}
-
-// Append this thread's deferred pairs (bits of dmask: register slot r pairs
-// particle ibase + r*kBlock with particle jg) to the warp queue; whenever 32 are
-// queued they are decided at once by the whole warp.
-template <int V>
-__device__ __noinline__ void defer_pairs(uint32_t dmask, int ibase, int jg, uint2* q, int& qcount,
-                                         const FrameDev& F, const FastParams& P, uint32_t* sh,
-                                         int lane, unsigned& ndeferred) {
-  for (;;) {
-    bool has = dmask != 0u;
-    unsigned bal = __ballot_sync(kFull, has);
-    if (bal == 0u) break;
-    if (has) {
-      int r = __ffs(dmask) - 1;
-      dmask &= dmask - 1u;
-      int pos = qcount + __popc(bal & ((1u << lane) - 1u));
-      q[pos] = make_uint2((unsigned)(ibase + r * kBlock), (unsigned)jg);
-    }
-    qcount += __popc(bal);
-    ndeferred += __popc(bal);
-    __syncwarp();
-    if (qcount >= 32) {
-      drain_queue<V>(F, P, q, 32, sh, lane);
-      __syncwarp();
-      int rest = qcount - 32;
-      if (lane < rest) q[lane] = q[32 + lane];
-      __syncwarp();
-      qcount = rest;
-    }
-  }
+  __syncwarp();
+  int rest = qcount - count;
+  if (lane < rest) q[lane] = q[32 + lane];
+  __syncwarp();
+  for (int o = 16; o > 0; o >>= 1) nexact += __shfl_xor_sync(kFull, nexact, o);
+  if (lane == 0 && nexact) atomicAdd(&const_cast<FrameDev*>(F)->exact, (unsigned long long)nexact);
+  return rest;
 }
 
 template <int V, bool MASKED>
-__device__ __forceinline__ void run_tile(const FrameDev& F, const FastParams& P, const ItemDesc& it,
+__device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
                                          const float4* __restrict__ sj, uint32_t* sh, uint2* q,
                                          int tid, int lane, unsigned& ndeferred) {
   float xi[kRegI], yi[kRegI], zi[kRegI];
@@ -457,51 +584,71 @@ __device__ __forceinline__ void run_tile(const FrameDev& F, const FastParams& P,
   for (int r = 0; r < kRegI; ++r) {
     int li = tid + r * kBlock;
     if (li < it.ni) {
-      float4 p = __ldg(F.X + ibase + r * kBlock);
+      float4 p = __ldg(F->X + ibase + r * kBlock);
       xi[r] = p.x; yi[r] = p.y; zi[r] = p.z;
     } else {
       xi[r] = __int_as_float(0x7fffffff); yi[r] = xi[r]; zi[r] = xi[r];
     }
   }
-  int qcount = 0;
+  const unsigned lt_mask = (1u << lane) - 1u;
   const float qnan = __int_as_float(0x7fffffff);
-  for (int jj = 0; jj < it.nj; ++jj) {
-    const float4 pj = sj[jj];
-    const int jg = it.j0 + jj;
+  const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);  // the j tile is padded with NaN particles
+  int qcount = 0;
+  for (int jj0 = 0; jj0 < nj4; jj0 += kJU) {
     uint32_t dmask = 0u;
 #pragma unroll
-    for (int r = 0; r < kRegI; ++r) {
-      float dx = __fsub_rn(pj.x, xi[r]);
-      float dy = __fsub_rn(pj.y, yi[r]);
-      float dz = __fsub_rn(pj.z, zi[r]);
-      if (MASKED) {
-        // intra-species: only j > i; all three components so no later test sees a number
-        if (!(jg > ibase + r * kBlock)) { dx = qnan; dy = qnan; dz = qnan; }
+    for (int u = 0; u < kJU; ++u) {
+      const float4 pj = sj[jj0 + u];
+#pragma unroll
+      for (int r = 0; r < kRegI; ++r) {
+        float dx = __fsub_rn(pj.x, xi[r]);
+        float dy = __fsub_rn(pj.y, yi[r]);
+        float dz = __fsub_rn(pj.z, zi[r]);
+        if (MASKED) {
+          // intra-species: only j > i; all three components so no later test sees a number
+          if (!(it.j0 + jj0 + u > ibase + r * kBlock)) { dx = qnan; dy = qnan; dz = qnan; }
+        }
+        bool nearedge;
+        uint32_t rel;
+        float qv;
+        fast_decide<V>(dx, dy, dz, P, nearedge, rel, qv);
+        if (!nearedge && rel < P.width) atomicAdd(sh + rel, 1u);
+        if (nearedge) dmask |= 1u << (u * kRegI + r);
       }
-      bool amb = false;
-      float t = pair_t<V>(dx, dy, dz, P, amb);
-      t = min_nan(t, P.tclamp);
-      float fl = __fadd_rd(t, kMagicFloor);
-      float fr = __fsub_rn(t, __fsub_rn(fl, kMagicFloor));
-      bool nearedge = fabsf(__fsub_rn(fr, 0.5f)) > P.thr;
-      if (V == V_TRIC_SEARCH) nearedge = nearedge || amb;
-      uint32_t rel = (uint32_t)(__float_as_int(fl) - P.kbase);
-      if (!nearedge && rel < P.width) atomicAdd(sh + rel, 1u);
-      if (nearedge) dmask |= (1u << r);
     }
-    if (__any_sync(kFull, dmask != 0u)) {
-      defer_pairs<V>(dmask, ibase, jg, q, qcount, F, P, sh, lane, ndeferred);
+    // queue the deferred pairs: one per lane per round, compacted with a ballot
+    unsigned bal = __ballot_sync(kFull, dmask != 0u);
+    while (bal) {
+      if (dmask) {
+        int b = __ffs(dmask) - 1;
+        dmask &= dmask - 1u;
+        int pos = qcount + __popc(bal & lt_mask);
+        q[pos] = make_uint2((unsigned)(ibase + (b & (kRegI - 1)) * kBlock), (unsigned)(it.j0 + jj0 + b / kRegI));
+      }
+      int added = __popc(bal);
+      qcount += added;
+      ndeferred += added;
+      if (qcount >= 32) {
+        __syncwarp();
+        qcount = drain_queue<V>(F, P.lo, P.width, q, qcount, sh, lane);
+      }
+      bal = __ballot_sync(kFull, dmask != 0u);
     }
   }
-  // decide what is left in the queue
-  drain_queue<V>(F, P, q, qcount, sh, lane);
+  __syncwarp();
+  if (qcount > 0) drain_queue<V>(F, P.lo, P.width, q, qcount, sh, lane);
   __syncwarp();
 }
 
+__device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P);
+
+// The decision parameters are reloaded per item (from the L1-cached frame
+// descriptor) so that only the fields of this variant are live in the loop.
 template <int V>
-__device__ void run_item(const FrameDev& F, const FastParams& P, const ItemDesc& it,
-                         const float4* sj, uint32_t* sh, uint2* q, int tid, int lane,
-                         unsigned& ndeferred) {
+__device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj, uint32_t* sh, uint2* q,
+                         int tid, int lane, unsigned& ndeferred) {
+  FastParams P;
+  load_fast_params(*F, it.pass, P);
   if (it.masked) run_tile<V, true>(F, P, it, sj, sh, q, tid, lane, ndeferred);
   else run_tile<V, false>(F, P, it, sj, sh, q, tid, lane, ndeferred);
 }
@@ -556,7 +703,32 @@ __device__ void decode_item(const PairLaunch& L, long long item, ItemDesc& it) {
   it.skip = (lo_bin >= s.fd->nbins) ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(kBlock) pair_kernel(PairLaunch L) {
+__device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
+  int lo_bin = pass * F.sweep_width;
+  int hi_bin = min(F.nbins, lo_bin + F.sweep_width);
+  P.S2 = F.S2;
+  P.qc2 = F.qc2;
+  P.qc1 = F.qc1;
+  P.qc0 = F.qc0;
+  P.kbase = __float_as_int(kMagicRound) + lo_bin;
+  P.width = (uint32_t)(hi_bin - lo_bin);
+  P.lo = lo_bin;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) P.b[c] = F.Bf[c];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) P.inv[c] = F.invf[c];
+  P.amb_thr = 0.5f - F.eps_s;
+}
+
+// One instance per minimum-image variant V: every segment of the launch has a
+// frame of that variant.
+template <int V>
+constexpr int min_blocks_per_sm() {
+  return (V == V_NONE || V == V_ORTHO) ? 3 : 2;
+}
+
+template <int V>
+__global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(PairLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int width_pad = (L.hist_width + 3) & ~3;
   uint32_t* sh = reinterpret_cast<uint32_t*>(smem_raw);
@@ -571,7 +743,6 @@ __global__ void __launch_bounds__(kBlock) pair_kernel(PairLaunch L) {
   const FrameDev* cur_fd = nullptr;
   int cur_h = -1, cur_pass = -1;
   unsigned long long since = 0;  // pairs accumulated in sh since the last flush
-  FastParams P;
   uint64_t* cur_dst = nullptr;
   int cur_width = 0;
 
@@ -604,39 +775,26 @@ __global__ void __launch_bounds__(kBlock) pair_kernel(PairLaunch L) {
           flush_hist(sh, cur_width, cur_dst, tid);
           __syncthreads();
         }
-        if (it.fd != cur_fd || it.pass != cur_pass) {
-          int lo_bin = it.pass * F.sweep_width;
-          int hi_bin = min(F.nbins, lo_bin + F.sweep_width);
-          P.S = F.S;
-          P.thr = F.all_defer ? -1.0f : 0.5f - F.delta;
-          P.tclamp = (float)hi_bin + 0.5f;
-          P.kbase = __float_as_int(kMagicFloor) + lo_bin;
-          P.width = (uint32_t)(hi_bin - lo_bin);
-          P.lo = lo_bin;
-#pragma unroll
-          for (int c = 0; c < 9; ++c) P.b[c] = F.Bf[c];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) P.inv[c] = F.invf[c];
-          P.amb_thr = 0.5f - F.eps_s;
-        }
+        int lo_bin = it.pass * F.sweep_width;
         cur_fd = it.fd;
         cur_h = it.h;
         cur_pass = it.pass;
-        cur_width = (int)P.width;
-        cur_dst = F.out + (size_t)it.h * F.nbins + P.lo;
+        cur_width = min(F.nbins, lo_bin + F.sweep_width) - lo_bin;
+        cur_dst = F.out + (size_t)it.h * F.nbins + lo_bin;
         since = 0;
       }
       since += pairs;
-      // stage the j tile (float4 per particle)
-      for (int k = tid; k < it.nj; k += kBlock) sj[k] = __ldg(F.X + it.j0 + k);
+      // stage the j tile (float4 per particle), padded with NaN particles to a multiple of kJU
+      const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);
+      for (int k = tid; k < nj4; k += kBlock) {
+        float4 v;
+        if (k < it.nj) v = __ldg(F.X + it.j0 + k);
+        else v = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff), __int_as_float(0x7fffffff), 0.f);
+        sj[k] = v;
+      }
       __syncthreads();
       unsigned ndef = 0;
-      switch (F.variant) {
-        case V_NONE: run_item<V_NONE>(F, P, it, sj, sh, q, tid, lane, ndef); break;
-        case V_ORTHO: run_item<V_ORTHO>(F, P, it, sj, sh, q, tid, lane, ndef); break;
-        case V_TRIC: run_item<V_TRIC>(F, P, it, sj, sh, q, tid, lane, ndef); break;
-        default: run_item<V_TRIC_SEARCH>(F, P, it, sj, sh, q, tid, lane, ndef); break;
-      }
+      run_item<V>(it.fd, it, sj, sh, q, tid, lane, ndef);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();
@@ -674,46 +832,43 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// For sampled pairs of one frame: the float32 bin coordinate t32 of the fast
-// path against t64 = nbins*sqrt(r2_64)/r_max from the binary64 definition.
-// out[0]: max |t32 - t64| / delta over pairs with t64 < nbins + 1 (bits of a
-// double); out[1]: pairs the fast path would decide (not near an edge) whose
-// float32 bin differs from the binary64 bin -- must be 0; out[2]: pairs checked.
+// For sampled pairs of one frame, the decision rule against the binary64
+// definition: out[0] = max |sqrt(q32) - t64| / (alpha t64 + beta) over pairs
+// inside the histogram (bits of a double; the analysis says < 1); out[1] =
+// pairs whose float32 or double-float decision differs from the binary64 bin
+// (must be 0); out[2] = pairs compared.
 template <int V>
-__device__ void check_window_pair(const FrameDev& F, const FastParams& P, int i, int j,
-                                  double* worst, unsigned long long* viol, unsigned long long* checked) {
+__device__ void check_window_pair(const FrameDev& F, const FastParams& P, int i, int j, double* worst,
+                                  unsigned long long* viol, unsigned long long* checked) {
   float4 pi = F.X[i], pj = F.X[j];
-  bool amb = false;
-  float t = pair_t<V>(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z), P, amb);
+  bool nearedge;
+  uint32_t rel;
+  float q;
+  fast_decide<V>(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z), P, nearedge, rel, q);
   double r2 = exact_r2<V>(F, pi, pj);
-  double t64 = __ddiv_rn(__dmul_rn((double)F.nbins, __dsqrt_rn(r2)), F.r_max);
   int k64 = bin_from_thresholds(F.T, F.nbins, r2);
-  float tc = min_nan(t, P.tclamp);
-  float fl = __fadd_rd(tc, kMagicFloor);
-  float fr = __fsub_rn(tc, __fsub_rn(fl, kMagicFloor));
-  bool nearedge = fabsf(__fsub_rn(fr, 0.5f)) > P.thr || amb;
-  int k32 = __float_as_int(fl) - __float_as_int(kMagicFloor);
-  if (t64 < (double)F.nbins + 1.0 && !amb) {
-    *worst = fmax(*worst, fabs((double)t - t64) / (double)F.delta);
+  double t64 = __dmul_rn(__dsqrt_rn(r2), (double)F.nbins / F.r_max);
+  if (t64 < (double)F.nbins + 1.0 && isfinite(q)) {
+    double tq = __dsqrt_rn((double)q);
+    *worst = fmax(*worst, fabs(tq - t64) / ((double)F.alpha_t * t64 + (double)F.beta_t));
     ++*checked;
   }
-  int k32c = k32 < F.nbins ? k32 : F.nbins;
-  if (!nearedge && k32c != k64) ++*viol;
+  if (!nearedge) {
+    int k32 = (int)rel;  // lo = 0 here
+    if (rel > (uint32_t)F.nbins) k32 = F.nbins;
+    if (k32 != k64) ++*viol;
+  } else {
+    int km = mid_bin<V>(F, pi, pj);
+    if (km >= 0 && km != k64) ++*viol;
+  }
 }
 
 __global__ void check_window_kernel(const FrameDev* Fp, uint64_t n_samples, uint64_t seed,
                                     unsigned long long* out) {
   const FrameDev& F = *Fp;
   FastParams P;
-  P.S = F.S;
-  P.thr = F.all_defer ? -1.0f : 0.5f - F.delta;
-  P.tclamp = (float)F.nbins + 0.5f;
-  P.kbase = __float_as_int(kMagicFloor);
-  P.width = (uint32_t)F.nbins;
-  P.lo = 0;
-  for (int c = 0; c < 9; ++c) P.b[c] = F.Bf[c];
-  for (int c = 0; c < 3; ++c) P.inv[c] = F.invf[c];
-  P.amb_thr = 0.5f - F.eps_s;
+  load_fast_params(F, 0, P);
+  P.width = (uint32_t)F.nbins;  // decide over the whole histogram
   double worst = 0.0;
   unsigned long long viol = 0, checked = 0;
   if (F.n >= 2) {
@@ -771,12 +926,22 @@ int pair_kernel_max_width() {
   return (int)(((size_t)optin - fixed) / 4) & ~3;
 }
 
-int pair_kernel_blocks_per_sm(int hist_width) {
+template <int V>
+int blocks_per_sm_v(int hist_width) {
   size_t smem = pair_kernel_smem(hist_width);
-  cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(pair_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel, kBlock, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<V>, kBlock, smem);
   return nb;
+}
+
+int pair_kernel_blocks_per_sm(int variant, int hist_width) {
+  switch (variant) {
+    case V_NONE: return blocks_per_sm_v<V_NONE>(hist_width);
+    case V_ORTHO: return blocks_per_sm_v<V_ORTHO>(hist_width);
+    case V_TRIC: return blocks_per_sm_v<V_TRIC>(hist_width);
+    default: return blocks_per_sm_v<V_TRIC_SEARCH>(hist_width);
+  }
 }
 
 cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cudaStream_t stream) {
@@ -799,11 +964,21 @@ cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* s
   return cudaGetLastError();
 }
 
-cudaError_t launch_pairs(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int V>
+cudaError_t launch_pairs_v(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(pair_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  pair_kernel<<<grid, kBlock, smem, stream>>>(p);
+  pair_kernel<V><<<grid, kBlock, smem, stream>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(const PairLaunch& p, int variant, int grid, size_t smem, cudaStream_t stream) {
+  switch (variant) {
+    case V_NONE: return launch_pairs_v<V_NONE>(p, grid, smem, stream);
+    case V_ORTHO: return launch_pairs_v<V_ORTHO>(p, grid, smem, stream);
+    case V_TRIC: return launch_pairs_v<V_TRIC>(p, grid, smem, stream);
+    default: return launch_pairs_v<V_TRIC_SEARCH>(p, grid, smem, stream);
+  }
 }
 
 }  // namespace dh

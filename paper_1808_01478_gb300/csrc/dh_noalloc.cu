@@ -30,7 +30,7 @@ constexpr size_t kNaCtl = 256;                                  // Control
 constexpr size_t kNaFrame = 512;                                // FrameDev
 constexpr size_t kNaJob = 256;                                  // StageJob
 constexpr size_t kNaSegs = 16 * 1024;                           // Segment[] (256 of them)
-constexpr size_t kNaT = ((size_t)DH_NOALLOC_MAX_BINS + 1) * 8;  // thresholds
+constexpr size_t kNaT = ((size_t)DH_NOALLOC_MAX_BINS + 1) * 16; // thresholds + float-pair copy
 constexpr size_t kNaTPad = (kNaT + 255) & ~(size_t)255;
 constexpr size_t kNaX = (size_t)DH_NOALLOC_MAX_N * 16;          // float4 coordinates
 constexpr size_t kNaOffFrame = kNaCtl;
@@ -164,7 +164,7 @@ extern "C" dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream_pt
   if (chunks > 0) DH_CUDA_TRY(launch_stage(job, 1, chunks, st));
   DH_CUDA_TRY(launch_frame_setup(fd, 1, 0, st));
   if (n_items > 0) {
-    int bps = pair_kernel_blocks_per_sm(pf.sweep_width);
+    int bps = pair_kernel_blocks_per_sm(pf.variant, pf.sweep_width);
     if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", pf.sweep_width);
     PairLaunch L;
     std::memset(&L, 0, sizeof L);
@@ -173,7 +173,7 @@ extern "C" dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream_pt
     L.n_items = n_items;
     L.hist_width = pf.sweep_width;
     L.ctl = ctl;
-    DH_CUDA_TRY(launch_pairs(L, pair_grid(num_sms, bps, n_items), pair_kernel_smem(pf.sweep_width), st));
+    DH_CUDA_TRY(launch_pairs(L, pf.variant, pair_grid(num_sms, bps, n_items), pair_kernel_smem(pf.sweep_width), st));
   }
   // Read back the flags into stack memory and wait.
   int32_t status = 0, bad = 0;

@@ -121,7 +121,8 @@ dh_status ThresholdCache::acquire(double r_max, int32_t nbins, cudaStream_t st, 
     map_.erase(victim);
   }
   double* t = nullptr;
-  DH_CUDA_TRY(cudaMallocAsync((void**)&t, sizeof(double) * (size_t)(nbins + 1), st));
+  // binary64 thresholds followed by their float-pair copy
+  DH_CUDA_TRY(cudaMallocAsync((void**)&t, 2 * sizeof(double) * (size_t)(nbins + 1), st));
   DH_CUDA_TRY(launch_thresholds(r_max, nbins, t, status_dev, st));
   if (launched) ++*launched;
   map_[key] = Entry{t, 1, ++tick_};
@@ -220,6 +221,7 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   F.X = X;
   F.out = out;
   F.T = T;
+  F.Tf = reinterpret_cast<const float2*>(T + f->nbins + 1);
   F.variant = pf.variant;
   F.nbins = f->nbins;
   F.n = (int32_t)f->n;
@@ -228,6 +230,7 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   for (int q = 0; q < 9; ++q) {
     F.B[q] = (f->box_type == DH_BOX_NONE) ? 0.0 : f->box[q];
     F.Bf[q] = (float)F.B[q];
+    F.Bl[q] = (float)(F.B[q] - (double)F.Bf[q]);
   }
   if (pf.variant == V_ORTHO) {
     F.Linv[0] = 1.0 / F.B[0];
@@ -244,6 +247,8 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   double S = (double)f->nbins / f->r_max;
   F.S = (float)S;
   F.eps_S = std::fabs((double)F.S - S) / S;
+  F.S2 = (float)(S * S);
+  F.eps_S2 = std::fabs((double)F.S2 - S * S) / (S * S) + 1e-15;
   F.margin = (float)pf.margin;
   for (int c = 0; c < 3; ++c) {
     F.cmin[c] = 0x7FFFFFFF;                // ordered encoding of +huge: min starts high
@@ -296,7 +301,8 @@ void release_held(dh_ctx* c) {
 // Enqueue everything for k planned frames.  dev_out[f] is where frame f's
 // histograms are accumulated on the device (already zeroed or holding the
 // values to accumulate onto).  Launches: one staging kernel for all frames,
-// one setup kernel, threshold tables not yet cached, one pair kernel.
+// one setup kernel, threshold tables not yet cached, and one pair-kernel
+// launch per minimum-image variant present (segments are grouped by variant).
 dh_status enqueue_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const std::vector<uint64_t*>& dev_out,
                          bool host_coords, bool with_pairs = true) {
   cudaStream_t st = c->stream();
@@ -315,16 +321,28 @@ dh_status enqueue_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
   FrameDev* dF = (FrameDev*)c->meta.p;
   std::vector<Segment> segs;
   int64_t n_items = 0;
-  for (int f = 0; f < k; ++f) n_items += add_segments(pfs[f], dF + f, n_items, segs);
+  int64_t vitems[kNumVariants] = {0, 0, 0, 0};
+  size_t vseg0[kNumVariants + 1] = {0, 0, 0, 0, 0};
+  auto plan = [&]() {
+    segs.clear();
+    n_items = 0;
+    for (int v = 0; v < kNumVariants; ++v) {
+      vseg0[v] = segs.size();
+      vitems[v] = 0;
+      for (int f = 0; f < k; ++f)
+        if (pfs[f].variant == v) vitems[v] += add_segments(pfs[f], dF + f, vitems[v], segs);
+      n_items += vitems[v];
+    }
+    vseg0[kNumVariants] = segs.size();
+  };
+  plan();
   size_t meta_bytes = sizeof(FrameDev) * (size_t)k + sizeof(StageJob) * (size_t)k +
                       sizeof(Segment) * std::max<size_t>(segs.size(), 1);
   DH_CUDA_TRY(c->meta.ensure(meta_bytes));
   DH_CUDA_TRY(c->hmeta.ensure(meta_bytes));
   if ((FrameDev*)c->meta.p != dF) {  // buffer moved: segments must point into the new one
     dF = (FrameDev*)c->meta.p;
-    segs.clear();
-    n_items = 0;
-    for (int f = 0; f < k; ++f) n_items += add_segments(pfs[f], dF + f, n_items, segs);
+    plan();
   }
   FrameDev* hF = (FrameDev*)c->hmeta.p;
   StageJob* hJ = (StageJob*)(hF + k);
@@ -373,26 +391,32 @@ dh_status enqueue_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
   }
   DH_CUDA_TRY(launch_frame_setup(dF, k, 0, st));
   ++launched;
-  // A2-A8: one persistent launch over every frame, species pair and bin sweep
+  // A2-A8: per variant, one persistent launch over its frames, species pairs and bin sweeps
   int grid = 0;
   int max_pass = 1;
   for (auto& pf : pfs) max_pass = std::max(max_pass, pf.sweeps);
   if (n_items > 0 && with_pairs) {
-    int bps = pair_kernel_blocks_per_sm(hist_width);
-    if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", hist_width);
-    grid = pair_grid(c->num_sms, bps, n_items);
-    size_t smem = pair_kernel_smem(hist_width);
-    DH_CUDA_TRY(cudaMemsetAsync(c->ctl.p, 0, sizeof(Control), st));
+    DH_CUDA_TRY(cudaMemsetAsync(c->ctl.p, 0, sizeof(Control) * kNumVariants, st));
     if (c->ev_pair0) DH_CUDA_TRY(cudaEventRecord(c->ev_pair0, st));
-    PairLaunch L;
-    std::memset(&L, 0, sizeof L);
-    L.segs = dS;
-    L.n_segs = (int32_t)segs.size();
-    L.n_items = n_items;
-    L.hist_width = hist_width;
-    L.ctl = (Control*)c->ctl.p;
-    DH_CUDA_TRY(launch_pairs(L, grid, smem, st));
-    ++launched;
+    for (int v = 0; v < kNumVariants; ++v) {
+      if (vitems[v] == 0) continue;
+      int width = 1;
+      for (int f = 0; f < k; ++f)
+        if (pfs[f].variant == v) width = std::max(width, pfs[f].sweep_width);
+      int bps = pair_kernel_blocks_per_sm(v, width);
+      if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", width);
+      int g = pair_grid(c->num_sms, bps, vitems[v]);
+      grid = std::max(grid, g);
+      PairLaunch L;
+      std::memset(&L, 0, sizeof L);
+      L.segs = dS + vseg0[v];
+      L.n_segs = (int32_t)(vseg0[v + 1] - vseg0[v]);
+      L.n_items = vitems[v];
+      L.hist_width = width;
+      L.ctl = (Control*)c->ctl.p + v;
+      DH_CUDA_TRY(launch_pairs(L, v, g, pair_kernel_smem(width), st));
+      ++launched;
+    }
     if (c->ev_pair1) DH_CUDA_TRY(cudaEventRecord(c->ev_pair1, st));
   }
   c->timed = (c->ev_pair0 != nullptr) && n_items > 0 && with_pairs;
@@ -572,7 +596,7 @@ dh_status dh_create(const dh_config* config, dh_ctx** out) {
   DH_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   c->max_width = pair_kernel_max_width();
   if (c->max_width < 1024) return fail(DH_ERR_CUDA, "not enough shared memory per block");
-  DH_CUDA_TRY(c->ctl.ensure(sizeof(Control)));
+  DH_CUDA_TRY(c->ctl.ensure(sizeof(Control) * kNumVariants));
   DH_CUDA_TRY(c->tstat.ensure(64));
   if (c->cfg.flags & DH_CFG_TIMING) {
     DH_CUDA_TRY(cudaEventCreate(&c->ev_pair0));

@@ -201,7 +201,7 @@ dh_status Server::start() {
   DH_CUDA_TRY(cudaMemsetAsync(tstat_.p, 0, 64, stream_));
   max_inflight_ = ctx_->cfg.max_inflight > 0 ? ctx_->cfg.max_inflight : 64;
   for (auto& s : slots_) {
-    DH_CUDA_TRY(s.ctl.ensure(sizeof(Control)));
+    DH_CUDA_TRY(s.ctl.ensure(sizeof(Control) * kNumVariants));
     DH_CUDA_TRY(cudaEventCreate(&s.ev0));
     DH_CUDA_TRY(cudaEventCreate(&s.ev1));
   }
@@ -453,9 +453,10 @@ bool Server::launch_wave() {
   double budget = rate_ * kWaveSeconds;
   double share = budget / (double)run.size();
   const double pairs_per_item = (double)kTile * (double)kTile;
-  std::vector<Segment> wsegs;
-  int64_t witems = 0;
-  int hist_width = 1;
+  // wave segments grouped by minimum-image variant (one pair-kernel launch each)
+  std::vector<Segment> vsegs[kNumVariants];
+  int64_t vitems[kNumVariants] = {0, 0, 0, 0};
+  int vwidth[kNumVariants] = {1, 1, 1, 1};
   double wpairs = 0;
   std::vector<Request*> finishing;
   for (Request* r : run) {
@@ -467,6 +468,7 @@ bool Server::launch_wave() {
         continue;
       }
     }
+    int v = r->pf.variant;
     int64_t take = std::max<int64_t>(1, (int64_t)(share / pairs_per_item));
     take = std::min(take, r->n_items - r->next);
     int64_t lo = r->next, hi = r->next + take;
@@ -475,38 +477,49 @@ bool Server::launch_wave() {
       int64_t a = std::max(lo, s.item0), b = std::min(hi, s.item0 + count);
       if (a >= b) continue;
       Segment w = s;
-      w.item0 = witems;
+      w.item0 = vitems[v];
       w.item_base = a - s.item0;
-      witems += b - a;
-      wsegs.push_back(w);
+      vitems[v] += b - a;
+      vsegs[v].push_back(w);
     }
     r->next = hi;
     r->last_wave = wave_seq_ + 1;
-    hist_width = std::max(hist_width, r->pf.sweep_width);
+    vwidth[v] = std::max(vwidth[v], r->pf.sweep_width);
     wpairs += (double)std::min<uint64_t>(r->pf.pairs, (uint64_t)((double)take * pairs_per_item));
     if (r->next >= r->n_items) finishing.push_back(r);
   }
-  if (witems == 0) return false;
-  size_t bytes = sizeof(Segment) * wsegs.size();
+  size_t nseg = 0;
+  for (int v = 0; v < kNumVariants; ++v) nseg += vsegs[v].size();
+  if (nseg == 0) return false;
+  size_t bytes = sizeof(Segment) * nseg;
   if (W.segs.ensure(bytes) != cudaSuccess || W.hsegs.ensure(bytes) != cudaSuccess) {
     thread_error_ = "out of memory for wave descriptors";
     return false;
   }
-  std::memcpy(W.hsegs.p, wsegs.data(), bytes);
+  size_t at = 0;
+  size_t vat[kNumVariants];
+  for (int v = 0; v < kNumVariants; ++v) {
+    vat[v] = at;
+    if (!vsegs[v].empty()) std::memcpy((Segment*)W.hsegs.p + at, vsegs[v].data(), sizeof(Segment) * vsegs[v].size());
+    at += vsegs[v].size();
+  }
   cudaMemcpyAsync(W.segs.p, W.hsegs.p, bytes, cudaMemcpyHostToDevice, stream_);
-  cudaMemsetAsync(W.ctl.p, 0, sizeof(Control), stream_);
-  PairLaunch L;
-  std::memset(&L, 0, sizeof L);
-  L.segs = (const Segment*)W.segs.p;
-  L.n_segs = (int32_t)wsegs.size();
-  L.n_items = witems;
-  L.hist_width = hist_width;
-  L.ctl = (Control*)W.ctl.p;
-  int bps = pair_kernel_blocks_per_sm(hist_width);
+  cudaMemsetAsync(W.ctl.p, 0, sizeof(Control) * kNumVariants, stream_);
   cudaEventRecord(W.ev0, stream_);
-  cudaError_t e = launch_pairs(L, pair_grid(ctx_->num_sms, bps, witems), pair_kernel_smem(hist_width), stream_);
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (vitems[v] == 0) continue;
+    PairLaunch L;
+    std::memset(&L, 0, sizeof L);
+    L.segs = (const Segment*)W.segs.p + vat[v];
+    L.n_segs = (int32_t)vsegs[v].size();
+    L.n_items = vitems[v];
+    L.hist_width = vwidth[v];
+    L.ctl = (Control*)W.ctl.p + v;
+    int bps = pair_kernel_blocks_per_sm(v, vwidth[v]);
+    cudaError_t e = launch_pairs(L, v, pair_grid(ctx_->num_sms, bps, vitems[v]), pair_kernel_smem(vwidth[v]), stream_);
+    if (e != cudaSuccess) thread_error_ = cudaGetErrorString(e);
+  }
   cudaEventRecord(W.ev1, stream_);
-  if (e != cudaSuccess) thread_error_ = cudaGetErrorString(e);
   W.busy = true;
   W.seq = ++wave_seq_;
   W.pairs = wpairs;
