@@ -49,7 +49,7 @@ struct FrameDev {
   int32_t cmax[3];
   int32_t bad;       // a non-finite coordinate was seen
   int32_t all_defer; // float32 decisions are not safe for this frame: every pair is deferred
-  float qc2, qc1, qc0;  // near-edge test: |q - n^2| <= qc2*q + qc1*s + qc0 (q = t^2, s ~ t)
+  float qb1, qb0;    // near-edge test: |n^2 - q| <= qb1*q + qb0 (no box) or qb1*s + qb0 (q = t^2, s ~ t)
   float mid2, mid1;  // double-float tier: |r2 - T[n]| <= mid2*r2 + mid1*s decides nothing
   float tie_eps;     // orthorhombic: | |d'_c| - L_c/2 | <= tie_eps is re-decided in binary64
   float delta;       // float32 window half-width in bin units at t = nbins (reported)

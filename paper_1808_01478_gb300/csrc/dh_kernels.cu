@@ -200,6 +200,7 @@ __global__ void stage_kernel(const StageJob* __restrict__ jobs, int n_jobs) {
 //  double-float tier: |r2_df - r2_64| <= 2^-38 r2 + 2 r |a_mid| with |a_mid|
 //  from 2^-40 times the wrap magnitudes (binary64 oracle rounding and the
 //  float pair arithmetic, both far below it).
+// beta also carries 2^-28 for the binary64 rounding of t itself (< 2^-29 for t < 2^22).
 // If a precondition of the float32 path fails (nearest-integer range,
 // triclinic margin) or the t-space bound reaches 1/4, every pair is deferred.
 __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
@@ -282,17 +283,23 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     I[0] = Ix; I[1] = Iy; I[2] = Iz;
     if (Sx > 1048576.0 || Sy > 1048576.0 || Sz > 1048576.0 || eps_s > 0.05f) all_defer = 1;
   }
-  double beta = S * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * (1.0 + 64.0 * u) + tie + 1.0 / 1048576.0;
+  double beta = S * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * (1.0 + 64.0 * u) + tie + 1.0 / 268435456.0;
   alpha = alpha * (1.0 + 1.0 / 1024.0) + 1e-12;
   double delta = alpha * ((double)F.nbins + 1.0) + beta;
   if (!(delta < 0.25)) all_defer = 1;
   const double slack = 1.0 + 1.0 / 1024.0;
+  // One-FMA forms of the q-space bound 2 alpha q + (alpha + 2 beta) t' + beta:
+  //  no box: t' <= (q + 1)/2 gives (2.5 alpha + beta) q + (alpha/2 + 2 beta);
+  //  periodic: for t' <= nbins + 2 (pairs beyond are never counted whatever the
+  //  decision), 2 alpha q <= 2 alpha (nbins + 2) t' and t' <= s (1 + 2^-18).
   if (all_defer) {
-    F.qc2 = F.qc1 = F.qc0 = 1e30f;
+    F.qb1 = F.qb0 = 1e30f;
+  } else if (F.variant == V_NONE) {
+    F.qb1 = (float)((2.5 * alpha + beta) * slack);
+    F.qb0 = (float)((0.5 * alpha + 2.0 * beta) * slack);
   } else {
-    F.qc2 = (float)(2.0 * alpha * slack);
-    F.qc1 = (float)((alpha + 2.0 * beta) * (1.0 + 1.0 / 262144.0) * slack);
-    F.qc0 = (float)(beta * slack);
+    F.qb1 = (float)((2.0 * alpha * ((double)F.nbins + 2.0) + alpha + 2.0 * beta) * (1.0 + 1.0 / 262144.0) * slack);
+    F.qb0 = (float)(beta * slack);
   }
   double Imax = fmax(I[0], fmax(I[1], I[2]));
   double amid = 1.7320508075688772 * (R[0] + R[1] + R[2] + 4.0 * Imax) / 1099511627776.0;  // 2^-40
@@ -312,7 +319,7 @@ constexpr int kJU = 4;  // j particles per deferral-mask group (mask bit = u * k
 
 struct FastParams {
   float S2;
-  float qc2, qc1, qc0;  // near-edge bound in q = t^2 space
+  float qb1, qb0;       // near-edge bound |n^2 - q| <= qb1*(q or s) + qb0 (q for V_NONE, s otherwise)
   int32_t kbase;        // bits(kMagicRound) + lo
   uint32_t width;       // hi - lo
   int32_t lo;
@@ -382,29 +389,100 @@ __device__ __forceinline__ float wrap_r2(float dx, float dy, float dz, const Fas
   return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// The float32 decision of one pair.  With q = r^2 * S^2 (= t^2) and n the
-// integer nearest to sqrt(q), the residual e = q - n^2 is rounded once (fma),
-// so its sign gives floor(t) = n or n-1 and |e| is compared with the bound
-// derived in frame_setup_kernel; within it the pair is deferred.
-// rel = floor(t) - lo (valid when !nearedge).  NaN pairs are never deferred
-// and never counted.
+// ---- packed float32 arithmetic: two pairs per instruction (FFMA2/FADD2/FMUL2)
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// float32 |d'|^2 of two pairs after the minimum image of the variant; each
+// component is rounded exactly as the scalar sequence of wrap_r2.
 template <int V>
-__device__ __forceinline__ void fast_decide(float dx, float dy, float dz, const FastParams& P, bool& nearedge,
-                                            uint32_t& rel, float& q_out) {
-  bool amb = false;
-  float r2 = wrap_r2<V>(dx, dy, dz, P, amb);
-  float q = __fmul_rn(r2, P.S2);
-  float s = sqrt_approx(q);
-  float sm = __fadd_rn(s, kMagicRound);
-  float n = __fsub_rn(sm, kMagicRound);
-  float e = __fmaf_rn(-n, n, q);
-  float bound = __fmaf_rn(P.qc2, q, __fmaf_rn(P.qc1, s, P.qc0));
-  nearedge = fabsf(e) <= bound;
-  if (V == V_TRIC_SEARCH) nearedge = nearedge || amb;
-  int k = __float_as_int(sm) - P.kbase;
-  if (e < 0.0f) k -= 1;
-  rel = (uint32_t)k;
-  q_out = q;
+__device__ __forceinline__ float2 wrap_r2_2(float2 dx, float2 dy, float2 dz, const FastParams& P, bool& amb_a,
+                                            bool& amb_b) {
+  const float2 M = bc2(kMagicRound), NM = bc2(-kMagicRound);
+  if (V == V_ORTHO) {
+    float2 kx = add2(fma2(dx, bc2(P.inv[0]), M), NM);
+    float2 ky = add2(fma2(dy, bc2(P.inv[1]), M), NM);
+    float2 kz = add2(fma2(dz, bc2(P.inv[2]), M), NM);
+    dx = fma2(kx, bc2(-P.b[0]), dx);
+    dy = fma2(ky, bc2(-P.b[4]), dy);
+    dz = fma2(kz, bc2(-P.b[8]), dz);
+  } else if (V == V_TRIC) {
+    float2 kz = add2(fma2(dz, bc2(P.inv[2]), M), NM);
+    dx = fma2(kz, bc2(-P.b[2]), dx);
+    dy = fma2(kz, bc2(-P.b[5]), dy);
+    dz = fma2(kz, bc2(-P.b[8]), dz);
+    float2 ky = add2(fma2(dy, bc2(P.inv[1]), M), NM);
+    dx = fma2(ky, bc2(-P.b[1]), dx);
+    dy = fma2(ky, bc2(-P.b[4]), dy);
+    float2 kx = add2(fma2(dx, bc2(P.inv[0]), M), NM);
+    dx = fma2(kx, bc2(-P.b[0]), dx);
+  } else if (V == V_TRIC_SEARCH) {
+    return make_float2(wrap_r2<V>(dx.x, dy.x, dz.x, P, amb_a), wrap_r2<V>(dx.y, dy.y, dz.y, P, amb_b));
+  }
+  return fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+}
+
+// Count or defer one pair, branch free: with rel = floor(t) - lo computed from
+// sm = s + 1.5*2^23 (bits(sm) - kbase = nearest integer - lo) and the residual
+// e = n^2 - q (e > 0: t < n, so floor(t) = n - 1), the pair is decided in float32
+// when |e| > bound (false for NaN); a decided pair inside this sweep increments
+// its shared-memory bin, an undecided one sets the bits `bit` of dmask.
+__device__ __forceinline__ void count_or_defer(float sm, float e, float bound, int kbase, uint32_t width,
+                                               uint32_t sbase, uint32_t bit, uint32_t& dmask) {
+  asm volatile(
+      "{\n\t.reg .pred pp, pn, pc;\n\t.reg .u32 rel, addr;\n\t.reg .f32 ae;\n\t"
+      "sub.u32 rel, %1, %2;\n\t"
+      "setp.gt.f32 pp, %3, 0f00000000;\n\t"
+      "@pp sub.u32 rel, rel, 1;\n\t"
+      "abs.f32 ae, %3;\n\t"
+      "setp.gtu.f32 pn, ae, %4;\n\t"
+      "setp.lt.and.u32 pc, rel, %5, pn;\n\t"
+      "@!pn or.b32 %0, %0, %7;\n\t"
+      "mad.lo.u32 addr, rel, 4, %6;\n\t"
+      "@pc red.shared.add.u32 [addr], 1;\n\t"
+      "}"
+      : "+r"(dmask)
+      : "r"(__float_as_uint(sm)), "r"(kbase), "f"(e), "f"(bound), "r"(width), "r"(sbase), "r"(bit));
+}
+
+// The float32 decision of two pairs (j, j+1 against one i).  With q = r^2 S^2
+// (= t^2) and n the integer nearest to sqrt(q), the residual e = n^2 - q is
+// rounded once (fma), so its sign gives floor(t) = n or n-1, and |e| is
+// compared with the bound derived in frame_setup_kernel; within it the pair
+// is deferred.  NaN pairs are never deferred and never counted.
+// decide_arith2 returns sm = s + 1.5*2^23, e and the bound as float pairs
+// (search variant: ambiguous images force the bound to +inf so the pair is
+// deferred); count_or_defer acts on them.
+template <int V>
+__device__ __forceinline__ void decide_arith2(float2 dx, float2 dy, float2 dz, const FastParams& P, float2& sm,
+                                              float2& e, float2& bound) {
+  bool amb_a = false, amb_b = false;
+  float2 r2 = wrap_r2_2<V>(dx, dy, dz, P, amb_a, amb_b);
+  float2 nq = mul2(r2, bc2(-P.S2));  // -q
+  float2 sq = make_float2(sqrt_approx(-nq.x), sqrt_approx(-nq.y));
+  sm = add2(sq, bc2(kMagicRound));
+  float2 n = add2(sm, bc2(-kMagicRound));
+  e = fma2(n, n, nq);  // n^2 - q
+  bound = (V == V_NONE) ? fma2(nq, bc2(-P.qb1), bc2(P.qb0)) : fma2(sq, bc2(P.qb1), bc2(P.qb0));
+  if (V == V_TRIC_SEARCH) {
+    if (amb_a) bound.x = INFINITY;
+    if (amb_b) bound.y = INFINITY;
+  }
+}
+
+// The same decision as count_or_defer, as values (used by the self check).
+template <int V>
+__device__ __forceinline__ void fast_decide2(float2 dx, float2 dy, float2 dz, const FastParams& P, bool& near_a,
+                                             bool& near_b, uint32_t& rel_a, uint32_t& rel_b) {
+  float2 sm, e, bound;
+  decide_arith2<V>(dx, dy, dz, P, sm, e, bound);
+  near_a = fabsf(e.x) <= bound.x;
+  near_b = fabsf(e.y) <= bound.y;
+  rel_a = (uint32_t)(__float_as_int(sm.x) - P.kbase - (e.x > 0.0f ? 1 : 0));
+  rel_b = (uint32_t)(__float_as_int(sm.y) - P.kbase - (e.y > 0.0f ? 1 : 0));
 }
 
 // ---- double-float middle tier
@@ -574,46 +652,52 @@ __device__ __noinline__ int drain_queue(const FrameDev* F, int lo, uint32_t widt
   return rest;
 }
 
+// j tile in shared memory as pairs of particles: A[p] = {x_2p, x_2p+1, y_2p, y_2p+1},
+// Z[p] = {z_2p, z_2p+1}, so one LDS.128 + one LDS.64 feed two j particles.
 template <int V, bool MASKED>
 __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
-                                         const float4* __restrict__ sj, uint32_t* sh, uint2* q,
-                                         int tid, int lane, unsigned& ndeferred) {
-  float xi[kRegI], yi[kRegI], zi[kRegI];
+                                         const float4* __restrict__ sjA, const float2* __restrict__ sjZ,
+                                         uint32_t* sh, uint2* q, int tid, int lane, unsigned& ndeferred) {
+  float2 xi[kRegI], yi[kRegI], zi[kRegI];  // i coordinates broadcast to both halves
   const int ibase = it.i0 + tid;
 #pragma unroll
   for (int r = 0; r < kRegI; ++r) {
     int li = tid + r * kBlock;
+    float x = __int_as_float(0x7fffffff), y = x, z = x;
     if (li < it.ni) {
       float4 p = __ldg(F->X + ibase + r * kBlock);
-      xi[r] = p.x; yi[r] = p.y; zi[r] = p.z;
-    } else {
-      xi[r] = __int_as_float(0x7fffffff); yi[r] = xi[r]; zi[r] = xi[r];
+      x = p.x; y = p.y; z = p.z;
     }
+    xi[r] = bc2(-x); yi[r] = bc2(-y); zi[r] = bc2(-z);  // negated: d = xj + (-xi)
   }
   const unsigned lt_mask = (1u << lane) - 1u;
   const float qnan = __int_as_float(0x7fffffff);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sh);
   const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);  // the j tile is padded with NaN particles
   int qcount = 0;
   for (int jj0 = 0; jj0 < nj4; jj0 += kJU) {
     uint32_t dmask = 0u;
+    // (u, r) are compile-time constants after unrolling: they name the mask bit
 #pragma unroll
-    for (int u = 0; u < kJU; ++u) {
-      const float4 pj = sj[jj0 + u];
+    for (int u = 0; u < kJU; u += 2) {
+      const float4 A = sjA[(jj0 + u) >> 1];
+      const float2 Z = sjZ[(jj0 + u) >> 1];
+      const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
 #pragma unroll
       for (int r = 0; r < kRegI; ++r) {
-        float dx = __fsub_rn(pj.x, xi[r]);
-        float dy = __fsub_rn(pj.y, yi[r]);
-        float dz = __fsub_rn(pj.z, zi[r]);
+        float2 dx = add2(xj, xi[r]);
+        float2 dy = add2(yj, yi[r]);
+        float2 dz = add2(Z, zi[r]);
         if (MASKED) {
           // intra-species: only j > i; all three components so no later test sees a number
-          if (!(it.j0 + jj0 + u > ibase + r * kBlock)) { dx = qnan; dy = qnan; dz = qnan; }
+          const int ig = ibase + r * kBlock, jg = it.j0 + jj0 + u;
+          if (!(jg > ig)) { dx.x = qnan; dy.x = qnan; dz.x = qnan; }
+          if (!(jg + 1 > ig)) { dx.y = qnan; dy.y = qnan; dz.y = qnan; }
         }
-        bool nearedge;
-        uint32_t rel;
-        float qv;
-        fast_decide<V>(dx, dy, dz, P, nearedge, rel, qv);
-        if (!nearedge && rel < P.width) atomicAdd(sh + rel, 1u);
-        if (nearedge) dmask |= 1u << (u * kRegI + r);
+        float2 sm, e, bound;
+        decide_arith2<V>(dx, dy, dz, P, sm, e, bound);
+        count_or_defer(sm.x, e.x, bound.x, P.kbase, P.width, sbase, 1u << (u * kRegI + r), dmask);
+        count_or_defer(sm.y, e.y, bound.y, P.kbase, P.width, sbase, 1u << ((u + 1) * kRegI + r), dmask);
       }
     }
     // queue the deferred pairs: one per lane per round, compacted with a ballot
@@ -645,12 +729,12 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P);
 // The decision parameters are reloaded per item (from the L1-cached frame
 // descriptor) so that only the fields of this variant are live in the loop.
 template <int V>
-__device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj, uint32_t* sh, uint2* q,
-                         int tid, int lane, unsigned& ndeferred) {
+__device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
+                         uint2* q, int tid, int lane, unsigned& ndeferred) {
   FastParams P;
   load_fast_params(*F, it.pass, P);
-  if (it.masked) run_tile<V, true>(F, P, it, sj, sh, q, tid, lane, ndeferred);
-  else run_tile<V, false>(F, P, it, sj, sh, q, tid, lane, ndeferred);
+  if (it.masked) run_tile<V, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
+  else run_tile<V, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
 }
 
 __device__ void flush_hist(uint32_t* sh, int width, uint64_t* dst, int tid) {
@@ -707,9 +791,8 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
   int lo_bin = pass * F.sweep_width;
   int hi_bin = min(F.nbins, lo_bin + F.sweep_width);
   P.S2 = F.S2;
-  P.qc2 = F.qc2;
-  P.qc1 = F.qc1;
-  P.qc0 = F.qc0;
+  P.qb1 = F.qb1;
+  P.qb0 = F.qb0;
   P.kbase = __float_as_int(kMagicRound) + lo_bin;
   P.width = (uint32_t)(hi_bin - lo_bin);
   P.lo = lo_bin;
@@ -732,8 +815,9 @@ __global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(Pa
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int width_pad = (L.hist_width + 3) & ~3;
   uint32_t* sh = reinterpret_cast<uint32_t*>(smem_raw);
-  float4* sj = reinterpret_cast<float4*>(sh + width_pad);
-  uint2* sq = reinterpret_cast<uint2*>(sj + kTile);
+  float4* sjA = reinterpret_cast<float4*>(sh + width_pad);
+  float2* sjZ = reinterpret_cast<float2*>(sjA + kTile / 2);
+  uint2* sq = reinterpret_cast<uint2*>(sjZ + kTile / 2);
   __shared__ ItemDesc s_it;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -784,17 +868,20 @@ __global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(Pa
         since = 0;
       }
       since += pairs;
-      // stage the j tile (float4 per particle), padded with NaN particles to a multiple of kJU
+      // stage the j tile in pair layout, padded with NaN particles to a multiple of kJU
       const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);
       for (int k = tid; k < nj4; k += kBlock) {
         float4 v;
         if (k < it.nj) v = __ldg(F.X + it.j0 + k);
         else v = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff), __int_as_float(0x7fffffff), 0.f);
-        sj[k] = v;
+        float* a = reinterpret_cast<float*>(sjA + (k >> 1));
+        a[k & 1] = v.x;
+        a[2 + (k & 1)] = v.y;
+        reinterpret_cast<float*>(sjZ + (k >> 1))[k & 1] = v.z;
       }
       __syncthreads();
       unsigned ndef = 0;
-      run_item<V>(it.fd, it, sj, sh, q, tid, lane, ndef);
+      run_item<V>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();
@@ -841,10 +928,12 @@ template <int V>
 __device__ void check_window_pair(const FrameDev& F, const FastParams& P, int i, int j, double* worst,
                                   unsigned long long* viol, unsigned long long* checked) {
   float4 pi = F.X[i], pj = F.X[j];
-  bool nearedge;
-  uint32_t rel;
-  float q;
-  fast_decide<V>(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z), P, nearedge, rel, q);
+  bool nearedge, nb_unused;
+  uint32_t rel, rb_unused;
+  const float2 dx = bc2(__fsub_rn(pj.x, pi.x)), dy = bc2(__fsub_rn(pj.y, pi.y)), dz = bc2(__fsub_rn(pj.z, pi.z));
+  fast_decide2<V>(dx, dy, dz, P, nearedge, nb_unused, rel, rb_unused);
+  bool amb0 = false, amb1 = false;
+  float q = __fmul_rn(wrap_r2_2<V>(dx, dy, dz, P, amb0, amb1).x, P.S2);
   double r2 = exact_r2<V>(F, pi, pj);
   int k64 = bin_from_thresholds(F.T, F.nbins, r2);
   double t64 = __dmul_rn(__dsqrt_rn(r2), (double)F.nbins / F.r_max);
@@ -913,7 +1002,7 @@ cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t 
 
 size_t pair_kernel_smem(int hist_width) {
   size_t w = (size_t)((hist_width + 3) & ~3);
-  return w * 4 + (size_t)kTile * 16 + (size_t)kWarps * kQueueCap * 8;
+  return w * 4 + (size_t)kTile * 12 + (size_t)kWarps * kQueueCap * 8;
 }
 
 int pair_kernel_max_width() {
