@@ -179,6 +179,15 @@ __global__ void stage_kernel(const StageJob* __restrict__ jobs, int n_jobs) {
 
 // ------------------------------------------------------------------ per-frame error window
 
+// Largest rounding error (half an ulp) of a float32 result whose exact value
+// has magnitude at most D.
+__device__ inline double half_ulp_below(double D) {
+  if (!(D > 0.0)) return 0.0;
+  int E;
+  frexp(D, &E);  // D = m 2^E, m in [1/2, 1): |x| <= D < 2^E
+  return ldexp(1.0, E - 25);
+}
+
 // Derives, for one frame, the bound of the float32 decision and of the
 // double-float tier from its box, r_max, nbins and the coordinate ranges found
 // by stage_kernel.  Every float32 operation rounds to nearest (relative error
@@ -188,12 +197,14 @@ __global__ void stage_kernel(const StageJob* __restrict__ jobs, int n_jobs) {
 //   alpha: rounding of d (none) or of the final wrapped d' (u), the
 //          r^2 = fma(dz,dz,fma(dy,dy,dx*dx)) chain (3u on r^2 -> 1.5u),
 //          float32 S^2 and the product q = r^2 S^2 ((eps_S2 + u)/2);
-//   beta:  S*|a|, a_c the absolute error of d'_c: rounding of xj - xi (u R_c),
-//          of each wrap intermediate (u |intermediate|) and the float32 box
-//          entries (|k| |B32 - B|); for orthorhombic boxes, where float32 and
-//          binary64 may round d/L to different images near a half integer
-//          (both then have |d'_c| within 2u R_c of L_c/2), a further S*4u|R|
-//          when t can reach S L_min/2 inside the histogram.
+//   beta:  S*|a|, a_c the absolute error of d'_c: rounding of xj - xi (half an
+//          ulp of the largest |d_c| <= R_c), of each wrap intermediate (half an
+//          ulp of its largest magnitude) and the float32 box entries
+//          (|k| |B32 - B|, |k| at most the nearest integer of the largest
+//          |d|/L); for orthorhombic boxes, where float32 and binary64 may round
+//          d/L to different images within eta of a half integer (both images
+//          then have |d'_c| within eta L of L_c/2), S*2 eta L for as many
+//          components as can reach L_c/2 below r_max (1 + 2/nbins).
 //  q-space test: with n the integer nearest to sqrt(q32), floor(t) is decided
 //  when |q32 - n^2| > (alpha t' + beta)(2 t' + 1) = 2 alpha q + (alpha + 2 beta) t' + beta,
 //  with t' <= s (1 + 2^-18) for s = sqrt.approx(q32).
@@ -226,31 +237,40 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   double dB[9];
   for (int q = 0; q < 9; ++q) dB[q] = fabs((double)F.Bf[q] - B[q]);
   if (F.variant == V_ORTHO) {
-    double Lmin = INFINITY, Rn2 = 0, Rmax = 0;
+    double Lmin = INFINITY, tie_c[3];
     for (int c = 0; c < 3; ++c) {
       double L = B[4 * c];
-      double K = floor(R[c] / L + 0.5) + 1.0;
-      a[c] = u * R[c] + K * dB[4 * c];
+      double K = floor(R[c] / L * (1.0 + 1e-9) + 0.5);  // largest |k| = nint(d/L) over |d| <= R_c
+      a[c] = half_ulp_below(R[c]) + K * dB[4 * c];
       I[c] = R[c] + K * L;
       if (R[c] / L > 1048576.0) all_defer = 1;  // nearest integer via the 1.5*2^23 trick needs |d/L| < 2^22
       Lmin = fmin(Lmin, L);
-      Rn2 += R[c] * R[c];
-      Rmax = fmax(Rmax, R[c]);
+      // float32 and binary64 can round d/L to different images only within eta of a
+      // half integer; both images then have |d'_c| within eta L of L/2
+      double eta = (half_ulp_below(R[c]) + R[c] * fabs((double)F.invf[c] - 1.0 / L)) / L + 1e-15 * (R[c] / L + 1.0);
+      tie_c[c] = 2.0 * eta * L;
     }
-    double t_tie = S * Lmin * 0.5 * (1.0 - 8.0 * u * sqrt(Rn2) / Lmin) - 1.0;
-    if (t_tie <= (double)F.nbins + 1.0) tie = S * 4.0 * u * sqrt(Rn2) * 1.01;
-    tie_eps = 8.0 * u * Rmax + 1e-12 * Lmin;
+    // components that can sit at L_c/2 while t <= nbins + 1 (r <= r_max (1 + 1/nbins))
+    double rr = F.r_max * (1.0 + 2.0 / (double)F.nbins);
+    int m = (int)fmin(3.0, floor(4.0 * rr * rr / (Lmin * Lmin)));
+    if (m >= 1) {
+      double t1 = fmax(tie_c[0], fmax(tie_c[1], tie_c[2]));
+      double t3 = sqrt(tie_c[0] * tie_c[0] + tie_c[1] * tie_c[1] + tie_c[2] * tie_c[2]);
+      tie = S * (m >= 3 ? t3 : (m == 2 ? fmin(t3, 1.4142135623730951 * t1) : t1)) * 1.01;
+    }
+    tie_eps = 2.0 * fmax(tie_c[0], fmax(tie_c[1], tie_c[2])) + 1e-12 * Lmin;
   } else if (F.variant == V_TRIC) {
-    // sequential wrap along c, then b, then a (Eq. 5 below half the plane spacing)
+    // sequential wrap along c, then b, then a (Eq. 5 below half the plane spacing);
+    // D are the largest magnitudes of the intermediates, K the largest |k|
     double ax = B[0], bx = B[1], cx = B[2], by = B[4], cy = B[5], cz = B[8];
-    double Kz = floor(R[2] / cz + 0.5) + 1.0;
+    double Kz = floor(R[2] / cz * (1.0 + 1e-9) + 0.5);
     double D1x = R[0] + Kz * fabs(cx), D1y = R[1] + Kz * fabs(cy);
-    double Ky = floor(D1y / by + 0.5) + 1.0;
+    double Ky = floor(D1y / by * (1.0 + 1e-9) + 0.5);
     double D2x = D1x + Ky * fabs(bx);
-    double Kx = floor(D2x / ax + 0.5) + 1.0;
-    a[0] = u * (R[0] + D1x + D2x) + Kz * dB[2] + Ky * dB[1] + Kx * dB[0];
-    a[1] = u * (R[1] + D1y) + Kz * dB[5] + Ky * dB[4];
-    a[2] = u * R[2] + Kz * dB[8];
+    double Kx = floor(D2x / ax * (1.0 + 1e-9) + 0.5);
+    a[0] = half_ulp_below(R[0]) + half_ulp_below(D1x) + half_ulp_below(D2x) + Kz * dB[2] + Ky * dB[1] + Kx * dB[0];
+    a[1] = half_ulp_below(R[1]) + half_ulp_below(D1y) + Kz * dB[5] + Ky * dB[4];
+    a[2] = half_ulp_below(R[2]) + Kz * dB[8];
     I[0] = D2x + Kx * ax;
     I[1] = D1y + Ky * by;
     I[2] = R[2] + Kz * cz;
@@ -807,7 +827,7 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
 // frame of that variant.
 template <int V>
 constexpr int min_blocks_per_sm() {
-  return (V == V_NONE || V == V_ORTHO) ? 3 : 2;
+  return (V == V_NONE || V == V_ORTHO || V == V_TRIC) ? 3 : 2;
 }
 
 template <int V>
