@@ -251,6 +251,121 @@ def run_reference(args, world, rank):
     return 0
 
 
+
+# ---------------------------------------------------------------- batched and served legs
+
+
+def run_batched_c4(ctx, stream, dev, args):
+    """C4: orthorhombic frames of uneven N in one dh_histogram_batch (CUDA graph)
+    against the same frames through one dh_histogram call each."""
+    import torch
+
+    import paper_1808_01478_gb300 as dh
+
+    frames = w.batch_frames(seed=7, n_frames=args.c4_frames)
+    pairs = sum(f.n_pairs() for f in frames)
+    X = [torch.from_numpy(f.coords).to(dev) for f in frames]
+    fas = [dh.FrameArgs(X[k], f.offsets, f.box_type, f.box, f.r_max, f.nbins) for k, f in enumerate(frames)]
+    ctx.histogram_batch(fas)
+    graph = ctx.stats()["graph_replays"]
+    ts = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.histogram_batch(fas)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    batch_ms = min(ts)
+    outs = [torch.zeros_like(fa.out) for fa in fas]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k, f in enumerate(frames):
+        ctx.histogram(X[k], f.offsets, f.box_type, f.box, f.r_max, f.nbins, outs[k])
+    e1.record(stream)
+    e1.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    same = all(torch.equal(outs[k], fas[k].out) for k in range(len(frames)))
+    return {"frames": len(frames), "pairs": pairs, "batch_gpairs_s": round(pairs / (batch_ms / 1e3) / 1e9, 3),
+            "batch_ms": round(batch_ms, 3), "cuda_graph": bool(graph),
+            "plain_loop_gpairs_s": round(pairs / (plain_ms / 1e3) / 1e9, 3), "plain_loop_ms": round(plain_ms, 3),
+            "identical_to_plain": same}
+
+
+def run_served_c5(dev_index, dev, capacity_pairs_s, args):
+    """C5: Poisson arrivals of frame requests (mixed boxes, 1-3 species, 2^10..2^14
+    bins, N log-uniform in [10^3, 10^6]) at offered load rho x the plain-path
+    capacity; coordinates and histograms stay on the device."""
+    import torch
+
+    import paper_1808_01478_gb300 as dh
+
+    rng = w.rng_for(2024)
+    frames = [w.served_request(rng) for _ in range(args.served_requests)]
+    pairs = np.array([f.n_pairs() for f in frames], dtype=np.float64)
+    fas = [dh.FrameArgs(torch.from_numpy(f.coords).to(dev), f.offsets, f.box_type, f.box, f.r_max, f.nbins)
+           for f in frames]
+    torch.cuda.synchronize()
+    lam = args.served_load * capacity_pairs_s / pairs.mean()
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(frames)))
+    done_t = [None] * len(frames)
+    sub_t = [None] * len(frames)
+    tickets = [None] * len(frames)
+    status = [None] * len(frames)
+    with dh.Context(dev_index, pool_bytes=8 << 30, max_inflight=64) as sctx:
+        # warm the server (pool, threads, kernels) outside the measurement
+        warm = dh.FrameArgs(frames[0].coords, frames[0].offsets, frames[0].box_type, frames[0].box,
+                            frames[0].r_max, frames[0].nbins)
+        sctx.wait(sctx.submit(warm))
+        stop = threading.Event()
+        lock = threading.Lock()
+
+        def poller():
+            while not stop.is_set():
+                with lock:
+                    live = [k for k in range(len(frames)) if tickets[k] is not None and done_t[k] is None]
+                for k in live:
+                    st = sctx.poll(tickets[k])
+                    if st != dh.DH_PENDING:
+                        done_t[k] = time.perf_counter()
+                        status[k] = st
+                time.sleep(50e-6)
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        for k in range(len(frames)):
+            target = t0 + arrivals[k]
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                time.sleep(min(0.0005, target - now))
+            sub_t[k] = time.perf_counter()
+            t = sctx.submit(fas[k])
+            with lock:
+                tickets[k] = t
+        deadline = time.perf_counter() + 600
+        while any(d is None for d in done_t) and time.perf_counter() < deadline:
+            time.sleep(0.001)
+        stop.set()
+        th.join()
+    ok = all(s == dh.DH_OK for s in status)
+    lat = np.array([(d - s_) * 1e3 for d, s_ in zip(done_t, sub_t)])
+    span = max(done_t) - min(sub_t)
+    # a sample of requests recomputed alone through the plain path must match bit for bit
+    check = []
+    with dh.Context(dev_index) as pctx:
+        for k in np.linspace(0, len(frames) - 1, 4).astype(int):
+            f = frames[k]
+            x = torch.from_numpy(f.coords).to(dev)
+            alone = pctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins)
+            check.append(bool(torch.equal(alone, fas[k].out)))
+    return {"requests": len(frames), "offered_load": args.served_load, "arrival_rate_per_s": round(lam, 3),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mean_ms": round(float(lat.mean()), 3), "gpairs_s": round(pairs.sum() / span / 1e9, 3),
+            "all_ok": ok, "alone_equals_mixed_sample": all(check), "pairs": float(pairs.sum())}
+
 # ---------------------------------------------------------------- GPU arm
 
 
@@ -361,6 +476,10 @@ def run_gpu(args, world, rank, local):
     h2d = sum(f.n * 12 for f in frames)
     d2h = sum(f.nbins * 8 for f in frames)
 
+    c4 = run_batched_c4(ctx, stream, dev, args) if args.c4_frames > 0 else None
+    capacity = statistics.mean(v["gpairs_s"] for v in plain.values()) * 1e9
+    served = run_served_c5(local, dev, capacity, args) if args.served_requests > 0 else None
+
     launches_per_step = stats_b["kernel_launches"]
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -371,8 +490,9 @@ def run_gpu(args, world, rank, local):
         "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "matches_device_result": e2e_ok},
         "plain": plain,
-        "batched": {"gpairs_s": round(value, 3), "deferred_frac": round(stats_b["deferred"] / max(1, stats_b["pairs"]), 6)},
-        "served": None,
+        "batched": {"gpairs_s": round(value, 3), "deferred_frac": round(stats_b["deferred"] / max(1, stats_b["pairs"]), 6),
+                    "cuda_graph": bool(stats_b["graph_replays"]), "c4": c4},
+        "served": served,
         "roofline": roofline,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -405,6 +525,9 @@ def main(argv=None) -> int:
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--c4-frames", type=int, default=256)
+    ap.add_argument("--served-requests", type=int, default=200)
+    ap.add_argument("--served-load", type=float, default=0.8)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -108,6 +108,8 @@ typedef struct {
   int32_t blocks;          /* CUDA blocks launched for the pair kernel */
   int32_t items;           /* work items (tile pairs) */
   int32_t kernel_launches; /* kernels launched by the call */
+  int32_t graph_replays;   /* 1 when the call ran as a replayed CUDA graph */
+  int32_t reserved;
   double pair_kernel_ms;   /* device time of the pair-kernel launches (needs DH_CFG_TIMING), else 0 */
 } dh_stats;
 
@@ -137,9 +139,12 @@ dh_status dh_histogram_async(dh_ctx* ctx, const dh_frame* frame);
 /* Wait for work enqueued by dh_histogram_async and report device-side errors. */
 dh_status dh_sync(dh_ctx* ctx);
 
-/* k frames of possibly different N, species, box and nbins through one
- * persistent launch per bin sweep.  All frames must use the same pointer kind
- * (all DH_DEVICE_PTRS or none).  Synchronous. */
+/* k frames of possibly different N, species, box and nbins (the frame-by-frame
+ * workload of the paper's engine, Sec. 3.3) through one persistent pair-kernel
+ * launch per minimum-image variant present, all bin sweeps included.  All
+ * frames must use the same pointer kind (all DH_DEVICE_PTRS or none).  With
+ * device pointers the launch sequence is captured as a CUDA graph and replayed
+ * (unless DH_CFG_NO_GRAPH).  Synchronous. */
 dh_status dh_histogram_batch(dh_ctx* ctx, const dh_frame* frames, int32_t k);
 
 /* Served path: submit one frame as a request.  Coordinates and output stay on

@@ -60,7 +60,8 @@ class dh_stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_uint64), ("deferred", ctypes.c_uint64),
                 ("exact_fallback", ctypes.c_uint64), ("sweeps", ctypes.c_int32),
                 ("blocks", ctypes.c_int32), ("items", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int32), ("pair_kernel_ms", ctypes.c_double)]
+                ("kernel_launches", ctypes.c_int32), ("graph_replays", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("pair_kernel_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -248,6 +249,7 @@ class FrameArgs:
             assert out.is_cuda and out.is_contiguous() and out.element_size() == 8
             flags |= DH_DEVICE_PTRS
             cptr, optr = coords.data_ptr(), out.data_ptr()
+            self.keep += [coords, out]  # the library reads these buffers until the call (or request) ends
         else:
             c = np.ascontiguousarray(coords, dtype=np.float32)
             if c.ndim == 2 and c.shape[1] == 4:

@@ -126,6 +126,7 @@ struct dh_ctx {
   cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;  // pair-kernel timing (DH_CFG_TIMING)
   bool timed = false;
   bool pending_async = false;
+  cudaGraphExec_t gexec = nullptr;  // batched path: executable graph, updated per call
 
   std::mutex server_mu;
   dh::Server* server = nullptr;
