@@ -292,49 +292,36 @@ def run_batched_c4(ctx, stream, dev, args):
             "identical_to_plain": same}
 
 
-def run_served_c5(dev_index, dev, capacity_pairs_s, args):
-    """C5: Poisson arrivals of frame requests (mixed boxes, 1-3 species, 2^10..2^14
-    bins, N log-uniform in [10^3, 10^6]) at offered load rho x the plain-path
-    capacity; coordinates and histograms stay on the device."""
-    import torch
-
+def _serve(dev_index, fas, pairs, arrivals):
+    """Submit request k at arrivals[k] seconds (one client thread) while a poller
+    thread records completions; returns latencies (ms), status and the span."""
     import paper_1808_01478_gb300 as dh
 
-    rng = w.rng_for(2024)
-    frames = [w.served_request(rng) for _ in range(args.served_requests)]
-    pairs = np.array([f.n_pairs() for f in frames], dtype=np.float64)
-    fas = [dh.FrameArgs(torch.from_numpy(f.coords).to(dev), f.offsets, f.box_type, f.box, f.r_max, f.nbins)
-           for f in frames]
-    torch.cuda.synchronize()
-    lam = args.served_load * capacity_pairs_s / pairs.mean()
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(frames)))
-    done_t = [None] * len(frames)
-    sub_t = [None] * len(frames)
-    tickets = [None] * len(frames)
-    status = [None] * len(frames)
+    n = len(fas)
+    done_t, sub_t, tickets, status = [None] * n, [None] * n, [None] * n, [None] * n
     with dh.Context(dev_index, pool_bytes=8 << 30, max_inflight=64) as sctx:
-        # warm the server (pool, threads, kernels) outside the measurement
-        warm = dh.FrameArgs(frames[0].coords, frames[0].offsets, frames[0].box_type, frames[0].box,
-                            frames[0].r_max, frames[0].nbins)
-        sctx.wait(sctx.submit(warm))
+        f0 = fas[0]
+        warm = dh.FrameArgs(f0.coords, f0.offsets, f0.frame.box_type, list(f0.frame.box), f0.frame.r_max,
+                            f0.frame.nbins)
+        sctx.wait(sctx.submit(warm))  # pool, lanes and kernels warm before the measurement
         stop = threading.Event()
         lock = threading.Lock()
 
         def poller():
             while not stop.is_set():
                 with lock:
-                    live = [k for k in range(len(frames)) if tickets[k] is not None and done_t[k] is None]
+                    live = [k for k in range(n) if tickets[k] is not None and done_t[k] is None]
                 for k in live:
                     st = sctx.poll(tickets[k])
                     if st != dh.DH_PENDING:
                         done_t[k] = time.perf_counter()
                         status[k] = st
-                time.sleep(50e-6)
+                time.sleep(100e-6)
 
         th = threading.Thread(target=poller, daemon=True)
         th.start()
         t0 = time.perf_counter()
-        for k in range(len(frames)):
+        for k in range(n):
             target = t0 + arrivals[k]
             while True:
                 now = time.perf_counter()
@@ -345,26 +332,64 @@ def run_served_c5(dev_index, dev, capacity_pairs_s, args):
             t = sctx.submit(fas[k])
             with lock:
                 tickets[k] = t
-        deadline = time.perf_counter() + 600
+        deadline = time.perf_counter() + 900
         while any(d is None for d in done_t) and time.perf_counter() < deadline:
             time.sleep(0.001)
         stop.set()
         th.join()
-    ok = all(s == dh.DH_OK for s in status)
     lat = np.array([(d - s_) * 1e3 for d, s_ in zip(done_t, sub_t)])
-    span = max(done_t) - min(sub_t)
-    # a sample of requests recomputed alone through the plain path must match bit for bit
-    check = []
+    return lat, status, max(done_t) - min(sub_t)
+
+
+def run_served_c5(dev_index, dev, args):
+    """C5: Poisson arrivals of frame requests (mixed boxes, 1-3 species, 2^10..2^14
+    bins, N log-uniform in [10^3, 10^6]) at offered loads rho x the capacity of
+    the plain per-frame path on the same requests, plus all requests at once
+    (the server's saturated throughput); coordinates and histograms stay on the
+    device."""
+    import torch
+
+    import paper_1808_01478_gb300 as dh
+
+    rng = w.rng_for(2024)
+    frames = [w.served_request(rng) for _ in range(args.served_requests)]
+    pairs = np.array([f.n_pairs() for f in frames], dtype=np.float64)
+    fas = [dh.FrameArgs(torch.from_numpy(f.coords).to(dev), f.offsets, f.box_type, f.box, f.r_max, f.nbins)
+           for f in frames]
+    torch.cuda.synchronize()
+    # the plain per-frame path on the same requests, one at a time: capacity and
+    # the latency of each request when it has the GPU to itself
+    alone_ms = []
+    ref = [torch.zeros_like(fa.out) for fa in fas]
     with dh.Context(dev_index) as pctx:
-        for k in np.linspace(0, len(frames) - 1, 4).astype(int):
-            f = frames[k]
-            x = torch.from_numpy(f.coords).to(dev)
-            alone = pctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins)
-            check.append(bool(torch.equal(alone, fas[k].out)))
-    return {"requests": len(frames), "offered_load": args.served_load, "arrival_rate_per_s": round(lam, 3),
-            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "mean_ms": round(float(lat.mean()), 3), "gpairs_s": round(pairs.sum() / span / 1e9, 3),
-            "all_ok": ok, "alone_equals_mixed_sample": all(check), "pairs": float(pairs.sum())}
+        pctx.histogram(fas[0].coords, frames[0].offsets, frames[0].box_type, frames[0].box, frames[0].r_max,
+                       frames[0].nbins, ref[0])
+        for k, f in enumerate(frames):
+            t0 = time.perf_counter()
+            pctx.histogram(fas[k].coords, f.offsets, f.box_type, f.box, f.r_max, f.nbins, ref[k])
+            alone_ms.append((time.perf_counter() - t0) * 1e3)
+    alone_ms = np.array(alone_ms)
+    capacity = pairs.sum() / (alone_ms.sum() / 1e3)
+    out = {"requests": len(frames), "pairs": float(pairs.sum()),
+           "plain_capacity_gpairs_s": round(capacity / 1e9, 3),
+           "plain_alone_p50_ms": round(float(np.percentile(alone_ms, 50)), 3),
+           "plain_alone_p99_ms": round(float(np.percentile(alone_ms, 99)), 3), "loads": {}}
+    arr_rng = w.rng_for(77)
+    for load in args.served_loads:
+        lam = load * capacity / pairs.mean()
+        arrivals = np.cumsum(arr_rng.exponential(1.0 / lam, size=len(frames)))
+        lat, status, span = _serve(dev_index, fas, pairs, arrivals)
+        same = all(torch.equal(ref[k], fas[k].out) for k in range(len(frames)))
+        out["loads"][str(load)] = {
+            "arrival_rate_per_s": round(lam, 3), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+            "p99_slowdown": round(float(np.percentile(lat / alone_ms, 99)), 3),
+            "gpairs_s": round(pairs.sum() / span / 1e9, 3),
+            "all_ok": all(s_ == dh.DH_OK for s_ in status), "identical_to_plain": same}
+    lat, status, span = _serve(dev_index, fas, pairs, np.zeros(len(frames)))
+    out["saturated_gpairs_s"] = round(pairs.sum() / span / 1e9, 3)
+    out["saturated_identical_to_plain"] = all(torch.equal(ref[k], fas[k].out) for k in range(len(frames)))
+    return out
 
 # ---------------------------------------------------------------- GPU arm
 
@@ -477,8 +502,7 @@ def run_gpu(args, world, rank, local):
     d2h = sum(f.nbins * 8 for f in frames)
 
     c4 = run_batched_c4(ctx, stream, dev, args) if args.c4_frames > 0 else None
-    capacity = statistics.mean(v["gpairs_s"] for v in plain.values()) * 1e9
-    served = run_served_c5(local, dev, capacity, args) if args.served_requests > 0 else None
+    served = run_served_c5(local, dev, args) if args.served_requests > 0 else None
 
     launches_per_step = stats_b["kernel_launches"]
     line = {
@@ -527,7 +551,7 @@ def main(argv=None) -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--c4-frames", type=int, default=256)
     ap.add_argument("--served-requests", type=int, default=200)
-    ap.add_argument("--served-load", type=float, default=0.8)
+    ap.add_argument("--served-loads", type=float, nargs="*", default=[0.5, 0.8])
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -82,6 +82,7 @@ typedef struct {
   uint64_t timeout_ns;   /* served path: bound on device-side waits (0: 2 s) */
   const char* tune_cache;/* autotuner cache file, or NULL for in-memory only */
   uint32_t flags;        /* DH_CFG_* */
+  uint32_t wave_us;      /* served path: target device time of one wave in microseconds (0: 6000) */
 } dh_config;
 
 typedef struct {

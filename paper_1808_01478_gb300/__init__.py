@@ -45,7 +45,7 @@ STATUS_NAMES = {0: "DH_OK", 1: "DH_PENDING", -1: "DH_ERR_INVALID", -2: "DH_ERR_N
 class dh_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("pool_bytes", ctypes.c_uint64),
                 ("max_inflight", ctypes.c_int32), ("timeout_ns", ctypes.c_uint64),
-                ("tune_cache", ctypes.c_char_p), ("flags", ctypes.c_uint32)]
+                ("tune_cache", ctypes.c_char_p), ("flags", ctypes.c_uint32), ("wave_us", ctypes.c_uint32)]
 
 
 class dh_frame(ctypes.Structure):
@@ -149,8 +149,8 @@ def dh_bin_thresholds(r_max: float, nbins: int) -> np.ndarray:
 
 
 def dh_create(device: int = 0, pool_bytes: int = 0, max_inflight: int = 0, timeout_ns: int = 0,
-              flags: int = 0) -> ctypes.c_void_p:
-    cfg = dh_config(device, pool_bytes, max_inflight, timeout_ns, None, flags)
+              flags: int = 0, wave_us: int = 0) -> ctypes.c_void_p:
+    cfg = dh_config(device, pool_bytes, max_inflight, timeout_ns, None, flags, wave_us)
     h = ctypes.c_void_p()
     _check(load_library().dh_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h
@@ -261,6 +261,7 @@ class FrameArgs:
             self.keep.append(c)
             cptr = c.ctypes.data if n else 0
             optr = out.ctypes.data if _is_torch(out) is False else out.data_ptr()
+        self.coords = coords
         if accumulate:
             flags |= DH_ACCUMULATE
         bx = np.zeros(9) if box is None else np.asarray(box, dtype=np.float64).reshape(9)
@@ -273,13 +274,15 @@ class Context:
     """One libdh context (device workspace, stream, threshold cache)."""
 
     def __init__(self, device: int = 0, **cfg):
+        self._inflight = {}
         self.handle = dh_create(device, **cfg)
         self.device = device
 
     def close(self):
         if self.handle:
-            dh_destroy(self.handle)
+            dh_destroy(self.handle)  # cancels and waits for every request still running
             self.handle = None
+            self._inflight.clear()
 
     def __enter__(self):
         return self
@@ -334,15 +337,23 @@ class Context:
         return {"max_ratio": float(out[0]), "violations": int(out[1]), "checked": int(out[2]),
                 "delta": float(out[3])}
 
-    # served path
+    # served path: the buffers of a submitted request are held here until its
+    # final status has been reported (the library reads and writes them until then)
     def submit(self, fa: FrameArgs) -> int:
-        return dh_submit(self.handle, fa.frame)
+        t = dh_submit(self.handle, fa.frame)
+        self._inflight[t] = fa
+        return t
+
+    def _final(self, ticket: int, status: int) -> int:
+        if status != DH_PENDING and not (status == DH_ERR_TIMEOUT):
+            self._inflight.pop(ticket, None)
+        return status
 
     def poll(self, ticket: int) -> int:
-        return dh_poll(self.handle, ticket)
+        return self._final(ticket, dh_poll(self.handle, ticket))
 
     def wait(self, ticket: int, timeout_ns: int = 60_000_000_000) -> int:
-        return dh_wait(self.handle, ticket, timeout_ns)
+        return self._final(ticket, dh_wait(self.handle, ticket, timeout_ns))
 
     def cancel(self, ticket: int) -> int:
         return dh_cancel(self.handle, ticket)

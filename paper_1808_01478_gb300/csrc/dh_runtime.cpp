@@ -107,6 +107,7 @@ dh_status ThresholdCache::acquire(double r_max, int32_t nbins, cudaStream_t st, 
   if (it != map_.end()) {
     it->second.refs++;
     it->second.last = ++tick_;
+    if (it->second.built_on != st) DH_CUDA_TRY(cudaStreamWaitEvent(st, it->second.ready, 0));
     *T = it->second.T;
     return DH_OK;
   }
@@ -116,16 +117,21 @@ dh_status ThresholdCache::acquire(double r_max, int32_t nbins, cudaStream_t st, 
     for (auto e = map_.begin(); e != map_.end(); ++e)
       if (e->second.refs == 0 && (victim == map_.end() || e->second.last < victim->second.last)) victim = e;
     if (victim == map_.end()) break;
+    cudaStreamWaitEvent(st, victim->second.ready, 0);
     cudaFreeAsync(victim->second.T, st);
+    cudaEventDestroy(victim->second.ready);
     rev_.erase(victim->second.T);
     map_.erase(victim);
   }
   double* t = nullptr;
+  cudaEvent_t ev = nullptr;
   // binary64 thresholds followed by their float-pair copy
   DH_CUDA_TRY(cudaMallocAsync((void**)&t, 2 * sizeof(double) * (size_t)(nbins + 1), st));
   DH_CUDA_TRY(launch_thresholds(r_max, nbins, t, status_dev, st));
+  DH_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  DH_CUDA_TRY(cudaEventRecord(ev, st));
   if (launched) ++*launched;
-  map_[key] = Entry{t, 1, ++tick_};
+  map_[key] = Entry{t, 1, ++tick_, st, ev};
   rev_[t] = key;
   *T = t;
   return DH_OK;
@@ -141,7 +147,11 @@ void ThresholdCache::release(const double* T) {
 
 void ThresholdCache::clear(cudaStream_t st) {
   std::lock_guard<std::mutex> g(mu_);
-  for (auto& kv : map_) cudaFreeAsync(kv.second.T, st);
+  for (auto& kv : map_) {
+    cudaStreamWaitEvent(st, kv.second.ready, 0);
+    cudaFreeAsync(kv.second.T, st);
+    cudaEventDestroy(kv.second.ready);
+  }
   map_.clear();
   rev_.clear();
 }

@@ -47,8 +47,9 @@ struct HostBuf {
 
 // Binary64 bin-threshold tables per (r_max, nbins), shared by all paths of a
 // context.  acquire() returns a table (building it on `st` if missing) and
-// holds a reference; release() drops it.  Unreferenced tables beyond the cap
-// are freed stream-ordered.
+// holds a reference; release() drops it.  A table built on one stream is made
+// visible to work on another stream through an event wait.  Unreferenced tables
+// beyond the cap are freed stream-ordered.
 class ThresholdCache {
  public:
   dh_status acquire(double r_max, int32_t nbins, cudaStream_t st, int32_t* status_dev, double** T,
@@ -66,6 +67,8 @@ class ThresholdCache {
     double* T;
     int refs;
     uint64_t last;
+    cudaStream_t built_on;  // stream of the build kernel
+    cudaEvent_t ready;      // recorded after it; other streams wait on it
   };
   std::mutex mu_;
   std::map<Key, Entry> map_;

@@ -8,9 +8,12 @@
 // budget sized for a few milliseconds).  A request that arrives while others
 // run is admitted as soon as pool memory and a slot are free, and its items
 // join the next wave next to the remaining items of the running requests, so
-// small frames are not stuck behind large ones.  All device work of the served
-// path is on one stream; completion is observed with CUDA events polled by the
-// scheduler, so no kernel ever waits on the host.
+// small frames are not stuck behind large ones.  Each minimum-image variant
+// (no box, orthorhombic, triclinic, triclinic with image search) has its own
+// lane: a stream and a pipeline of waves, so the kernels of different lanes
+// overlap on the device and fill each other's launch tails.  Completion is
+// observed with CUDA events polled by the scheduler, so no kernel ever waits on
+// the host.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,7 +39,7 @@ using Clock = std::chrono::steady_clock;
 constexpr size_t kAlign = 256;
 constexpr int kWaveSlots = 4;          // waves that may be in flight at once
 constexpr int kWavesAhead = 2;         // waves kept enqueued ahead of the GPU
-constexpr double kWaveSeconds = 0.006; // target device time of one wave
+constexpr double kWaveSecondsDefault = 0.006;  // target device time of one wave
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -135,6 +138,16 @@ struct WaveSlot {
   double pairs = 0;
 };
 
+// One minimum-image variant: its stream and its pipeline of waves.
+struct Lane {
+  cudaStream_t stream = nullptr;
+  WaveSlot slots[kWaveSlots];
+  std::deque<int> inflight;  // slot indices in launch order
+  uint64_t wave_seq = 0, done_seq = 0;
+  double rate = 1.0e12;      // measured pairs/s of recent waves
+  DevBuf tstat;              // threshold build status
+};
+
 }  // namespace
 
 class Server {
@@ -152,7 +165,7 @@ class Server {
  private:
   void loop();
   void admit();
-  bool launch_wave();
+  bool launch_wave(int v);
   void reap();
   dh_status prep(Request& r);
   dh_status finalize_enqueue(Request& r);
@@ -161,16 +174,12 @@ class Server {
 
   dh_ctx* ctx_;
   int device_ = 0;
-  cudaStream_t stream_ = nullptr;
   void* pool_ = nullptr;
   void* pinned_ = nullptr;
   Arena dev_arena_, pin_arena_;
-  DevBuf tstat_;
   int max_inflight_ = 64;
-  WaveSlot slots_[kWaveSlots];
-  uint64_t wave_seq_ = 0, done_seq_ = 0;
-  std::deque<int> inflight_;  // slot indices in launch order
-  double rate_ = 1.0e12;      // measured pairs/s of recent waves
+  double wave_seconds_ = kWaveSecondsDefault;
+  Lane lanes_[kNumVariants];
 
   std::mutex mu_;
   std::condition_variable cv_work_, cv_done_;
@@ -186,7 +195,6 @@ class Server {
 dh_status Server::start() {
   device_ = ctx_->device;
   DH_CUDA_TRY(cudaSetDevice(device_));
-  DH_CUDA_TRY(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
   size_t free_b = 0, total_b = 0;
   DH_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   size_t pool = ctx_->cfg.pool_bytes ? (size_t)ctx_->cfg.pool_bytes
@@ -197,13 +205,17 @@ dh_status Server::start() {
   size_t pin = std::min<size_t>(std::max<size_t>(pool / 8, (size_t)64 << 20), (size_t)512 << 20);
   DH_CUDA_TRY(cudaMallocHost(&pinned_, pin));
   pin_arena_.init(pin);
-  DH_CUDA_TRY(tstat_.ensure(64));
-  DH_CUDA_TRY(cudaMemsetAsync(tstat_.p, 0, 64, stream_));
   max_inflight_ = ctx_->cfg.max_inflight > 0 ? ctx_->cfg.max_inflight : 64;
-  for (auto& s : slots_) {
-    DH_CUDA_TRY(s.ctl.ensure(sizeof(Control) * kNumVariants));
-    DH_CUDA_TRY(cudaEventCreate(&s.ev0));
-    DH_CUDA_TRY(cudaEventCreate(&s.ev1));
+  if (ctx_->cfg.wave_us) wave_seconds_ = 1e-6 * (double)ctx_->cfg.wave_us;
+  for (Lane& ln : lanes_) {
+    DH_CUDA_TRY(cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking));
+    DH_CUDA_TRY(ln.tstat.ensure(64));
+    DH_CUDA_TRY(cudaMemsetAsync(ln.tstat.p, 0, 64, ln.stream));
+    for (auto& w : ln.slots) {
+      DH_CUDA_TRY(w.ctl.ensure(sizeof(Control)));
+      DH_CUDA_TRY(cudaEventCreate(&w.ev0));
+      DH_CUDA_TRY(cudaEventCreate(&w.ev1));
+    }
   }
   th_ = std::thread([this] { loop(); });
   return DH_OK;
@@ -219,7 +231,8 @@ void Server::shutdown() {
   }
   cv_work_.notify_all();
   if (th_.joinable()) th_.join();
-  if (stream_) cudaStreamSynchronize(stream_);
+  for (Lane& ln : lanes_)
+    if (ln.stream) cudaStreamSynchronize(ln.stream);
   std::lock_guard<std::mutex> g(mu_);
   for (Request* r : active_) {
     release_resources(*r);
@@ -229,20 +242,22 @@ void Server::shutdown() {
   for (auto& kv : all_)
     if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
   all_.clear();
-  for (auto& s : slots_) {
-    s.segs.release();
-    s.hsegs.release();
-    s.ctl.release();
-    if (s.ev0) cudaEventDestroy(s.ev0);
-    if (s.ev1) cudaEventDestroy(s.ev1);
-    s.ev0 = s.ev1 = nullptr;
+  for (Lane& ln : lanes_) {
+    for (auto& w : ln.slots) {
+      w.segs.release();
+      w.hsegs.release();
+      w.ctl.release();
+      if (w.ev0) cudaEventDestroy(w.ev0);
+      if (w.ev1) cudaEventDestroy(w.ev1);
+      w.ev0 = w.ev1 = nullptr;
+    }
+    ln.tstat.release();
+    if (ln.stream) cudaStreamDestroy(ln.stream);
+    ln.stream = nullptr;
   }
-  tstat_.release();
   if (pool_) cudaFree(pool_);
   if (pinned_) cudaFreeHost(pinned_);
   pool_ = pinned_ = nullptr;
-  if (stream_) cudaStreamDestroy(stream_);
-  stream_ = nullptr;
   cv_done_.notify_all();
 }
 
@@ -391,7 +406,9 @@ void Server::admit() {
 
 // Enqueue the per-request preparation: uploads, thresholds, staging, window setup.
 dh_status Server::prep(Request& r) {
-  dh_status s = ctx_->tcache.acquire(r.frame.r_max, r.frame.nbins, stream_, (int32_t*)tstat_.p, &r.T, nullptr);
+  Lane& ln = lanes_[r.pf.variant];
+  cudaStream_t st = ln.stream;
+  dh_status s = ctx_->tcache.acquire(r.frame.r_max, r.frame.nbins, st, (int32_t*)ln.tstat.p, &r.T, nullptr);
   if (s != DH_OK) return s;
   fill_frame_dev(r.pf, *r.fd_pin, r.X, r.hist, r.T);
   std::memset(r.job_pin, 0, sizeof(StageJob));
@@ -401,62 +418,66 @@ dh_status Server::prep(Request& r) {
   r.job_pin->n = r.frame.n;
   r.job_pin->stride = r.stride;
   r.job_pin->chunk0 = 0;
-  DH_CUDA_TRY(cudaMemcpyAsync(r.fd, r.fd_pin, sizeof(FrameDev), cudaMemcpyHostToDevice, stream_));
-  DH_CUDA_TRY(cudaMemcpyAsync(r.job_dev, r.job_pin, sizeof(StageJob), cudaMemcpyHostToDevice, stream_));
+  DH_CUDA_TRY(cudaMemcpyAsync(r.fd, r.fd_pin, sizeof(FrameDev), cudaMemcpyHostToDevice, st));
+  DH_CUDA_TRY(cudaMemcpyAsync(r.job_dev, r.job_pin, sizeof(StageJob), cudaMemcpyHostToDevice, st));
   if (!r.dev_ptrs && r.frame.n > 0)
     DH_CUDA_TRY(cudaMemcpyAsync(r.raw, r.raw_pin, 4 * (size_t)r.stride * (size_t)r.frame.n,
-                                cudaMemcpyHostToDevice, stream_));
+                                cudaMemcpyHostToDevice, st));
   if (!r.dev_ptrs || !(r.frame.flags & DH_ACCUMULATE))
-    DH_CUDA_TRY(cudaMemsetAsync(r.hist, 0, 8 * r.res_count, stream_));
+    DH_CUDA_TRY(cudaMemsetAsync(r.hist, 0, 8 * r.res_count, st));
   int64_t chunks = (r.frame.n + kStageChunk - 1) / kStageChunk;
-  if (chunks > 0) DH_CUDA_TRY(launch_stage(r.job_dev, 1, chunks, stream_));
-  DH_CUDA_TRY(launch_frame_setup(r.fd, 1, 0, stream_));
+  if (chunks > 0) DH_CUDA_TRY(launch_stage(r.job_dev, 1, chunks, st));
+  DH_CUDA_TRY(launch_frame_setup(r.fd, 1, 0, st));
   r.prepped = true;
   return DH_OK;
 }
 
 // After the request's last wave: read back its flags and (host outputs) histograms.
 dh_status Server::finalize_enqueue(Request& r) {
-  DH_CUDA_TRY(cudaMemcpyAsync(r.fd_pin, r.fd, sizeof(FrameDev), cudaMemcpyDeviceToHost, stream_));
+  cudaStream_t st = lanes_[r.pf.variant].stream;
+  DH_CUDA_TRY(cudaMemcpyAsync(r.fd_pin, r.fd, sizeof(FrameDev), cudaMemcpyDeviceToHost, st));
   if (!r.dev_ptrs)
-    DH_CUDA_TRY(cudaMemcpyAsync(r.res_pin, r.hist, 8 * r.res_count, cudaMemcpyDeviceToHost, stream_));
+    DH_CUDA_TRY(cudaMemcpyAsync(r.res_pin, r.hist, 8 * r.res_count, cudaMemcpyDeviceToHost, st));
   if (!r.done_ev) DH_CUDA_TRY(cudaEventCreateWithFlags(&r.done_ev, cudaEventDisableTiming));
-  DH_CUDA_TRY(cudaEventRecord(r.done_ev, stream_));
+  DH_CUDA_TRY(cudaEventRecord(r.done_ev, st));
   r.finalize_enqueued = true;
   return DH_OK;
 }
 
-// One wave: a fair share of the pair budget from every running request.
-bool Server::launch_wave() {
+// One wave of lane v: a fair share of the lane's pair budget from every
+// running request of that variant, as one pair-kernel launch.
+bool Server::launch_wave(int v) {
+  Lane& ln = lanes_[v];
   int slot = -1;
   for (int k = 0; k < kWaveSlots; ++k)
-    if (!slots_[k].busy) {
+    if (!ln.slots[k].busy) {
       slot = k;
       break;
     }
   if (slot < 0) return false;
   std::vector<Request*> run;
-  for (Request* r : active_)
-    if (!r->cancel && r->next < r->n_items) run.push_back(r);
-  // requests with nothing to compute (no pairs) still need their preparation and read-back
   for (Request* r : active_) {
-    if (r->cancel || r->finalize_enqueued || r->n_items > 0) continue;
-    dh_status s = r->prepped ? DH_OK : prep(*r);
-    if (s == DH_OK) s = finalize_enqueue(*r);
-    if (s != DH_OK) {
-      r->cancel = true;
-      r->error = last_error_message();
+    if (r->pf.variant != v || r->cancel) continue;
+    if (r->next < r->n_items) {
+      run.push_back(r);
+    } else if (!r->finalize_enqueued && r->n_items == 0) {
+      // nothing to compute (no pairs): preparation and read-back only
+      dh_status s = r->prepped ? DH_OK : prep(*r);
+      if (s == DH_OK) s = finalize_enqueue(*r);
+      if (s != DH_OK) {
+        r->cancel = true;
+        r->error = last_error_message();
+      }
     }
   }
   if (run.empty()) return false;
-  WaveSlot& W = slots_[slot];
-  double budget = rate_ * kWaveSeconds;
-  double share = budget / (double)run.size();
+  WaveSlot& W = ln.slots[slot];
+  const double budget = ln.rate * wave_seconds_;
+  const double share = budget / (double)run.size();
   const double pairs_per_item = (double)kTile * (double)kTile;
-  // wave segments grouped by minimum-image variant (one pair-kernel launch each)
-  std::vector<Segment> vsegs[kNumVariants];
-  int64_t vitems[kNumVariants] = {0, 0, 0, 0};
-  int vwidth[kNumVariants] = {1, 1, 1, 1};
+  std::vector<Segment> wsegs;
+  int64_t witems = 0;
+  int width = 1;
   double wpairs = 0;
   std::vector<Request*> finishing;
   for (Request* r : run) {
@@ -468,62 +489,50 @@ bool Server::launch_wave() {
         continue;
       }
     }
-    int v = r->pf.variant;
     int64_t take = std::max<int64_t>(1, (int64_t)(share / pairs_per_item));
     take = std::min(take, r->n_items - r->next);
     int64_t lo = r->next, hi = r->next + take;
-    for (const Segment& s : r->segs) {
-      int64_t count = s.intra ? (int64_t)s.n_ti * (s.n_ti + 1) / 2 : (int64_t)s.n_ti * s.n_tj;
-      int64_t a = std::max(lo, s.item0), b = std::min(hi, s.item0 + count);
+    for (const Segment& sg : r->segs) {
+      int64_t count = sg.intra ? (int64_t)sg.n_ti * (sg.n_ti + 1) / 2 : (int64_t)sg.n_ti * sg.n_tj;
+      int64_t a = std::max(lo, sg.item0), b = std::min(hi, sg.item0 + count);
       if (a >= b) continue;
-      Segment w = s;
-      w.item0 = vitems[v];
-      w.item_base = a - s.item0;
-      vitems[v] += b - a;
-      vsegs[v].push_back(w);
+      Segment w = sg;
+      w.item0 = witems;
+      w.item_base = a - sg.item0;
+      witems += b - a;
+      wsegs.push_back(w);
     }
     r->next = hi;
-    r->last_wave = wave_seq_ + 1;
-    vwidth[v] = std::max(vwidth[v], r->pf.sweep_width);
+    r->last_wave = ln.wave_seq + 1;
+    width = std::max(width, r->pf.sweep_width);
     wpairs += (double)std::min<uint64_t>(r->pf.pairs, (uint64_t)((double)take * pairs_per_item));
     if (r->next >= r->n_items) finishing.push_back(r);
   }
-  size_t nseg = 0;
-  for (int v = 0; v < kNumVariants; ++v) nseg += vsegs[v].size();
-  if (nseg == 0) return false;
-  size_t bytes = sizeof(Segment) * nseg;
+  if (witems == 0) return false;
+  size_t bytes = sizeof(Segment) * wsegs.size();
   if (W.segs.ensure(bytes) != cudaSuccess || W.hsegs.ensure(bytes) != cudaSuccess) {
     thread_error_ = "out of memory for wave descriptors";
     return false;
   }
-  size_t at = 0;
-  size_t vat[kNumVariants];
-  for (int v = 0; v < kNumVariants; ++v) {
-    vat[v] = at;
-    if (!vsegs[v].empty()) std::memcpy((Segment*)W.hsegs.p + at, vsegs[v].data(), sizeof(Segment) * vsegs[v].size());
-    at += vsegs[v].size();
-  }
-  cudaMemcpyAsync(W.segs.p, W.hsegs.p, bytes, cudaMemcpyHostToDevice, stream_);
-  cudaMemsetAsync(W.ctl.p, 0, sizeof(Control) * kNumVariants, stream_);
-  cudaEventRecord(W.ev0, stream_);
-  for (int v = 0; v < kNumVariants; ++v) {
-    if (vitems[v] == 0) continue;
-    PairLaunch L;
-    std::memset(&L, 0, sizeof L);
-    L.segs = (const Segment*)W.segs.p + vat[v];
-    L.n_segs = (int32_t)vsegs[v].size();
-    L.n_items = vitems[v];
-    L.hist_width = vwidth[v];
-    L.ctl = (Control*)W.ctl.p + v;
-    int bps = pair_kernel_blocks_per_sm(v, vwidth[v]);
-    cudaError_t e = launch_pairs(L, v, pair_grid(ctx_->num_sms, bps, vitems[v]), pair_kernel_smem(vwidth[v]), stream_);
-    if (e != cudaSuccess) thread_error_ = cudaGetErrorString(e);
-  }
-  cudaEventRecord(W.ev1, stream_);
+  std::memcpy(W.hsegs.p, wsegs.data(), bytes);
+  cudaMemcpyAsync(W.segs.p, W.hsegs.p, bytes, cudaMemcpyHostToDevice, ln.stream);
+  cudaMemsetAsync(W.ctl.p, 0, sizeof(Control), ln.stream);
+  PairLaunch L;
+  std::memset(&L, 0, sizeof L);
+  L.segs = (const Segment*)W.segs.p;
+  L.n_segs = (int32_t)wsegs.size();
+  L.n_items = witems;
+  L.hist_width = width;
+  L.ctl = (Control*)W.ctl.p;
+  int bps = pair_kernel_blocks_per_sm(v, width);
+  cudaEventRecord(W.ev0, ln.stream);
+  cudaError_t e = launch_pairs(L, v, pair_grid(ctx_->num_sms, bps, witems), pair_kernel_smem(width), ln.stream);
+  cudaEventRecord(W.ev1, ln.stream);
+  if (e != cudaSuccess) thread_error_ = cudaGetErrorString(e);
   W.busy = true;
-  W.seq = ++wave_seq_;
+  W.seq = ++ln.wave_seq;
   W.pairs = wpairs;
-  inflight_.push_back(slot);
+  ln.inflight.push_back(slot);
   for (Request* r : finishing)
     if (finalize_enqueue(*r) != DH_OK) {
       r->cancel = true;
@@ -533,17 +542,19 @@ bool Server::launch_wave() {
 }
 
 void Server::reap() {
-  while (!inflight_.empty()) {
-    WaveSlot& W = slots_[inflight_.front()];
-    cudaError_t q = cudaEventQuery(W.ev1);
-    if (q == cudaErrorNotReady) break;
-    if (q != cudaSuccess) thread_error_ = cudaGetErrorString(q);
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, W.ev0, W.ev1) == cudaSuccess && ms > 0.05f && W.pairs > 0)
-      rate_ = 0.7 * rate_ + 0.3 * (W.pairs / (ms * 1e-3));
-    done_seq_ = W.seq;
-    W.busy = false;
-    inflight_.pop_front();
+  for (Lane& ln : lanes_) {
+    while (!ln.inflight.empty()) {
+      WaveSlot& W = ln.slots[ln.inflight.front()];
+      cudaError_t q = cudaEventQuery(W.ev1);
+      if (q == cudaErrorNotReady) break;
+      if (q != cudaSuccess) thread_error_ = cudaGetErrorString(q);
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, W.ev0, W.ev1) == cudaSuccess && ms > 0.05f && W.pairs > 0)
+        ln.rate = 0.7 * ln.rate + 0.3 * (W.pairs / (ms * 1e-3));
+      ln.done_seq = W.seq;
+      W.busy = false;
+      ln.inflight.pop_front();
+    }
   }
   for (size_t k = 0; k < active_.size();) {
     Request& r = *active_[k];
@@ -570,7 +581,7 @@ void Server::reap() {
         finished = true;
         complete(r, DH_ERR_CUDA, cudaGetErrorString(q));
       }
-    } else if (r.cancel && r.last_wave <= done_seq_) {
+    } else if (r.cancel && r.last_wave <= lanes_[r.pf.variant].done_seq) {
       finished = true;  // no work of it left on the device
       complete(r, r.error.empty() ? DH_ERR_CANCELLED : DH_ERR_CUDA,
                r.error.empty() ? "cancelled" : r.error.c_str());
@@ -590,10 +601,12 @@ void Server::loop() {
   while (!stop_) {
     reap();
     admit();
-    while ((int)inflight_.size() < kWavesAhead && launch_wave()) {
-    }
+    for (int v = 0; v < kNumVariants; ++v)
+      while ((int)lanes_[v].inflight.size() < kWavesAhead && launch_wave(v)) {
+      }
     reap();
-    bool busy = !inflight_.empty();
+    bool busy = false;
+    for (Lane& ln : lanes_) busy |= !ln.inflight.empty();
     for (Request* r : active_)
       if (r->finalize_enqueued || r->cancel) busy = true;
     if (busy) {
