@@ -15,7 +15,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libdh.so")
+# DH_LIB_PATH selects another build of the same library (for example a debug build)
+LIB_PATH = os.environ.get("DH_LIB_PATH") or os.path.join(_HERE, "_lib", "libdh.so")
 
 DH_OK = 0
 DH_PENDING = 1

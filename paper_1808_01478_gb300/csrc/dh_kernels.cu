@@ -449,9 +449,11 @@ __device__ __forceinline__ float2 wrap_r2_2(float2 dx, float2 dy, float2 dz, con
 // sm = s + 1.5*2^23 (bits(sm) - kbase = nearest integer - lo) and the residual
 // e = n^2 - q (e > 0: t < n, so floor(t) = n - 1), the pair is decided in float32
 // when |e| > bound (false for NaN); a decided pair inside this sweep increments
-// its shared-memory bin, an undecided one sets the bits `bit` of dmask.
+// its shared-memory bin, an undecided one sets the bits `bit` of dmask.  Every
+// pair issues its increment: pairs not counted here add to a scratch word of
+// their lane (never read), which keeps the sequence free of branches.
 __device__ __forceinline__ void count_or_defer(float sm, float e, float bound, int kbase, uint32_t width,
-                                               uint32_t sbase, uint32_t bit, uint32_t& dmask) {
+                                               uint32_t sbase, uint32_t bit, uint32_t nulladdr, uint32_t& dmask) {
   asm volatile(
       "{\n\t.reg .pred pp, pn, pc;\n\t.reg .u32 rel, addr;\n\t.reg .f32 ae;\n\t"
       "sub.u32 rel, %1, %2;\n\t"
@@ -462,10 +464,12 @@ __device__ __forceinline__ void count_or_defer(float sm, float e, float bound, i
       "setp.lt.and.u32 pc, rel, %5, pn;\n\t"
       "@!pn or.b32 %0, %0, %7;\n\t"
       "mad.lo.u32 addr, rel, 4, %6;\n\t"
-      "@pc red.shared.add.u32 [addr], 1;\n\t"
+      "selp.u32 addr, addr, %8, pc;\n\t"
+      "red.shared.add.u32 [addr], 1;\n\t"
       "}"
       : "+r"(dmask)
-      : "r"(__float_as_uint(sm)), "r"(kbase), "f"(e), "f"(bound), "r"(width), "r"(sbase), "r"(bit));
+      : "r"(__float_as_uint(sm)), "r"(kbase), "f"(e), "f"(bound), "r"(width), "r"(sbase), "r"(bit),
+        "r"(nulladdr));
 }
 
 // The float32 decision of two pairs (j, j+1 against one i).  With q = r^2 S^2
@@ -693,6 +697,8 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
   const unsigned lt_mask = (1u << lane) - 1u;
   const float qnan = __int_as_float(0x7fffffff);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sh);
+  // one scratch word per lane right after the j tile, for increments of pairs not counted
+  const uint32_t nulladdr = (uint32_t)__cvta_generic_to_shared(sjZ + kTile / 2) + 4u * (uint32_t)lane;
   const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);  // the j tile is padded with NaN particles
   int qcount = 0;
   for (int jj0 = 0; jj0 < nj4; jj0 += kJU) {
@@ -716,8 +722,8 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
         }
         float2 sm, e, bound;
         decide_arith2<V>(dx, dy, dz, P, sm, e, bound);
-        count_or_defer(sm.x, e.x, bound.x, P.kbase, P.width, sbase, 1u << (u * kRegI + r), dmask);
-        count_or_defer(sm.y, e.y, bound.y, P.kbase, P.width, sbase, 1u << ((u + 1) * kRegI + r), dmask);
+        count_or_defer(sm.x, e.x, bound.x, P.kbase, P.width, sbase, 1u << (u * kRegI + r), nulladdr, dmask);
+        count_or_defer(sm.y, e.y, bound.y, P.kbase, P.width, sbase, 1u << ((u + 1) * kRegI + r), nulladdr, dmask);
       }
     }
     // queue the deferred pairs: one per lane per round, compacted with a ballot
@@ -837,7 +843,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(Pa
   uint32_t* sh = reinterpret_cast<uint32_t*>(smem_raw);
   float4* sjA = reinterpret_cast<float4*>(sh + width_pad);
   float2* sjZ = reinterpret_cast<float2*>(sjA + kTile / 2);
-  uint2* sq = reinterpret_cast<uint2*>(sjZ + kTile / 2);
+  uint2* sq = reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(sjZ + kTile / 2) + 128);
   __shared__ ItemDesc s_it;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1022,7 +1028,7 @@ cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t 
 
 size_t pair_kernel_smem(int hist_width) {
   size_t w = (size_t)((hist_width + 3) & ~3);
-  return w * 4 + (size_t)kTile * 12 + (size_t)kWarps * kQueueCap * 8;
+  return w * 4 + (size_t)kTile * 12 + 128 + (size_t)kWarps * kQueueCap * 8;
 }
 
 int pair_kernel_max_width() {
