@@ -98,7 +98,9 @@ typedef struct {
   uint32_t flags;                  /* DH_DEVICE_PTRS | DH_ACCUMULATE | DH_COORDS_F4 */
 } dh_frame;
 
-#define DH_MAX_BINS 4194304
+/* 2^22 - 64: the float32 bin coordinate, clamped a few bins beyond the last
+   one, must stay below 2^22 for its nearest-integer step to be exact. */
+#define DH_MAX_BINS 4194240
 
 /* Per-context statistics of the most recent dh_histogram / dh_histogram_batch call. */
 typedef struct {

@@ -36,7 +36,7 @@ DH_ACCUMULATE = 0x2
 DH_COORDS_F4 = 0x4
 DH_CFG_NO_GRAPH = 0x1
 DH_CFG_TIMING = 0x2
-DH_MAX_BINS = 4194304
+DH_MAX_BINS = 4194240
 
 STATUS_NAMES = {0: "DH_OK", 1: "DH_PENDING", -1: "DH_ERR_INVALID", -2: "DH_ERR_NOMEM",
                 -3: "DH_ERR_CUDA", -4: "DH_ERR_TIMEOUT", -5: "DH_ERR_CANCELLED",

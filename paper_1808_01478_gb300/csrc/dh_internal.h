@@ -96,9 +96,11 @@ struct Control {
 struct PairLaunch {
   const Segment* segs;
   int32_t n_segs;
-  int32_t hist_width;  // shared-memory bins per block
+  int32_t hist_width;  // shared-memory bins per histogram copy (the widest sweep of the launch)
   int64_t n_items;
   Control* ctl;
+  int32_t hist_depth;  // private histogram copies per block (warp w uses copy w mod depth); 0 means 1
+  int32_t multi;       // nonzero when some sweep of the launch starts above bin 0
 };
 
 // ---- launchers (dh_kernels.cu); all enqueue on `stream` and return the launch error
@@ -111,9 +113,9 @@ cudaError_t launch_pairs(const PairLaunch& p, int variant, int grid, size_t smem
 cudaError_t launch_check_sqrt(unsigned long long* out, cudaStream_t stream);
 cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t seed, unsigned long long* out,
                                 cudaStream_t stream);
-size_t pair_kernel_smem(int hist_width);
+size_t pair_kernel_smem(int hist_width, int depth = 1);
 int pair_kernel_max_width();
-int pair_kernel_blocks_per_sm(int variant, int hist_width);
+int pair_kernel_blocks_per_sm(int variant, int hist_width, int depth = 1);
 
 // Host/device shared definition of the binary64 bin of Alg. 1 (used to build thresholds).
 int64_t host_bin_of(double r2, double r_max, int32_t nbins);

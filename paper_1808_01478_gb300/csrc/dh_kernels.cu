@@ -340,13 +340,17 @@ constexpr int kJU = 4;  // j particles per deferral-mask group (mask bit = u * k
 struct FastParams {
   float S2;
   float qb1, qb0;       // near-edge bound |n^2 - q| <= qb1*(q or s) + qb0 (q for V_NONE, s otherwise)
-  int32_t kbase;        // bits(kMagicRound) + lo
+  int32_t kb1;          // bits(kMagicRound) + lo + 1
   uint32_t width;       // hi - lo
-  int32_t lo;
+  int32_t lo, hi;       // bins [lo, hi) of this sweep
   float b[9];
   float inv[3];
   float amb_thr;        // search variant: 0.5 - eps_s
 };
+
+// Guard words on each side of a shared-memory histogram copy: the increments
+// of pairs outside [lo, hi) land there (see count_or_defer).
+constexpr int kGuard = 36;
 
 struct ItemDesc {
   FrameDev* fd;
@@ -445,49 +449,57 @@ __device__ __forceinline__ float2 wrap_r2_2(float2 dx, float2 dy, float2 dz, con
   return fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
 }
 
-// Count or defer one pair, branch free: with rel = floor(t) - lo computed from
-// sm = s + 1.5*2^23 (bits(sm) - kbase = nearest integer - lo) and the residual
-// e = n^2 - q (e > 0: t < n, so floor(t) = n - 1), the pair is decided in float32
-// when |e| > bound (false for NaN); a decided pair inside this sweep increments
-// its shared-memory bin, an undecided one sets the bits `bit` of dmask.  Every
-// pair issues its increment: pairs not counted here add to a scratch word of
-// their lane (never read), which keeps the sequence free of branches.
-__device__ __forceinline__ void count_or_defer(float sm, float e, float bound, int kbase, uint32_t width,
-                                               uint32_t sbase, uint32_t bit, uint32_t nulladdr, uint32_t& dmask) {
+// Count one pair, branch free.  With sm = s_c + 1.5*2^23 (s_c the clamped root,
+// bits(sm) - bits(1.5*2^23) = its nearest integer n) and the residual
+// e = n^2 - q (e > 0: t < n, so floor(t) = n - 1; e < 0: floor(t) = n), the
+// bin relative to the sweep is v - kb1 with v = bits(sm) + signbit(e), and the
+// shared-memory address is 4 v + hbase.  Every pair increments that word.  The
+// clamp of s_c to [lo - lane, hi + 1 + lane] (integers below 2^22) keeps the
+// relative bin in [-1 - lane, width + 1 + lane]: pairs outside the sweep, and
+// NaN pairs (s_c = hi + 1 + lane, e NaN with a clear sign bit: bin width + lane),
+// land in the guard words, spread over the lanes.  A clamped pair that is
+// decided is decided right: e > bound means t lies within the clamp's integer
+// and the one below, e < -bound that t lies above it, out of the sweep (and
+// the converse at the lower clamp).  A pair with |e| <= bound (false for NaN)
+// also sets the bit `bit` of dmask: it is counted provisionally and re-decided
+// by the drain, which moves its count to the exact bin when the two differ.
+__device__ __forceinline__ void count_or_defer(float sm, float e, float bound, uint32_t hbase, uint32_t bit,
+                                               uint32_t& dmask) {
   asm volatile(
-      "{\n\t.reg .pred pp, pn, pc;\n\t.reg .u32 rel, addr;\n\t.reg .f32 ae;\n\t"
-      "sub.u32 rel, %1, %2;\n\t"
-      "setp.gt.f32 pp, %3, 0f00000000;\n\t"
-      "@pp sub.u32 rel, rel, 1;\n\t"
-      "abs.f32 ae, %3;\n\t"
-      "setp.gtu.f32 pn, ae, %4;\n\t"
-      "setp.lt.and.u32 pc, rel, %5, pn;\n\t"
-      "@!pn or.b32 %0, %0, %7;\n\t"
-      "mad.lo.u32 addr, rel, 4, %6;\n\t"
-      "selp.u32 addr, addr, %8, pc;\n\t"
+      "{\n\t.reg .pred pn;\n\t.reg .u32 eb, sg, v, addr;\n\t.reg .f32 ae;\n\t"
+      "mov.b32 eb, %2;\n\t"
+      "shr.u32 sg, eb, 31;\n\t"
+      "add.u32 v, %1, sg;\n\t"
+      "mad.lo.u32 addr, v, 4, %4;\n\t"
+      "abs.f32 ae, %2;\n\t"
+      "setp.gtu.f32 pn, ae, %3;\n\t"
+      "@!pn or.b32 %0, %0, %5;\n\t"
       "red.shared.add.u32 [addr], 1;\n\t"
       "}"
       : "+r"(dmask)
-      : "r"(__float_as_uint(sm)), "r"(kbase), "f"(e), "f"(bound), "r"(width), "r"(sbase), "r"(bit),
-        "r"(nulladdr));
+      : "r"(__float_as_uint(sm)), "f"(e), "f"(bound), "r"(hbase), "r"(bit));
 }
 
 // The float32 decision of two pairs (j, j+1 against one i).  With q = r^2 S^2
-// (= t^2) and n the integer nearest to sqrt(q), the residual e = n^2 - q is
-// rounded once (fma), so its sign gives floor(t) = n or n-1, and |e| is
-// compared with the bound derived in frame_setup_kernel; within it the pair
-// is deferred.  NaN pairs are never deferred and never counted.
-// decide_arith2 returns sm = s + 1.5*2^23, e and the bound as float pairs
+// (= t^2) and n the integer nearest to the clamped root s_c, the residual
+// e = n^2 - q is rounded once (fma), so its sign gives floor(t) = n or n-1, and
+// |e| is compared with the bound derived in frame_setup_kernel; within it the
+// pair is deferred.  The clamp (chi = hi + 1 + lane, and clo = lo - lane for
+// sweeps that start above bin 0) sends far pairs to guard words with a large
+// |e|, so they are not deferred; NaN pairs are never deferred.
+// decide_arith2 returns sm = s_c + 1.5*2^23, e and the bound as float pairs
 // (search variant: ambiguous images force the bound to +inf so the pair is
 // deferred); count_or_defer acts on them.
-template <int V>
-__device__ __forceinline__ void decide_arith2(float2 dx, float2 dy, float2 dz, const FastParams& P, float2& sm,
-                                              float2& e, float2& bound) {
+template <int V, bool MULTI>
+__device__ __forceinline__ void decide_arith2(float2 dx, float2 dy, float2 dz, const FastParams& P, float chi,
+                                              float clo, float2& sm, float2& e, float2& bound) {
   bool amb_a = false, amb_b = false;
   float2 r2 = wrap_r2_2<V>(dx, dy, dz, P, amb_a, amb_b);
   float2 nq = mul2(r2, bc2(-P.S2));  // -q
   float2 sq = make_float2(sqrt_approx(-nq.x), sqrt_approx(-nq.y));
-  sm = add2(sq, bc2(kMagicRound));
+  float2 sc = make_float2(fminf(sq.x, chi), fminf(sq.y, chi));  // NaN -> chi
+  if (MULTI) sc = make_float2(fmaxf(sc.x, clo), fmaxf(sc.y, clo));
+  sm = add2(sc, bc2(kMagicRound));
   float2 n = add2(sm, bc2(-kMagicRound));
   e = fma2(n, n, nq);  // n^2 - q
   bound = (V == V_NONE) ? fma2(nq, bc2(-P.qb1), bc2(P.qb0)) : fma2(sq, bc2(P.qb1), bc2(P.qb0));
@@ -497,16 +509,33 @@ __device__ __forceinline__ void decide_arith2(float2 dx, float2 dy, float2 dz, c
   }
 }
 
-// The same decision as count_or_defer, as values (used by the self check).
+// The same decision as count_or_defer, as values (used by the self check;
+// single sweep, lane 0's clamp).
 template <int V>
 __device__ __forceinline__ void fast_decide2(float2 dx, float2 dy, float2 dz, const FastParams& P, bool& near_a,
                                              bool& near_b, uint32_t& rel_a, uint32_t& rel_b) {
   float2 sm, e, bound;
-  decide_arith2<V>(dx, dy, dz, P, sm, e, bound);
+  decide_arith2<V, false>(dx, dy, dz, P, (float)(P.hi + 1), 0.0f, sm, e, bound);
   near_a = fabsf(e.x) <= bound.x;
   near_b = fabsf(e.y) <= bound.y;
-  rel_a = (uint32_t)(__float_as_int(sm.x) - P.kbase - (e.x > 0.0f ? 1 : 0));
-  rel_b = (uint32_t)(__float_as_int(sm.y) - P.kbase - (e.y > 0.0f ? 1 : 0));
+  rel_a = __float_as_uint(sm.x) + (__float_as_uint(e.x) >> 31) - (uint32_t)P.kb1;
+  rel_b = __float_as_uint(sm.y) + (__float_as_uint(e.y) >> 31) - (uint32_t)P.kb1;
+}
+
+// The relative bin at which the float32 path counted a pair (provisionally,
+// if it deferred it): the scalar replay of decide_arith2 and count_or_defer,
+// operation for operation, for the lane `src_lane` that evaluated the pair.
+template <int V, bool MULTI>
+__device__ __forceinline__ int provisional_rel(const FastParams& P, float4 pi, float4 pj, int src_lane) {
+  bool amb = false;
+  float r2 = wrap_r2<V>(__fadd_rn(pj.x, -pi.x), __fadd_rn(pj.y, -pi.y), __fadd_rn(pj.z, -pi.z), P, amb);
+  float nq = __fmul_rn(r2, -P.S2);
+  float sc = fminf(sqrt_approx(-nq), (float)(P.hi + 1 + src_lane));
+  if (MULTI) sc = fmaxf(sc, (float)(P.lo - src_lane));
+  float sm = __fadd_rn(sc, kMagicRound);
+  float n = __fadd_rn(sm, -kMagicRound);
+  float e = __fmaf_rn(n, n, nq);
+  return (int)(__float_as_uint(sm) + (__float_as_uint(e) >> 31) - (uint32_t)P.kb1);
 }
 
 // ---- double-float middle tier
@@ -652,20 +681,29 @@ __device__ __forceinline__ int deferred_bin(const FrameDev& F, float4 pi, float4
   return k;
 }
 
-// Decide the first `count` (<= 32) queued pairs, one per lane, and shift the
+__device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P);
+
+// Decide the first `count` (<= 32) queued pairs, one per lane, move the
+// provisional count of each to its exact bin where they differ, and shift the
 // rest of the queue down.  Out of line so the hot loop keeps its registers.
-template <int V>
-__device__ __noinline__ int drain_queue(const FrameDev* F, int lo, uint32_t width, uint2* q, int qcount,
-                                        uint32_t* sh, int lane) {
+// i0 is the first i of the tile: lane (i - i0) mod 32 evaluated the pair.
+template <int V, bool MULTI>
+__device__ __noinline__ int drain_queue(const FrameDev* F, int pass, int i0, uint2* q, int qcount, uint32_t* sh,
+                                        int lane) {
   const int count = qcount < 32 ? qcount : 32;
   unsigned nexact = 0;
   if (lane < count) {
     uint2 e = q[lane];
     float4 pi = __ldg(F->X + e.x);
     float4 pj = __ldg(F->X + e.y);
-    int k = deferred_bin<V>(*F, pi, pj, nexact);
-    uint32_t rel = (uint32_t)(k - lo);
-    if (rel < width) atomicAdd(sh + rel, 1u);
+    FastParams P;
+    load_fast_params(*F, pass, P);
+    int relp = provisional_rel<V, MULTI>(P, pi, pj, (int)((e.x - (uint32_t)i0) & 31u));
+    int relx = deferred_bin<V>(*F, pi, pj, nexact) - P.lo;
+    if (relx != relp) {
+      atomicAdd(sh + relp, 0xFFFFFFFFu);  // relp lies in the histogram or its guard words
+      if ((uint32_t)relx < P.width) atomicAdd(sh + relx, 1u);
+    }
   }
   __syncwarp();
   int rest = qcount - count;
@@ -678,7 +716,7 @@ __device__ __noinline__ int drain_queue(const FrameDev* F, int lo, uint32_t widt
 
 // j tile in shared memory as pairs of particles: A[p] = {x_2p, x_2p+1, y_2p, y_2p+1},
 // Z[p] = {z_2p, z_2p+1}, so one LDS.128 + one LDS.64 feed two j particles.
-template <int V, bool MASKED>
+template <int V, bool MASKED, bool MULTI>
 __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
                                          const float4* __restrict__ sjA, const float2* __restrict__ sjZ,
                                          uint32_t* sh, uint2* q, int tid, int lane, unsigned& ndeferred) {
@@ -696,9 +734,10 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
   }
   const unsigned lt_mask = (1u << lane) - 1u;
   const float qnan = __int_as_float(0x7fffffff);
-  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sh);
-  // one scratch word per lane right after the j tile, for increments of pairs not counted
-  const uint32_t nulladdr = (uint32_t)__cvta_generic_to_shared(sjZ + kTile / 2) + 4u * (uint32_t)lane;
+  // address of bin rel = 4 (rel + kb1) + hbase (mod 2^32); clamp of the root per lane
+  const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(sh) - 4u * (uint32_t)P.kb1;
+  const float chi = (float)(P.hi + 1 + lane);
+  const float clo = (float)(P.lo - lane);
   const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);  // the j tile is padded with NaN particles
   int qcount = 0;
   for (int jj0 = 0; jj0 < nj4; jj0 += kJU) {
@@ -721,9 +760,9 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
           if (!(jg + 1 > ig)) { dx.y = qnan; dy.y = qnan; dz.y = qnan; }
         }
         float2 sm, e, bound;
-        decide_arith2<V>(dx, dy, dz, P, sm, e, bound);
-        count_or_defer(sm.x, e.x, bound.x, P.kbase, P.width, sbase, 1u << (u * kRegI + r), nulladdr, dmask);
-        count_or_defer(sm.y, e.y, bound.y, P.kbase, P.width, sbase, 1u << ((u + 1) * kRegI + r), nulladdr, dmask);
+        decide_arith2<V, MULTI>(dx, dy, dz, P, chi, clo, sm, e, bound);
+        count_or_defer(sm.x, e.x, bound.x, hbase, 1u << (u * kRegI + r), dmask);
+        count_or_defer(sm.y, e.y, bound.y, hbase, 1u << ((u + 1) * kRegI + r), dmask);
       }
     }
     // queue the deferred pairs: one per lane per round, compacted with a ballot
@@ -740,36 +779,43 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
       ndeferred += added;
       if (qcount >= 32) {
         __syncwarp();
-        qcount = drain_queue<V>(F, P.lo, P.width, q, qcount, sh, lane);
+        qcount = drain_queue<V, MULTI>(F, it.pass, it.i0, q, qcount, sh, lane);
       }
       bal = __ballot_sync(kFull, dmask != 0u);
     }
   }
   __syncwarp();
-  if (qcount > 0) drain_queue<V>(F, P.lo, P.width, q, qcount, sh, lane);
+  if (qcount > 0) drain_queue<V, MULTI>(F, it.pass, it.i0, q, qcount, sh, lane);
   __syncwarp();
 }
 
-__device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P);
-
 // The decision parameters are reloaded per item (from the L1-cached frame
 // descriptor) so that only the fields of this variant are live in the loop.
-template <int V>
+// MULTI: some sweep of the launch starts above bin 0, so the root is also
+// clamped from below (valid for every sweep, a separate kernel for registers).
+template <int V, bool MULTI>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
                          uint2* q, int tid, int lane, unsigned& ndeferred) {
   FastParams P;
   load_fast_params(*F, it.pass, P);
-  if (it.masked) run_tile<V, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
-  else run_tile<V, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
+  if (it.masked) run_tile<V, true, MULTI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
+  else run_tile<V, false, MULTI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
 }
 
-__device__ void flush_hist(uint32_t* sh, int width, uint64_t* dst, int tid) {
+// Adds the `depth` private copies (stride words apart) bin by bin into the
+// global uint64 histogram and clears them, with their guard words.
+__device__ void flush_hist(uint32_t* sh, int width, int depth, int stride, uint64_t* dst, int tid) {
   for (int k = tid; k < width; k += kBlock) {
-    uint32_t v = sh[k];
-    if (v) {
-      atomicAdd((unsigned long long*)(dst + k), (unsigned long long)v);
-      sh[k] = 0u;
+    uint32_t v = 0u;
+    for (int c = 0; c < depth; ++c) {
+      v += sh[c * stride + k];
+      sh[c * stride + k] = 0u;
     }
+    if (v) atomicAdd((unsigned long long*)(dst + k), (unsigned long long)v);
+  }
+  for (int k = tid; k < depth * 2 * kGuard; k += kBlock) {
+    int c = k / (2 * kGuard), g = k - c * 2 * kGuard;
+    sh[c * stride + (g < kGuard ? g - kGuard : width + g - kGuard)] = 0u;
   }
 }
 
@@ -819,9 +865,10 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
   P.S2 = F.S2;
   P.qb1 = F.qb1;
   P.qb0 = F.qb0;
-  P.kbase = __float_as_int(kMagicRound) + lo_bin;
+  P.kb1 = __float_as_int(kMagicRound) + lo_bin + 1;
   P.width = (uint32_t)(hi_bin - lo_bin);
   P.lo = lo_bin;
+  P.hi = hi_bin;
 #pragma unroll
   for (int c = 0; c < 9; ++c) P.b[c] = F.Bf[c];
 #pragma unroll
@@ -829,26 +876,30 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
   P.amb_thr = 0.5f - F.eps_s;
 }
 
-// One instance per minimum-image variant V: every segment of the launch has a
-// frame of that variant.
+// One instance per minimum-image variant V (every segment of the launch has a
+// frame of that variant) and per MULTI.
 template <int V>
 constexpr int min_blocks_per_sm() {
   return (V == V_NONE || V == V_ORTHO || V == V_TRIC) ? 3 : 2;
 }
 
-template <int V>
+template <int V, bool MULTI>
 __global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(PairLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int width_pad = (L.hist_width + 3) & ~3;
-  uint32_t* sh = reinterpret_cast<uint32_t*>(smem_raw);
-  float4* sjA = reinterpret_cast<float4*>(sh + width_pad);
+  // `depth` private histogram copies, each [kGuard guard words | bins | kGuard
+  // guard words] (stride words), then the j tile and the per-warp queues
+  const int depth = L.hist_depth > 1 ? L.hist_depth : 1;
+  const int stride = ((L.hist_width + 3) & ~3) + 2 * kGuard;
+  uint32_t* hist0 = reinterpret_cast<uint32_t*>(smem_raw) + kGuard;
+  float4* sjA = reinterpret_cast<float4*>(reinterpret_cast<uint32_t*>(smem_raw) + depth * stride);
   float2* sjZ = reinterpret_cast<float2*>(sjA + kTile / 2);
-  uint2* sq = reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(sjZ + kTile / 2) + 128);
+  uint2* sq = reinterpret_cast<uint2*>(sjZ + kTile / 2);
   __shared__ ItemDesc s_it;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint2* q = sq + warp * kQueueCap;
-  for (int k = tid; k < width_pad; k += kBlock) sh[k] = 0u;
+  uint32_t* sh = hist0 + (warp % depth) * stride;  // this warp's copy
+  for (int k = tid; k < depth * stride; k += kBlock) reinterpret_cast<uint32_t*>(smem_raw)[k] = 0u;
 
   const FrameDev* cur_fd = nullptr;
   int cur_h = -1, cur_pass = -1;
@@ -882,7 +933,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(Pa
       if (it.fd != cur_fd || it.h != cur_h || it.pass != cur_pass || since + pairs > 0xFFFFFFFFull) {
         if (cur_fd) {
           __syncthreads();
-          flush_hist(sh, cur_width, cur_dst, tid);
+          flush_hist(hist0, cur_width, depth, stride, cur_dst, tid);
           __syncthreads();
         }
         int lo_bin = it.pass * F.sweep_width;
@@ -907,14 +958,14 @@ __global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(Pa
       }
       __syncthreads();
       unsigned ndef = 0;
-      run_item<V>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef);
+      run_item<V, MULTI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();
   }
   if (cur_fd) {
     __syncthreads();
-    flush_hist(sh, cur_width, cur_dst, tid);
+    flush_hist(hist0, cur_width, depth, stride, cur_dst, tid);
   }
 }
 
@@ -984,6 +1035,7 @@ __global__ void check_window_kernel(const FrameDev* Fp, uint64_t n_samples, uint
   FastParams P;
   load_fast_params(F, 0, P);
   P.width = (uint32_t)F.nbins;  // decide over the whole histogram
+  P.hi = F.nbins;
   double worst = 0.0;
   unsigned long long viol = 0, checked = 0;
   if (F.n >= 2) {
@@ -1026,9 +1078,9 @@ cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t 
 
 // ------------------------------------------------------------------ launchers
 
-size_t pair_kernel_smem(int hist_width) {
-  size_t w = (size_t)((hist_width + 3) & ~3);
-  return w * 4 + (size_t)kTile * 12 + 128 + (size_t)kWarps * kQueueCap * 8;
+size_t pair_kernel_smem(int hist_width, int depth) {
+  size_t stride = (size_t)((hist_width + 3) & ~3) + 2 * kGuard;
+  return (size_t)(depth > 1 ? depth : 1) * stride * 4 + (size_t)kTile * 12 + (size_t)kWarps * kQueueCap * 8;
 }
 
 int pair_kernel_max_width() {
@@ -1042,20 +1094,22 @@ int pair_kernel_max_width() {
 }
 
 template <int V>
-int blocks_per_sm_v(int hist_width) {
-  size_t smem = pair_kernel_smem(hist_width);
-  cudaFuncSetAttribute(pair_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel<V>, kBlock, smem);
-  return nb;
+int blocks_per_sm_v(int hist_width, int depth) {
+  size_t smem = pair_kernel_smem(hist_width, depth);
+  int nb0 = 0, nb1 = 0;
+  cudaFuncSetAttribute(pair_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, pair_kernel<V, false>, kBlock, smem);
+  cudaFuncSetAttribute(pair_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, pair_kernel<V, true>, kBlock, smem);
+  return nb0 < nb1 ? nb0 : nb1;
 }
 
-int pair_kernel_blocks_per_sm(int variant, int hist_width) {
+int pair_kernel_blocks_per_sm(int variant, int hist_width, int depth) {
   switch (variant) {
-    case V_NONE: return blocks_per_sm_v<V_NONE>(hist_width);
-    case V_ORTHO: return blocks_per_sm_v<V_ORTHO>(hist_width);
-    case V_TRIC: return blocks_per_sm_v<V_TRIC>(hist_width);
-    default: return blocks_per_sm_v<V_TRIC_SEARCH>(hist_width);
+    case V_NONE: return blocks_per_sm_v<V_NONE>(hist_width, depth);
+    case V_ORTHO: return blocks_per_sm_v<V_ORTHO>(hist_width, depth);
+    case V_TRIC: return blocks_per_sm_v<V_TRIC>(hist_width, depth);
+    default: return blocks_per_sm_v<V_TRIC_SEARCH>(hist_width, depth);
   }
 }
 
@@ -1079,12 +1133,18 @@ cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* s
   return cudaGetLastError();
 }
 
+template <int V, bool MULTI>
+cudaError_t launch_pairs_vm(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
+  cudaError_t e =
+      cudaFuncSetAttribute(pair_kernel<V, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  pair_kernel<V, MULTI><<<grid, kBlock, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
 template <int V>
 cudaError_t launch_pairs_v(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(pair_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  pair_kernel<V><<<grid, kBlock, smem, stream>>>(p);
-  return cudaGetLastError();
+  return p.multi ? launch_pairs_vm<V, true>(p, grid, smem, stream) : launch_pairs_vm<V, false>(p, grid, smem, stream);
 }
 
 cudaError_t launch_pairs(const PairLaunch& p, int variant, int grid, size_t smem, cudaStream_t stream) {

@@ -172,6 +172,7 @@ extern "C" dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream_pt
     L.n_segs = n_segs;
     L.n_items = n_items;
     L.hist_width = pf.sweep_width;
+    L.multi = pf.sweeps > 1;
     L.ctl = ctl;
     DH_CUDA_TRY(launch_pairs(L, pf.variant, pair_grid(num_sms, bps, n_items), pair_kernel_smem(pf.sweep_width), st));
   }

@@ -321,6 +321,7 @@ struct CallPlan {
   int64_t vitems[kNumVariants] = {0, 0, 0, 0};
   size_t vseg0[kNumVariants + 1] = {0, 0, 0, 0, 0};
   int vwidth[kNumVariants] = {1, 1, 1, 1};
+  int vmulti[kNumVariants] = {0, 0, 0, 0};
   int vgrid[kNumVariants] = {0, 0, 0, 0};
   std::vector<size_t> raw_off;  // per frame, offset in c->raw (host coordinates)
   int max_pass = 1;
@@ -401,9 +402,13 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
   for (int v = 0; v < kNumVariants; ++v) {
     P.vgrid[v] = 0;
     if (P.vitems[v] == 0 || !with_pairs) continue;
-    int width = 1;
+    int width = 1, multi = 0;
     for (int f = 0; f < k; ++f)
-      if (pfs[f].variant == v) width = std::max(width, pfs[f].sweep_width);
+      if (pfs[f].variant == v) {
+        width = std::max(width, pfs[f].sweep_width);
+        multi |= pfs[f].sweeps > 1;
+      }
+    P.vmulti[v] = multi;
     int bps = pair_kernel_blocks_per_sm(v, width);
     if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", width);
     P.vwidth[v] = width;
@@ -455,6 +460,7 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
       L.n_segs = (int32_t)(P.vseg0[v + 1] - P.vseg0[v]);
       L.n_items = P.vitems[v];
       L.hist_width = P.vwidth[v];
+      L.multi = P.vmulti[v];
       L.ctl = (Control*)c->ctl.p + v;
       DH_CUDA_TRY(launch_pairs(L, v, P.vgrid[v], pair_kernel_smem(P.vwidth[v]), st));
       ++launched;

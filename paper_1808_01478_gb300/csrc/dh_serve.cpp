@@ -477,7 +477,7 @@ bool Server::launch_wave(int v) {
   const double pairs_per_item = (double)kTile * (double)kTile;
   std::vector<Segment> wsegs;
   int64_t witems = 0;
-  int width = 1;
+  int width = 1, multi = 0;
   double wpairs = 0;
   std::vector<Request*> finishing;
   for (Request* r : run) {
@@ -505,6 +505,7 @@ bool Server::launch_wave(int v) {
     r->next = hi;
     r->last_wave = ln.wave_seq + 1;
     width = std::max(width, r->pf.sweep_width);
+    multi |= r->pf.sweeps > 1;
     wpairs += (double)std::min<uint64_t>(r->pf.pairs, (uint64_t)((double)take * pairs_per_item));
     if (r->next >= r->n_items) finishing.push_back(r);
   }
@@ -523,6 +524,7 @@ bool Server::launch_wave(int v) {
   L.n_segs = (int32_t)wsegs.size();
   L.n_items = witems;
   L.hist_width = width;
+  L.multi = multi;
   L.ctl = (Control*)W.ctl.p;
   int bps = pair_kernel_blocks_per_sm(v, width);
   cudaEventRecord(W.ev0, ln.stream);
