@@ -72,6 +72,10 @@ typedef enum { DH_BOX_NONE = 0, DH_BOX_ORTHO = 1, DH_BOX_TRICLINIC = 2 } dh_box_
 /* dh_config.flags */
 #define DH_CFG_NO_GRAPH 0x1u /* batched path: launch directly instead of replaying a CUDA graph */
 #define DH_CFG_TIMING 0x2u   /* record CUDA events around the pair-kernel launches (dh_stats.pair_kernel_ms) */
+#define DH_CFG_AUTOTUNE 0x4u /* plain and batched paths: measure the launch shapes (j-tile length,
+                                private histogram copies per block, blocks per SM) of every new
+                                launch key on a synthetic batch of its shape before the first call
+                                that needs it, and use the fastest; see dh_tune_cache_count */
 
 typedef struct dh_ctx dh_ctx;
 
@@ -80,7 +84,8 @@ typedef struct {
   uint64_t pool_bytes;   /* served path: device memory the admission control may use (0: 1/2 of free) */
   int32_t max_inflight;  /* served path: most requests resident on the device at once (0: 64) */
   uint64_t timeout_ns;   /* served path: bound on device-side waits (0: 2 s) */
-  const char* tune_cache;/* autotuner cache file, or NULL for in-memory only */
+  const char* tune_cache;/* autotuner cache file (read at dh_create, rewritten after each new
+                            measurement), or NULL for in-memory only */
   uint32_t flags;        /* DH_CFG_* */
   uint32_t wave_us;      /* served path: target device time of one wave in microseconds (0: 6000) */
 } dh_config;
@@ -112,8 +117,12 @@ typedef struct {
   int32_t items;           /* work items (tile pairs) */
   int32_t kernel_launches; /* kernels launched by the call */
   int32_t graph_replays;   /* 1 when the call ran as a replayed CUDA graph */
-  int32_t reserved;
+  int32_t tune_runs;       /* autotuner measurement launches made before the call (DH_CFG_AUTOTUNE) */
   double pair_kernel_ms;   /* device time of the pair-kernel launches (needs DH_CFG_TIMING), else 0 */
+  int32_t tile_j;          /* launch shape of the largest pair-kernel launch: j-tile length, */
+  int32_t hist_depth;      /*   private histogram copies per block, */
+  int32_t blocks_per_sm;   /*   and blocks per SM */
+  int32_t reserved;
 } dh_stats;
 
 /* Create a context on config->device (NULL: device 0, defaults).  Owns a CUDA
@@ -178,6 +187,22 @@ const char* dh_last_error(dh_ctx* ctx);
  * a pair with r^2 = q lies in bin k iff thresholds[k] <= q < thresholds[k+1],
  * and is counted iff q < thresholds[nbins].  thresholds must hold nbins+1 doubles. */
 dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds);
+
+/* Host-only helper, no GPU needed: reads an autotuner cache file, the text file
+ * that dh_create reads and the autotuner rewrites (DH_CFG_AUTOTUNE with
+ * dh_config.tune_cache): lines starting with '#' are comments, every other line
+ * is one launch key and its measured shape,
+ *   sms variant width_log2 n_log2 frames_log4 tile_j depth bps gpairs_s
+ * (variant: 0 none, 1 orthorhombic, 2 triclinic, 3 triclinic with the
+ * 27-image search; width_log2 = ceil(log2 of the shared-memory histogram
+ * width); n_log2 = round(log2 of the mean particles per frame); frames_log4 =
+ * min(3, floor(log4 of the frames per launch)); tile_j in {256, 512, 1024};
+ * depth in {1, 2, 4}; bps >= 1; gpairs_s > 0).  *n_entries receives the number
+ * of distinct launch keys with a well-formed line for a GPU with sm_count SMs
+ * (a later line replaces an earlier one of the same key); lines for other SM
+ * counts and malformed lines are skipped.  DH_ERR_NOTFOUND if the file cannot
+ * be read. */
+dh_status dh_tune_cache_count(const char* path, int32_t sm_count, int32_t* n_entries);
 
 /* Diagnostics of the float32 decision rule (not part of the histogram).
  *  what = DH_CHECK_SQRT: out[0] = largest relative error of the float32 square

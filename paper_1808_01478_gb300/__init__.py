@@ -36,6 +36,7 @@ DH_ACCUMULATE = 0x2
 DH_COORDS_F4 = 0x4
 DH_CFG_NO_GRAPH = 0x1
 DH_CFG_TIMING = 0x2
+DH_CFG_AUTOTUNE = 0x4
 DH_MAX_BINS = 4194240
 
 STATUS_NAMES = {0: "DH_OK", 1: "DH_PENDING", -1: "DH_ERR_INVALID", -2: "DH_ERR_NOMEM",
@@ -62,7 +63,9 @@ class dh_stats(ctypes.Structure):
                 ("exact_fallback", ctypes.c_uint64), ("sweeps", ctypes.c_int32),
                 ("blocks", ctypes.c_int32), ("items", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int32), ("graph_replays", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("pair_kernel_ms", ctypes.c_double)]
+                ("tune_runs", ctypes.c_int32), ("pair_kernel_ms", ctypes.c_double),
+                ("tile_j", ctypes.c_int32), ("hist_depth", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -96,6 +99,7 @@ _SIGNATURES = {
     "dh_selfcheck": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                       ctypes.c_void_p], ctypes.c_int),
     "dh_histogram_noalloc": ([ctypes.POINTER(dh_frame), ctypes.c_void_p], ctypes.c_int),
+    "dh_tune_cache_count": ([ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
 }
 
 DH_NOALLOC_MAX_N = 131072
@@ -149,9 +153,16 @@ def dh_bin_thresholds(r_max: float, nbins: int) -> np.ndarray:
     return out
 
 
+def dh_tune_cache_count(path: str, sm_count: int) -> int:
+    n = ctypes.c_int32(0)
+    _check(load_library().dh_tune_cache_count(os.fsencode(path), int(sm_count), ctypes.byref(n)))
+    return n.value
+
+
 def dh_create(device: int = 0, pool_bytes: int = 0, max_inflight: int = 0, timeout_ns: int = 0,
-              flags: int = 0, wave_us: int = 0) -> ctypes.c_void_p:
-    cfg = dh_config(device, pool_bytes, max_inflight, timeout_ns, None, flags, wave_us)
+              flags: int = 0, wave_us: int = 0, tune_cache: str | None = None) -> ctypes.c_void_p:
+    cfg = dh_config(device, pool_bytes, max_inflight, timeout_ns,
+                    None if tune_cache is None else os.fsencode(tune_cache), flags, wave_us)
     h = ctypes.c_void_p()
     _check(load_library().dh_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h

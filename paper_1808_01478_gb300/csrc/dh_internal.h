@@ -65,12 +65,12 @@ struct FrameDev {
 // [item0, item0 + count) are the segment's items [item_base, item_base + count).
 struct Segment {
   FrameDev* fd;
-  int32_t intra;     // a == b: only tiles ti <= tj, pairs j > i
+  int32_t intra;     // a == b: only j tiles not below the i tile, pairs j > i
   int32_t h;         // histogram index within the frame
   int32_t pass;      // bin sweep: bins [pass*w, min(nbins, (pass+1)*w)), w = fd->sweep_width
-  int32_t n_ti, n_tj;
+  int32_t n_ti, n_tj;  // i tiles of kTile particles, j tiles of kTile/jm particles
   int32_t a0, na, b0, nb;  // frame-local particle ranges of species a and b
-  int32_t pad;
+  int32_t jm;        // j tiles per i tile (1, 2 or 4; 0 means 1)
   int64_t item0;     // first launch item of this segment
   int64_t item_base; // segment-local index of that item
 };

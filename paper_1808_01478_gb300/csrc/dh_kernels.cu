@@ -820,7 +820,9 @@ __device__ void flush_hist(uint32_t* sh, int width, int depth, int stride, uint6
 }
 
 // Work item -> tile pair.  Items of a segment are numbered row by row over
-// (ti, tj); intra-species segments keep only tj >= ti (upper triangle).
+// (ti, tj), i tiles of kTile particles and j tiles of kTile/jm; intra-species
+// segments keep only j tiles that do not end before the i tile starts
+// (tj >= jm ti), and mask pairs j <= i in those that overlap it (tj < jm (ti + 1)).
 __device__ void decode_item(const PairLaunch& L, long long item, ItemDesc& it) {
   int lo = 0, hi = L.n_segs - 1;
   while (lo < hi) {
@@ -828,20 +830,22 @@ __device__ void decode_item(const PairLaunch& L, long long item, ItemDesc& it) {
     if (L.segs[mid].item0 <= item) lo = mid; else hi = mid - 1;
   }
   const Segment& s = L.segs[lo];
+  const int jm = s.jm > 1 ? s.jm : 1;
+  const int tile_j = kTile / jm;
   long long lid = item - s.item0 + s.item_base;
   int ti, tj;
   if (s.intra) {
-    // row ti starts at ti*n - ti*(ti-1)/2
-    long long n = s.n_ti;
-    int a = 0, b = (int)n - 1;
+    // row ti holds tj in [jm ti, n_tj) and starts at ti n_tj - jm ti (ti - 1) / 2
+    long long n = s.n_tj;
+    int a = 0, b = s.n_ti - 1;
     while (a < b) {
       int m = (a + b + 1) >> 1;
-      long long start = (long long)m * n - (long long)m * (m - 1) / 2;
+      long long start = (long long)m * n - (long long)jm * m * (m - 1) / 2;
       if (start <= lid) a = m; else b = m - 1;
     }
     ti = a;
-    long long start = (long long)ti * n - (long long)ti * (ti - 1) / 2;
-    tj = ti + (int)(lid - start);
+    long long start = (long long)ti * n - (long long)jm * ti * (ti - 1) / 2;
+    tj = jm * ti + (int)(lid - start);
   } else {
     ti = (int)(lid / s.n_tj);
     tj = (int)(lid - (long long)ti * s.n_tj);
@@ -852,9 +856,9 @@ __device__ void decode_item(const PairLaunch& L, long long item, ItemDesc& it) {
   it.pass = s.pass;
   it.i0 = s.a0 + ti * kTile;
   it.ni = min(kTile, s.na - ti * kTile);
-  it.j0 = s.b0 + tj * kTile;
-  it.nj = min(kTile, s.nb - tj * kTile);
-  it.masked = (s.intra && ti == tj) ? 1 : 0;
+  it.j0 = s.b0 + tj * tile_j;
+  it.nj = min(tile_j, s.nb - tj * tile_j);
+  it.masked = (s.intra && tj < jm * (ti + 1)) ? 1 : 0;
   int lo_bin = s.pass * s.fd->sweep_width;
   it.skip = (lo_bin >= s.fd->nbins) ? 1 : 0;
 }

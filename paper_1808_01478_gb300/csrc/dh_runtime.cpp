@@ -268,8 +268,10 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
 
 // Tiles of one frame's species pairs for every bin sweep, appended to segs
 // (fd: the frame's device descriptor); returns the item count.
-int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::vector<Segment>& segs) {
+int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::vector<Segment>& segs, int jm) {
   const dh_frame* f = pf.src;
+  jm = (jm == 2 || jm == 4) ? jm : 1;
+  const int tile_j = kTile / jm;
   const int64_t* o = f->species_offsets;
   int S = f->n_species;
   int64_t items = 0;
@@ -291,10 +293,13 @@ int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::v
         s.b0 = (int32_t)o[b];
         s.nb = nb;
         s.n_ti = (na + kTile - 1) / kTile;
-        s.n_tj = (nb + kTile - 1) / kTile;
+        s.n_tj = (nb + tile_j - 1) / tile_j;
+        s.jm = jm;
         s.item0 = item0 + items;
         s.item_base = 0;
-        items += intra ? (int64_t)s.n_ti * (s.n_ti + 1) / 2 : (int64_t)s.n_ti * s.n_tj;
+        // intra: row ti keeps the j tiles tj >= jm ti (at least one, since na > (n_ti - 1) kTile)
+        items += intra ? (int64_t)s.n_ti * s.n_tj - (int64_t)jm * s.n_ti * (s.n_ti - 1) / 2
+                       : (int64_t)s.n_ti * s.n_tj;
         segs.push_back(s);
       }
   }
@@ -306,6 +311,41 @@ namespace {
 void release_held(dh_ctx* c) {
   for (const double* T : c->held_tables) c->tcache.release(T);
   c->held_tables.clear();
+}
+
+// The frames of one minimum-image variant in a call, as the autotuner keys them.
+struct VariantSummary {
+  int frames = 0, width = 1, multi = 0;
+  double pairs = 0.0;
+  TuneKey key() const { return make_tune_key(0, width, frames ? pairs / frames : 0.0, frames); }
+};
+
+VariantSummary summarize(const std::vector<PlannedFrame>& pfs, int v) {
+  VariantSummary s;
+  for (const auto& pf : pfs)
+    if (pf.variant == v) {
+      ++s.frames;
+      s.width = std::max(s.width, pf.sweep_width);
+      s.multi |= pf.sweeps > 1;
+      s.pairs += (double)pf.pairs;
+    }
+  return s;
+}
+
+TuneKey variant_key(const VariantSummary& s, int v) {
+  TuneKey k = s.key();
+  k.variant = v;
+  return k;
+}
+
+// Launch shape for a variant: forced during a measurement, else the tuned
+// shape of its key, else one j tile per i tile, one histogram copy and as
+// many blocks per SM as fit.
+LaunchParams launch_params(dh_ctx* c, const VariantSummary& s, int v) {
+  if (c->tune_forced) return c->tune_force;
+  LaunchParams p;
+  if (c->tuner.lookup(variant_key(s, v), &p)) return p;
+  return LaunchParams{};
 }
 
 // Host-side plan of one call: buffers sized, threshold tables referenced,
@@ -322,6 +362,7 @@ struct CallPlan {
   size_t vseg0[kNumVariants + 1] = {0, 0, 0, 0, 0};
   int vwidth[kNumVariants] = {1, 1, 1, 1};
   int vmulti[kNumVariants] = {0, 0, 0, 0};
+  LaunchParams vparams[kNumVariants];
   int vgrid[kNumVariants] = {0, 0, 0, 0};
   std::vector<size_t> raw_off;  // per frame, offset in c->raw (host coordinates)
   int max_pass = 1;
@@ -349,6 +390,11 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
   // device metadata: FrameDev[k] | StageJob[k] | Segment[m], uploaded in one copy;
   // segments are grouped by minimum-image variant (one pair-kernel launch each)
   std::vector<Segment> segs;
+  VariantSummary vsum[kNumVariants];
+  for (int v = 0; v < kNumVariants; ++v) {
+    vsum[v] = summarize(pfs, v);
+    P.vparams[v] = launch_params(c, vsum[v], v);
+  }
   auto plan_segments = [&](FrameDev* dF) {
     segs.clear();
     P.n_items = 0;
@@ -356,7 +402,8 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
       P.vseg0[v] = segs.size();
       P.vitems[v] = 0;
       for (int f = 0; f < k; ++f)
-        if (pfs[f].variant == v) P.vitems[v] += add_segments(pfs[f], dF + f, P.vitems[v], segs);
+        if (pfs[f].variant == v)
+          P.vitems[v] += add_segments(pfs[f], dF + f, P.vitems[v], segs, P.vparams[v].jm);
       P.n_items += P.vitems[v];
     }
     P.vseg0[kNumVariants] = segs.size();
@@ -402,17 +449,18 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
   for (int v = 0; v < kNumVariants; ++v) {
     P.vgrid[v] = 0;
     if (P.vitems[v] == 0 || !with_pairs) continue;
-    int width = 1, multi = 0;
-    for (int f = 0; f < k; ++f)
-      if (pfs[f].variant == v) {
-        width = std::max(width, pfs[f].sweep_width);
-        multi |= pfs[f].sweeps > 1;
-      }
-    P.vmulti[v] = multi;
-    int bps = pair_kernel_blocks_per_sm(v, width);
-    if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", width);
+    const int width = vsum[v].width;
+    P.vmulti[v] = vsum[v].multi;
+    LaunchParams& lp = P.vparams[v];
+    int bps_max = pair_kernel_blocks_per_sm(v, width, lp.depth);
+    if (bps_max < 1 && lp.depth > 1) {
+      lp.depth = 1;  // the copies do not fit: one copy
+      bps_max = pair_kernel_blocks_per_sm(v, width, 1);
+    }
+    if (bps_max < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", width);
+    lp.bps = lp.bps > 0 ? std::min(lp.bps, bps_max) : bps_max;
     P.vwidth[v] = width;
-    P.vgrid[v] = pair_grid(c->num_sms, bps, P.vitems[v]);
+    P.vgrid[v] = pair_grid(c->num_sms, lp.bps, P.vitems[v]);
   }
   return DH_OK;
 }
@@ -442,7 +490,8 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
   DH_CUDA_TRY(launch_frame_setup(dF, k, 0, st));
   ++launched;
   // A2-A8: per variant, one persistent launch over its frames, species pairs and bin sweeps
-  int grid = 0;
+  int grid = 0, top = -1;
+  int64_t top_items = 0;
   bool any = false;
   for (int v = 0; v < kNumVariants; ++v) any |= P.vgrid[v] > 0;
   // timing events: inside a stream capture they must become event-record nodes
@@ -460,11 +509,16 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
       L.n_segs = (int32_t)(P.vseg0[v + 1] - P.vseg0[v]);
       L.n_items = P.vitems[v];
       L.hist_width = P.vwidth[v];
+      L.hist_depth = P.vparams[v].depth;
       L.multi = P.vmulti[v];
       L.ctl = (Control*)c->ctl.p + v;
-      DH_CUDA_TRY(launch_pairs(L, v, P.vgrid[v], pair_kernel_smem(P.vwidth[v]), st));
+      DH_CUDA_TRY(launch_pairs(L, v, P.vgrid[v], pair_kernel_smem(P.vwidth[v], P.vparams[v].depth), st));
       ++launched;
       grid = std::max(grid, P.vgrid[v]);
+      if (P.vitems[v] > top_items) {
+        top_items = P.vitems[v];
+        top = v;
+      }
     }
     if (c->ev_pair1) DH_CUDA_TRY(cudaEventRecordWithFlags(c->ev_pair1, st, ev_flags));
   }
@@ -476,6 +530,12 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
   S.blocks = grid;
   S.items = (int32_t)std::min<int64_t>(P.n_items, 0x7FFFFFFF);
   S.kernel_launches = launched + P.launched;
+  S.tune_runs = c->tune_runs;
+  if (top >= 0) {
+    S.tile_j = kTile / P.vparams[top].jm;
+    S.hist_depth = P.vparams[top].depth;
+    S.blocks_per_sm = P.vparams[top].bps;
+  }
   return DH_OK;
 }
 
@@ -504,11 +564,13 @@ dh_status finish_frames(dh_ctx* c, int k) {
   }
   for (int f = 0; f < k; ++f) {
     c->stats.deferred += hF[f].deferred;
-    c->stats.exact_fallback += hF[f].deferred;
+    c->stats.exact_fallback += hF[f].exact;
     if (hF[f].bad) return fail(DH_ERR_INVALID, "frame %d has non-finite coordinates", f);
   }
   return DH_OK;
 }
+
+dh_status autotune_call(dh_ctx* c, const std::vector<PlannedFrame>& pfs);
 
 // One call: check, plan, then enqueue directly or (batched device-pointer
 // calls) as a CUDA graph that is captured per call and replayed through an
@@ -523,6 +585,11 @@ dh_status run_frames(dh_ctx* c, const dh_frame* frames, int k, bool wait, bool u
     if (s != DH_OK) return s;
     if (((frames[f].flags & DH_DEVICE_PTRS) != 0) != dev)
       return fail(DH_ERR_INVALID, "all frames of a batch must use the same pointer kind");
+  }
+  if (!c->tune_forced) {
+    c->tune_runs = 0;
+    dh_status ts = autotune_call(c, pfs);
+    if (ts != DH_OK) return ts;
   }
   const bool graph = use_graph && dev && !(c->cfg.flags & DH_CFG_NO_GRAPH);
   cudaStream_t st = c->stream();
@@ -620,6 +687,157 @@ dh_status run_frames(dh_ctx* c, const dh_frame* frames, int k, bool wait, bool u
   return DH_OK;
 }
 
+// ---- autotuner measurements
+
+uint64_t splitmix64(uint64_t& z) {
+  uint64_t x = (z += 0x9E3779B97F4A7C15ull);
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// Measures every launch shape on a synthetic batch shaped like the frames of
+// variant v in the call (same histogram width and sweeps, the mean frame size,
+// up to 64 frames, about 6e9 pairs): uniform particles at density 0.1 in a
+// cube (none: every pair in range; orthorhombic: r_max = L/2) or in the
+// 70/80/100-degree cell (r_max = 0.95 h_min/2, or 0.75 h_min for the 27-image
+// search).  The fastest shape is stored under the variant's launch key.
+dh_status tune_variant(dh_ctx* c, int v, const VariantSummary& vs) {
+  const double mean_pairs = vs.pairs / std::max(vs.frames, 1);
+  int64_t n = (int64_t)std::llround(std::sqrt(2.0 * std::max(mean_pairs, 1.0)));
+  n = std::min<int64_t>(std::max<int64_t>(n, 64), 110000);
+  const double pairs_one = 0.5 * (double)n * (double)(n - 1);
+  const int nf = (int)std::min<int64_t>(std::max<int64_t>(std::llround(6e9 / pairs_one), 1),
+                                        std::min(vs.frames, 64));
+  const int nbins = vs.multi ? 2 * vs.width : vs.width;
+  const double vol = (double)n / 0.1;
+  double box[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double r_max = 0.0;
+  int32_t box_type = DH_BOX_NONE;
+  if (v == V_NONE || v == V_ORTHO) {
+    double L = std::cbrt(vol);
+    box[0] = box[4] = box[8] = L;
+    box_type = (v == V_NONE) ? DH_BOX_NONE : DH_BOX_ORTHO;
+    r_max = (v == V_NONE) ? L * std::sqrt(3.0) * 1.0001 : 0.5 * L;
+  } else {
+    const double d2r = 3.14159265358979323846 / 180.0, ca = std::cos(70 * d2r), cb = std::cos(80 * d2r), cg = std::cos(100 * d2r),
+                 sg = std::sin(100 * d2r);
+    const double cy = (ca - cb * cg) / sg, cz = std::sqrt(1.0 - cb * cb - cy * cy);
+    const double l = std::cbrt(vol / (sg * cz));
+    box[0] = l; box[1] = l * cg; box[2] = l * cb;
+    box[4] = l * sg; box[5] = l * cy;
+    box[8] = l * cz;
+    // plane spacings: V / |b x c|, V / |c x a|, V / |a x b|
+    const double a[3] = {box[0], 0, 0}, b[3] = {box[1], box[4], 0}, cc[3] = {box[2], box[5], box[8]};
+    auto cross_norm = [](const double* x, const double* y) {
+      double u = x[1] * y[2] - x[2] * y[1], w = x[2] * y[0] - x[0] * y[2], z = x[0] * y[1] - x[1] * y[0];
+      return std::sqrt(u * u + w * w + z * z);
+    };
+    const double V = box[0] * box[4] * box[8];
+    const double h_min = std::min(V / cross_norm(b, cc), std::min(V / cross_norm(cc, a), V / cross_norm(a, b)));
+    box_type = DH_BOX_TRICLINIC;
+    r_max = (v == V_TRIC) ? 0.95 * 0.5 * h_min : 0.75 * h_min;
+  }
+  std::vector<float> hx((size_t)nf * n * 3);
+  uint64_t z = 0x5eedull + (uint64_t)v;
+  for (size_t q = 0; q < hx.size(); q += 3) {
+    double s0 = (double)(splitmix64(z) >> 11) * 0x1.0p-53, s1 = (double)(splitmix64(z) >> 11) * 0x1.0p-53,
+           s2 = (double)(splitmix64(z) >> 11) * 0x1.0p-53;
+    hx[q] = (float)(box[0] * s0 + box[1] * s1 + box[2] * s2);
+    hx[q + 1] = (float)(box[4] * s1 + box[5] * s2);
+    hx[q + 2] = (float)(box[8] * s2);
+    if (v == V_NONE) {  // the cube as a non-periodic region
+      double L = box[0];
+      hx[q] = (float)(L * s0); hx[q + 1] = (float)(L * s1); hx[q + 2] = (float)(L * s2);
+    }
+  }
+  if (v == V_NONE) std::fill(box, box + 9, 0.0);
+  DevBuf dx, dout;
+  DH_CUDA_TRY(dx.ensure(sizeof(float) * hx.size()));
+  DH_CUDA_TRY(dout.ensure(sizeof(uint64_t) * (size_t)nf * nbins));
+  DH_CUDA_TRY(cudaMemcpy(dx.p, hx.data(), sizeof(float) * hx.size(), cudaMemcpyHostToDevice));
+  int64_t offs[2] = {0, n};
+  std::vector<dh_frame> fr((size_t)nf);
+  for (int f = 0; f < nf; ++f) {
+    dh_frame& d = fr[f];
+    std::memset(&d, 0, sizeof d);
+    d.coords = (const float*)dx.p + (size_t)f * n * 3;
+    d.n = n;
+    d.species_offsets = offs;
+    d.n_species = 1;
+    d.box_type = box_type;
+    std::memcpy(d.box, box, sizeof box);
+    d.r_max = r_max;
+    d.nbins = nbins;
+    d.out = (uint64_t*)dout.p + (size_t)f * nbins;
+    d.flags = DH_DEVICE_PTRS;
+  }
+  const bool own_events = (c->ev_pair0 == nullptr);
+  if (own_events) {
+    DH_CUDA_TRY(cudaEventCreate(&c->ev_pair0));
+    DH_CUDA_TRY(cudaEventCreate(&c->ev_pair1));
+  }
+  c->tune_forced = true;
+  TuneEntry best;
+  dh_status s = DH_OK;
+  auto measure = [&](const LaunchParams& p, double* gps) {
+    c->tune_force = p;
+    dh_status r = run_frames(c, fr.data(), nf, true, false);
+    if (r != DH_OK) return r;
+    ++c->tune_runs;
+    double ms = c->stats.pair_kernel_ms;
+    *gps = ms > 0.0 ? pairs_one * nf / (ms * 1e6) : 0.0;
+    return DH_OK;
+  };
+  double g = 0.0;
+  s = measure(LaunchParams{}, &g);  // warm-up (first launches of a shape)
+  for (int jm = 1; jm <= 4 && s == DH_OK; jm *= 2)
+    for (int depth = 1; depth <= 4 && s == DH_OK; depth *= 2) {
+      int bmax = pair_kernel_blocks_per_sm(v, vs.width, depth);
+      for (int bps = bmax; bps >= 1 && bps >= bmax - 1 && s == DH_OK; --bps) {
+        LaunchParams p;
+        p.jm = jm;
+        p.depth = depth;
+        p.bps = bps;
+        s = measure(p, &g);
+        if (s == DH_OK && g > best.gpairs_s) {
+          best.p = p;
+          best.gpairs_s = g;
+        }
+      }
+    }
+  c->tune_forced = false;
+  if (own_events) {
+    cudaEventDestroy(c->ev_pair0);
+    cudaEventDestroy(c->ev_pair1);
+    c->ev_pair0 = c->ev_pair1 = nullptr;
+  }
+  if (s != DH_OK) return s;
+  if (best.gpairs_s > 0.0) {
+    c->tuner.store(variant_key(vs, v), best);
+    if (!c->tune_path.empty()) c->tuner.save(c->tune_path, c->num_sms);
+  }
+  return DH_OK;
+}
+
+// Before a call (DH_CFG_AUTOTUNE, outside any stream capture): measure the
+// launch keys of its variants that have no tuned shape yet.
+dh_status autotune_call(dh_ctx* c, const std::vector<PlannedFrame>& pfs) {
+  if (!(c->cfg.flags & DH_CFG_AUTOTUNE)) return DH_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DH_CUDA_TRY(cudaStreamIsCapturing(c->stream(), &cs));
+  if (cs != cudaStreamCaptureStatusNone) return DH_OK;
+  for (int v = 0; v < kNumVariants; ++v) {
+    VariantSummary vs = summarize(pfs, v);
+    if (vs.frames == 0 || vs.pairs <= 0.0) continue;
+    LaunchParams p;
+    if (c->tuner.lookup(variant_key(vs, v), &p)) continue;
+    dh_status s = tune_variant(c, v, vs);
+    if (s != DH_OK) return s;
+  }
+  return DH_OK;
+}
+
 dh_status selfcheck(dh_ctx* c, int32_t what, const dh_frame* frame, uint64_t n_samples, uint64_t seed, double* out) {
   cudaStream_t st = c->stream();
   DevBuf res;
@@ -707,6 +925,11 @@ dh_status dh_create(const dh_config* config, dh_ctx** out) {
     DH_CUDA_TRY(cudaEventCreate(&c->ev_pair0));
     DH_CUDA_TRY(cudaEventCreate(&c->ev_pair1));
   }
+  if (c->cfg.tune_cache && c->cfg.tune_cache[0]) {
+    c->tune_path = c->cfg.tune_cache;
+    c->tuner.load(c->tune_path, c->num_sms);  // a missing file is an empty table
+  }
+  c->cfg.tune_cache = nullptr;  // the caller's string is not kept
   *out = c.release();
   return DH_OK;
 }

@@ -90,7 +90,45 @@ struct PlannedFrame {
 
 dh_status check_frame(const dh_frame* f, PlannedFrame& pf, int max_width);
 void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64_t* out, const double* T);
-int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::vector<Segment>& segs);
+// jm: j tiles of kTile/jm particles per i tile of kTile
+int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::vector<Segment>& segs, int jm = 1);
+
+// Launch shape of one pair-kernel launch.
+struct LaunchParams {
+  int32_t jm = 1;     // j tiles per i tile: tile_j = kTile / jm
+  int32_t depth = 1;  // private histogram copies per block
+  int32_t bps = 0;    // blocks per SM (0: as many as fit)
+};
+
+// Autotuner key of a launch: variant, histogram width, frame size, frame count (all bucketed).
+struct TuneKey {
+  int32_t variant = 0, width_log2 = 0, n_log2 = 0, frames_log4 = 0;
+  bool operator<(const TuneKey& o) const {
+    if (variant != o.variant) return variant < o.variant;
+    if (width_log2 != o.width_log2) return width_log2 < o.width_log2;
+    if (n_log2 != o.n_log2) return n_log2 < o.n_log2;
+    return frames_log4 < o.frames_log4;
+  }
+};
+struct TuneEntry {
+  LaunchParams p;
+  double gpairs_s = 0.0;
+};
+TuneKey make_tune_key(int variant, int width, double mean_pairs_per_frame, int frames);
+
+// Measured launch shapes per key (dh_tune.cpp), optionally kept in a text file.
+class Tuner {
+ public:
+  bool lookup(const TuneKey& k, LaunchParams* p);
+  void store(const TuneKey& k, const TuneEntry& e);
+  size_t size();
+  int load(const std::string& path, int sms);   // entries read, -1 if the file cannot be read
+  bool save(const std::string& path, int sms);
+
+ private:
+  std::mutex mu_;
+  std::map<TuneKey, TuneEntry> map_;
+};
 // Blocks for the pair kernel: `bps` per SM, at most one per item.
 int pair_grid(int num_sms, int bps, int64_t n_items);
 
@@ -124,6 +162,12 @@ struct dh_ctx {
   dh::DevBuf tstat;    // threshold build status
   dh::ThresholdCache tcache;
   std::vector<const double*> held_tables;  // tables referenced by work not yet finished
+
+  dh::Tuner tuner;
+  std::string tune_path;           // autotuner cache file ("" for none)
+  bool tune_forced = false;        // measurement in progress: every launch uses tune_force
+  dh::LaunchParams tune_force;
+  int32_t tune_runs = 0;           // measurement launches made for the current call
 
   dh_stats stats{};
   cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;  // pair-kernel timing (DH_CFG_TIMING)
