@@ -61,6 +61,36 @@ def load_peaks() -> dict:
         return {}
 
 
+TRAFFIC_FILE = os.path.join("profiles", "pair_kernel_dram_n1m_batch.txt")
+
+
+def committed_traffic() -> int | None:
+    """DRAM bytes of the pair-kernel launches of one headline step, from the
+    committed ncu capture, or None once the kernel sources differ from the ones
+    the capture was taken with."""
+    import hashlib
+
+    try:
+        lines = open(os.path.join(ROOT, TRAFFIC_FILE)).read().splitlines()
+    except OSError:
+        return None
+    total = 0
+    for line in lines:
+        p = line.split()
+        if not p or p[0].startswith("#"):
+            continue
+        if p[0] == "source_sha256":
+            try:
+                digest = hashlib.sha256(open(os.path.join(ROOT, p[1]), "rb").read()).hexdigest()
+            except OSError:
+                return None
+            if digest != p[2]:
+                return None
+        elif p[0] == "launch":
+            total += int(p[3]) + int(p[4])
+    return total or None
+
+
 def alu_peak_tops(sm_count: int, mhz: float) -> float:
     return sm_count * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
 
@@ -470,8 +500,13 @@ def run_gpu(args, world, rank, local):
     mean_pair_s = statistics.mean(pair_ms) / 1e3
     achieved = ops / mean_pair_s / 1e12
     peak = alu_peak_tops(SM_COUNT, sm_max)
+    headline_size = (args.n, args.nbins) == (1_000_000, 10_000)
+    traffic = committed_traffic() if headline_size else None
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "traffic_basis": ("DRAM bytes read + written by the step's three pair-kernel launches (ncu, "
+                                  f"{TRAFFIC_FILE}); algorithmic: 3 x (16 B x N + 8 B x nbins)"
+                                  if traffic else None),
                 "kernel": "dh::pair_kernel", "ops_per_step": ops,
                 "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max clock)"}
 
