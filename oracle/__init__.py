@@ -66,6 +66,8 @@ class OracleLib:
         lib.dh_oracle_bin.restype = ctypes.c_int64
         lib.dh_oracle_pairs_r2.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, P, P]
         lib.dh_oracle_pairs_r2.restype = None
+        lib.dh_oracle_rdf.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P, ctypes.c_uint64, P]
+        lib.dh_oracle_rdf.restype = None
         lib.dh_oracle_max_threads.argtypes = []
         lib.dh_oracle_max_threads.restype = ctypes.c_int
         self.lib = lib
@@ -112,6 +114,19 @@ class OracleLib:
     def bin_of(self, r2: float, r_max: float, nbins: int) -> int:
         return int(self.lib.dh_oracle_bin(float(r2), float(r_max), int(nbins)))
 
+    def rdf(self, counts, r_max: float, pair_density, n_frames: int) -> np.ndarray:
+        """g(r) of Eq. 1 per bin from histograms summed over n_frames frames;
+        pair_density[h] = N_pairs / V of histogram h."""
+        c = np.ascontiguousarray(counts, dtype=np.uint64)
+        c2 = c.reshape(-1, c.shape[-1])
+        dens = np.ascontiguousarray(pair_density, dtype=np.float64).reshape(-1)
+        if dens.shape[0] != c2.shape[0]:
+            raise ValueError("one pair density per histogram")
+        g = np.empty(c2.shape, dtype=np.float64)
+        self.lib.dh_oracle_rdf(_ptr(c2), c2.shape[0], c2.shape[1], float(r_max), _ptr(dens), int(n_frames),
+                               _ptr(g))
+        return g.reshape(c.shape)
+
 
 def default() -> OracleLib:
     global _default
@@ -154,3 +169,7 @@ def pairs_r2(coords, ii, jj, box_type, box):
 
 def bin_of(r2: float, r_max: float, nbins: int) -> int:
     return default().bin_of(r2, r_max, nbins)
+
+
+def rdf(counts, r_max: float, pair_density, n_frames: int):
+    return default().rdf(counts, r_max, pair_density, n_frames)

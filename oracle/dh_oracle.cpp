@@ -201,6 +201,26 @@ void dh_oracle_pairs_r2(const float* coords, const int64_t* ii, const int64_t* j
   for (int64_t p = 0; p < m; ++p) out[p] = pair_r2(coords + 3 * ii[p], coords + 3 * jj[p], b);
 }
 
+// Radial distribution function of Eq. 1 from histograms of Eqs. 3-4 that hold
+// counts summed over n_frames frames: per bin k (r_k = k dr, dr = r_max/nbins,
+// Eq. 4), the mean pairs per frame in the bin divided by the pairs a uniform
+// pair density N_pairs / V (pair_density[h]) puts in the bin's spherical shell,
+// whose volume (4 pi / 3)(r_{k+1}^3 - r_k^3) is the finite-bin form of the
+// 4 pi r^2 dr of Eq. 1.  counts and g are n_hist x nbins, row-major.
+void dh_oracle_rdf(const uint64_t* counts, int32_t n_hist, int32_t nbins, double r_max,
+                   const double* pair_density, uint64_t n_frames, double* g) {
+  const double pi = 3.14159265358979323846;
+  const double dr = r_max / (double)nbins;
+  for (int32_t h = 0; h < n_hist; ++h)
+    for (int32_t k = 0; k < nbins; ++k) {
+      double r0 = (double)k * dr;
+      double r1 = (double)(k + 1) * dr;
+      double shell = 4.0 * pi / 3.0 * (r1 * r1 * r1 - r0 * r0 * r0);
+      double per_frame = (double)counts[(size_t)h * nbins + k] / (double)n_frames;
+      g[(size_t)h * nbins + k] = per_frame / (pair_density[h] * shell);
+    }
+}
+
 int dh_oracle_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -31,6 +31,11 @@ MUTANTS = {
                        "double dy = (double)xj[1] - (double)xi[0];"),
     "inter_starts_at_species_a": ("int64_t jstart = intra ? i + 1 : b0;",
                                   "int64_t jstart = intra ? i + 1 : a0;"),
+    "rdf_shell_squares": ("double shell = 4.0 * pi / 3.0 * (r1 * r1 * r1 - r0 * r0 * r0);",
+                          "double shell = 4.0 * pi / 3.0 * (r1 * r1 - r0 * r0);"),
+    "rdf_ignores_frames": ("double per_frame = (double)counts[(size_t)h * nbins + k] / (double)n_frames;",
+                           "double per_frame = (double)counts[(size_t)h * nbins + k];"),
+    "rdf_upper_edge_only": ("double r0 = (double)k * dr;", "double r0 = 0.0;"),
     "hist_order_swapped": ("return a * S - a * (a - 1) / 2 + (b - a);",
                            "return (S * (S + 1) / 2 - 1) - (a * S - a * (a - 1) / 2 + (b - a));"),
 }
@@ -50,6 +55,9 @@ PIN_TESTS = [
     (pins.test_exact_rational_recomputation, {"box_type": pins.ORTHO}),
     (pins.test_exact_rational_recomputation, {"box_type": pins.TRIC}),
     (pins.test_ideal_gas_closed_form, {"box_type": pins.ORTHO}),
+    (pins.test_rdf_hand_shells, {}),
+    (pins.test_rdf_frames_and_density_scale, {}),
+    (pins.test_rdf_ideal_gas_is_one, {}),
 ]
 
 

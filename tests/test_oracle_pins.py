@@ -389,3 +389,46 @@ def test_bin_function_monotone_and_half_open(oracle_mod):
     bins = [oracle_mod.bin_of(v, r_max, nbins) for v in r2]
     assert all(b0 <= b1 for b0, b1 in zip(bins, bins[1:]))
     assert oracle_mod.bin_of(r_max * r_max, r_max, nbins) == nbins
+
+
+# ---------------------------------------------------------------- g(r) normalisation (Eq. 1)
+
+
+def test_rdf_hand_shells(oracle_mod):
+    # dr = 1: the shells hold (4 pi / 3)(1, 7, 19); at pair density 3 / (4 pi) a uniform
+    # distribution puts 1, 7 and 19 pairs in them, so these counts give g = 1 in every bin
+    g = oracle_mod.rdf(np.array([[1, 7, 19]], np.uint64), 3.0, [3.0 / (4.0 * math.pi)], 1)
+    assert np.allclose(g, 1.0, rtol=1e-14, atol=0)
+
+
+def test_rdf_frames_and_density_scale(oracle_mod):
+    c = np.array([[5, 0, 40, 123], [2, 9, 0, 77]], np.uint64)
+    g1 = oracle_mod.rdf(c, 2.0, [0.5, 0.25], 1)
+    # counts summed over 4 identical frames, divided by 4 frames: the same g
+    assert np.allclose(oracle_mod.rdf(c * np.uint64(4), 2.0, [0.5, 0.25], 4), g1, rtol=1e-14, atol=0)
+    # twice the pair density: half the g
+    assert np.allclose(oracle_mod.rdf(c, 2.0, [1.0, 0.5], 1), 0.5 * g1, rtol=1e-14, atol=0)
+    # bin k of width dr = r_max / nbins holds (4 pi / 3) dr^3 (3k^2 + 3k + 1) of volume
+    dr = 0.5
+    shell = 4.0 * math.pi / 3.0 * dr ** 3 * np.array([1.0, 7.0, 19.0, 37.0])
+    assert np.allclose(g1[0], c[0] / (0.5 * shell), rtol=1e-13, atol=0)
+
+
+def test_rdf_ideal_gas_is_one(oracle_mod):
+    # uniform particles in a periodic box (r_max <= L/2): g = 1 up to counting noise, for the
+    # two intra-species histograms (N_a(N_a-1)/2 / V) and the inter-species one (N_a N_b / V)
+    box = w.ortho_box(24.0)
+    r_max, nbins = 12.0, 30
+    f = w.uniform_frame(22, 6000, ORTHO, box, r_max, nbins, n_species=2)
+    h = oracle_mod.histogram_frame(f, nthreads=8)
+    na, nb = f.species_sizes()
+    V = w.box_volume(box)
+    dens = [na * (na - 1) / 2 / V, na * nb / V, nb * (nb - 1) / 2 / V]
+    g = oracle_mod.rdf(h, r_max, dens, 1)
+    dr = r_max / nbins
+    k = np.arange(nbins, dtype=np.float64)
+    for hh in range(3):
+        expect = dens[hh] * 4.0 * math.pi / 3.0 * dr ** 3 * (3 * k * k + 3 * k + 1)
+        z = (g[hh] - 1.0) * np.sqrt(expect)  # Poisson: sd of g is 1/sqrt(expected count)
+        assert np.all(np.abs(z) < 6.0), np.abs(z).max()
+        assert abs((g[hh] * expect).sum() / expect.sum() - 1.0) < 0.01
