@@ -73,9 +73,10 @@ typedef enum { DH_BOX_NONE = 0, DH_BOX_ORTHO = 1, DH_BOX_TRICLINIC = 2 } dh_box_
 #define DH_CFG_NO_GRAPH 0x1u /* batched path: launch directly instead of replaying a CUDA graph */
 #define DH_CFG_TIMING 0x2u   /* record CUDA events around the pair-kernel launches (dh_stats.pair_kernel_ms) */
 #define DH_CFG_AUTOTUNE 0x4u /* plain and batched paths: measure the launch shapes (j-tile length,
-                                private histogram copies per block, blocks per SM) of every new
-                                launch key on a synthetic batch of its shape before the first call
-                                that needs it, and use the fastest; see dh_tune_cache_count */
+                                threads per block, private histogram copies per block, blocks per
+                                SM) of every new launch key on a synthetic batch of its shape
+                                before the first call that needs it, and use the fastest; see
+                                dh_tune_cache_count */
 
 typedef struct dh_ctx dh_ctx;
 
@@ -121,8 +122,8 @@ typedef struct {
   double pair_kernel_ms;   /* device time of the pair-kernel launches (needs DH_CFG_TIMING), else 0 */
   int32_t tile_j;          /* launch shape of the largest pair-kernel launch: j-tile length, */
   int32_t hist_depth;      /*   private histogram copies per block, */
-  int32_t blocks_per_sm;   /*   and blocks per SM */
-  int32_t reserved;
+  int32_t blocks_per_sm;   /*   blocks per SM */
+  int32_t block_threads;   /*   and threads per block */
 } dh_stats;
 
 /* Create a context on config->device (NULL: device 0, defaults).  Owns a CUDA
@@ -175,6 +176,23 @@ dh_status dh_wait(dh_ctx* ctx, uint64_t ticket, uint64_t timeout_ns);
 /* Cancel a queued or running request; its output is left unspecified. */
 dh_status dh_cancel(dh_ctx* ctx, uint64_t ticket);
 
+/* Radial distribution function g(r) of Eq. 1 from histograms summed over the
+ * frames of a trajectory (Eqs. 2-4; sum the frames into one histogram with
+ * DH_ACCUMULATE).  For each of n_hist histograms of nbins bins:
+ *   g[h][k] = (counts[h][k] / n_frames) / (pair_density[h] * (4 pi / 3)(r_{k+1}^3 - r_k^3)),
+ * r_k = k r_max / nbins: the mean pairs per frame in bin k over the pairs that a
+ * uniform pair density puts in its spherical shell (the finite-bin form of the
+ * 4 pi r^2 dr of Eq. 1).  pair_density is a host array of n_hist values N_pairs / V
+ * (N_a (N_a - 1) / 2 / V within a species, N_a N_b / V between two; the caller
+ * chooses V, e.g. the box volume, or its average over the frames).  counts
+ * (uint64) and g (double) are device pointers on the context's device, n_hist x
+ * nbins row-major.  Binary64 arithmetic on the GPU, on the context's stream; the
+ * call returns when g is written.  DH_ERR_INVALID: NULL pointers, n_hist < 1,
+ * nbins outside [1, DH_MAX_BINS], r_max not > 0 and finite, n_frames = 0, or a
+ * pair density not > 0 and finite. */
+dh_status dh_rdf(dh_ctx* ctx, const uint64_t* counts, int32_t n_hist, int32_t nbins, double r_max,
+                 const double* pair_density, uint64_t n_frames, double* g);
+
 /* Statistics of the last dh_histogram / dh_histogram_batch call on ctx. */
 dh_status dh_get_stats(dh_ctx* ctx, dh_stats* stats);
 
@@ -192,12 +210,13 @@ dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds);
  * that dh_create reads and the autotuner rewrites (DH_CFG_AUTOTUNE with
  * dh_config.tune_cache): lines starting with '#' are comments, every other line
  * is one launch key and its measured shape,
- *   sms variant width_log2 n_log2 frames_log4 tile_j depth bps gpairs_s
+ *   sms variant width_log2 n_log2 frames_log4 tile_j block depth bps gpairs_s
  * (variant: 0 none, 1 orthorhombic, 2 triclinic, 3 triclinic with the
  * 27-image search; width_log2 = ceil(log2 of the shared-memory histogram
  * width); n_log2 = round(log2 of the mean particles per frame); frames_log4 =
  * min(3, floor(log4 of the frames per launch)); tile_j in {256, 512, 1024};
- * depth in {1, 2, 4}; bps >= 1; gpairs_s > 0).  *n_entries receives the number
+ * block, the threads per block, in {256, 512}; depth in {1, 2, 4}; bps, the
+ * blocks per SM, >= 1 (at most what fits is used); gpairs_s > 0).  *n_entries receives the number
  * of distinct launch keys with a well-formed line for a GPU with sm_count SMs
  * (a later line replaces an earlier one of the same key); lines for other SM
  * counts and malformed lines are skipped.  DH_ERR_NOTFOUND if the file cannot

@@ -65,7 +65,7 @@ class dh_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int32), ("graph_replays", ctypes.c_int32),
                 ("tune_runs", ctypes.c_int32), ("pair_kernel_ms", ctypes.c_double),
                 ("tile_j", ctypes.c_int32), ("hist_depth", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +99,8 @@ _SIGNATURES = {
     "dh_selfcheck": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                       ctypes.c_void_p], ctypes.c_int),
     "dh_histogram_noalloc": ([ctypes.POINTER(dh_frame), ctypes.c_void_p], ctypes.c_int),
+    "dh_rdf": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                ctypes.c_uint64, ctypes.c_void_p], ctypes.c_int),
     "dh_tune_cache_count": ([ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
 }
 
@@ -224,6 +226,16 @@ def dh_histogram_noalloc(frame: dh_frame, stream_ptr: int | None = None) -> None
     _check(load_library().dh_histogram_noalloc(ctypes.byref(frame), ctypes.c_void_p(stream_ptr or 0)))
 
 
+def dh_rdf(ctx, counts_ptr: int, n_hist: int, nbins: int, r_max: float, pair_density, n_frames: int,
+           g_ptr: int) -> None:
+    """g(r) of Eq. 1 on the device: counts_ptr (uint64) and g_ptr (double) are device pointers."""
+    dens = np.ascontiguousarray(pair_density, dtype=np.float64).reshape(-1)
+    if dens.shape[0] != int(n_hist):
+        raise ValueError("one pair density per histogram")
+    _check(load_library().dh_rdf(ctx, ctypes.c_void_p(counts_ptr), int(n_hist), int(nbins), float(r_max),
+                                 dens.ctypes.data_as(ctypes.c_void_p), int(n_frames), ctypes.c_void_p(g_ptr)), ctx)
+
+
 def dh_get_stats(ctx) -> dict:
     s = dh_stats()
     _check(load_library().dh_get_stats(ctx, ctypes.byref(s)), ctx)
@@ -339,6 +351,21 @@ class Context:
 
     def stats(self) -> dict:
         return dh_get_stats(self.handle)
+
+    def rdf(self, counts, r_max: float, pair_density, n_frames: int):
+        """g(r) (torch float64, same shape) from device histograms `counts` (torch
+        int64/uint64 viewed as counts, shape (n_hist, nbins) or (nbins,)) summed
+        over n_frames frames; pair_density: N_pairs / V per histogram."""
+        import torch
+
+        if not (_is_torch(counts) and counts.is_cuda and counts.is_contiguous()):
+            raise TypeError("counts must be a contiguous CUDA tensor")
+        if counts.dtype not in (torch.int64, torch.uint64):
+            raise TypeError("counts must be 64-bit integers")
+        c2 = counts.reshape(-1, counts.shape[-1])
+        g = torch.empty(counts.shape, dtype=torch.float64, device=counts.device)
+        dh_rdf(self.handle, c2.data_ptr(), c2.shape[0], c2.shape[1], r_max, pair_density, n_frames, g.data_ptr())
+        return g
 
     def check_sqrt(self) -> float:
         return float(dh_selfcheck(self.handle, DH_CHECK_SQRT)[0])

@@ -15,10 +15,10 @@ enum Variant : int32_t {
   V_TRIC_SEARCH = 3,  // triclinic, larger r_max: Eq. 5 wrap plus the 27-image search
 };
 
-constexpr int kBlock = 256;          // threads per block of the pair kernel
-constexpr int kRegI = 4;             // i-particles held in registers per thread
-constexpr int kTile = kBlock * kRegI;  // particles per tile edge (i and j)
-constexpr int kWarps = kBlock / 32;
+constexpr int kTile = 1024;          // i particles per work item (and the longest j tile)
+// Pair-kernel blocks: 256 threads with 4 i particles each, or 512 threads with 2.
+constexpr int kBlockSmall = 256;
+constexpr int kBlockLarge = 512;
 constexpr int kQueueCap = 64;        // deferred pairs per warp queue
 constexpr int kNumVariants = 4;
 
@@ -101,6 +101,8 @@ struct PairLaunch {
   Control* ctl;
   int32_t hist_depth;  // private histogram copies per block (warp w uses copy w mod depth); 0 means 1
   int32_t multi;       // nonzero when some sweep of the launch starts above bin 0
+  int32_t block;       // threads per block: kBlockSmall (0 means it) or kBlockLarge
+  int32_t pad;
 };
 
 // ---- launchers (dh_kernels.cu); all enqueue on `stream` and return the launch error
@@ -113,9 +115,11 @@ cudaError_t launch_pairs(const PairLaunch& p, int variant, int grid, size_t smem
 cudaError_t launch_check_sqrt(unsigned long long* out, cudaStream_t stream);
 cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t seed, unsigned long long* out,
                                 cudaStream_t stream);
-size_t pair_kernel_smem(int hist_width, int depth = 1);
+cudaError_t launch_rdf(const uint64_t* counts, int32_t n_hist, int32_t nbins, double r_max,
+                       const double* pair_density, uint64_t n_frames, double* g, cudaStream_t stream);
+size_t pair_kernel_smem(int hist_width, int depth = 1, int block = kBlockSmall);
 int pair_kernel_max_width();
-int pair_kernel_blocks_per_sm(int variant, int hist_width, int depth = 1);
+int pair_kernel_blocks_per_sm(int variant, int hist_width, int depth = 1, int block = kBlockSmall);
 
 // Host/device shared definition of the binary64 bin of Alg. 1 (used to build thresholds).
 int64_t host_bin_of(double r2, double r_max, int32_t nbins);

@@ -22,6 +22,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "dh_internal.h"
@@ -335,7 +336,7 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
 
 // ------------------------------------------------------------------ A2-A8: pair kernel
 
-constexpr int kJU = 4;  // j particles per deferral-mask group (mask bit = u * kRegI + r)
+constexpr int kJU = 4;  // j particles per deferral-mask group (mask bit = u * RI + r)
 
 struct FastParams {
   float S2;
@@ -716,18 +717,19 @@ __device__ __noinline__ int drain_queue(const FrameDev* F, int pass, int i0, uin
 
 // j tile in shared memory as pairs of particles: A[p] = {x_2p, x_2p+1, y_2p, y_2p+1},
 // Z[p] = {z_2p, z_2p+1}, so one LDS.128 + one LDS.64 feed two j particles.
-template <int V, bool MASKED, bool MULTI>
+template <int V, bool MASKED, bool MULTI, int RI>
 __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
                                          const float4* __restrict__ sjA, const float2* __restrict__ sjZ,
                                          uint32_t* sh, uint2* q, int tid, int lane, unsigned& ndeferred) {
-  float2 xi[kRegI], yi[kRegI], zi[kRegI];  // i coordinates broadcast to both halves
+  constexpr int BLOCK = kTile / RI;
+  float2 xi[RI], yi[RI], zi[RI];  // i coordinates broadcast to both halves
   const int ibase = it.i0 + tid;
 #pragma unroll
-  for (int r = 0; r < kRegI; ++r) {
-    int li = tid + r * kBlock;
+  for (int r = 0; r < RI; ++r) {
+    int li = tid + r * BLOCK;
     float x = __int_as_float(0x7fffffff), y = x, z = x;
     if (li < it.ni) {
-      float4 p = __ldg(F->X + ibase + r * kBlock);
+      float4 p = __ldg(F->X + ibase + r * BLOCK);
       x = p.x; y = p.y; z = p.z;
     }
     xi[r] = bc2(-x); yi[r] = bc2(-y); zi[r] = bc2(-z);  // negated: d = xj + (-xi)
@@ -749,20 +751,20 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
       const float2 Z = sjZ[(jj0 + u) >> 1];
       const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
 #pragma unroll
-      for (int r = 0; r < kRegI; ++r) {
+      for (int r = 0; r < RI; ++r) {
         float2 dx = add2(xj, xi[r]);
         float2 dy = add2(yj, yi[r]);
         float2 dz = add2(Z, zi[r]);
         if (MASKED) {
           // intra-species: only j > i; all three components so no later test sees a number
-          const int ig = ibase + r * kBlock, jg = it.j0 + jj0 + u;
+          const int ig = ibase + r * BLOCK, jg = it.j0 + jj0 + u;
           if (!(jg > ig)) { dx.x = qnan; dy.x = qnan; dz.x = qnan; }
           if (!(jg + 1 > ig)) { dx.y = qnan; dy.y = qnan; dz.y = qnan; }
         }
         float2 sm, e, bound;
         decide_arith2<V, MULTI>(dx, dy, dz, P, chi, clo, sm, e, bound);
-        count_or_defer(sm.x, e.x, bound.x, hbase, 1u << (u * kRegI + r), dmask);
-        count_or_defer(sm.y, e.y, bound.y, hbase, 1u << ((u + 1) * kRegI + r), dmask);
+        count_or_defer(sm.x, e.x, bound.x, hbase, 1u << (u * RI + r), dmask);
+        count_or_defer(sm.y, e.y, bound.y, hbase, 1u << ((u + 1) * RI + r), dmask);
       }
     }
     // queue the deferred pairs: one per lane per round, compacted with a ballot
@@ -772,7 +774,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
         int b = __ffs(dmask) - 1;
         dmask &= dmask - 1u;
         int pos = qcount + __popc(bal & lt_mask);
-        q[pos] = make_uint2((unsigned)(ibase + (b & (kRegI - 1)) * kBlock), (unsigned)(it.j0 + jj0 + b / kRegI));
+        q[pos] = make_uint2((unsigned)(ibase + (b % RI) * BLOCK), (unsigned)(it.j0 + jj0 + b / RI));
       }
       int added = __popc(bal);
       qcount += added;
@@ -793,19 +795,20 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
 // descriptor) so that only the fields of this variant are live in the loop.
 // MULTI: some sweep of the launch starts above bin 0, so the root is also
 // clamped from below (valid for every sweep, a separate kernel for registers).
-template <int V, bool MULTI>
+template <int V, bool MULTI, int RI>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
                          uint2* q, int tid, int lane, unsigned& ndeferred) {
   FastParams P;
   load_fast_params(*F, it.pass, P);
-  if (it.masked) run_tile<V, true, MULTI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
-  else run_tile<V, false, MULTI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
+  if (it.masked) run_tile<V, true, MULTI, RI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
+  else run_tile<V, false, MULTI, RI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
 }
 
 // Adds the `depth` private copies (stride words apart) bin by bin into the
 // global uint64 histogram and clears them, with their guard words.
 __device__ void flush_hist(uint32_t* sh, int width, int depth, int stride, uint64_t* dst, int tid) {
-  for (int k = tid; k < width; k += kBlock) {
+  const int nthreads = blockDim.x;
+  for (int k = tid; k < width; k += nthreads) {
     uint32_t v = 0u;
     for (int c = 0; c < depth; ++c) {
       v += sh[c * stride + k];
@@ -813,7 +816,7 @@ __device__ void flush_hist(uint32_t* sh, int width, int depth, int stride, uint6
     }
     if (v) atomicAdd((unsigned long long*)(dst + k), (unsigned long long)v);
   }
-  for (int k = tid; k < depth * 2 * kGuard; k += kBlock) {
+  for (int k = tid; k < depth * 2 * kGuard; k += nthreads) {
     int c = k / (2 * kGuard), g = k - c * 2 * kGuard;
     sh[c * stride + (g < kGuard ? g - kGuard : width + g - kGuard)] = 0u;
   }
@@ -882,13 +885,16 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
 
 // One instance per minimum-image variant V (every segment of the launch has a
 // frame of that variant) and per MULTI.
-template <int V>
+// Register budgets: 256-thread blocks keep three (two for the search variant)
+// blocks per SM; 512-thread blocks, meant for wide histograms, one.
+template <int V, int RI>
 constexpr int min_blocks_per_sm() {
-  return (V == V_NONE || V == V_ORTHO || V == V_TRIC) ? 3 : 2;
+  return RI == 2 ? 1 : ((V == V_NONE || V == V_ORTHO || V == V_TRIC) ? 3 : 2);
 }
 
-template <int V, bool MULTI>
-__global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(PairLaunch L) {
+template <int V, bool MULTI, int RI>
+__global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_kernel(PairLaunch L) {
+  constexpr int BLOCK = kTile / RI;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // `depth` private histogram copies, each [kGuard guard words | bins | kGuard
   // guard words] (stride words), then the j tile and the per-warp queues
@@ -903,7 +909,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(Pa
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint2* q = sq + warp * kQueueCap;
   uint32_t* sh = hist0 + (warp % depth) * stride;  // this warp's copy
-  for (int k = tid; k < depth * stride; k += kBlock) reinterpret_cast<uint32_t*>(smem_raw)[k] = 0u;
+  for (int k = tid; k < depth * stride; k += BLOCK) reinterpret_cast<uint32_t*>(smem_raw)[k] = 0u;
 
   const FrameDev* cur_fd = nullptr;
   int cur_h = -1, cur_pass = -1;
@@ -951,7 +957,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(Pa
       since += pairs;
       // stage the j tile in pair layout, padded with NaN particles to a multiple of kJU
       const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);
-      for (int k = tid; k < nj4; k += kBlock) {
+      for (int k = tid; k < nj4; k += BLOCK) {
         float4 v;
         if (k < it.nj) v = __ldg(F.X + it.j0 + k);
         else v = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff), __int_as_float(0x7fffffff), 0.f);
@@ -962,7 +968,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks_per_sm<V>()) pair_kernel(Pa
       }
       __syncthreads();
       unsigned ndef = 0;
-      run_item<V, MULTI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef);
+      run_item<V, MULTI, RI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();
@@ -1080,11 +1086,41 @@ cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ g(r), Eq. 1
+
+// g = (counts / n_frames) / (pair density x shell volume) per bin, binary64.
+// The shell of bin k, (4 pi / 3)(r_{k+1}^3 - r_k^3) with r_k = k dr, is
+// evaluated as (4 pi / 3) dr^3 (3k(k+1) + 1): the integer factor is exact for
+// k < 2^25, so no cancellation between the two cubes.
+__global__ void rdf_kernel(const uint64_t* __restrict__ counts, int32_t n_hist, int32_t nbins, double r_max,
+                           const double* __restrict__ dens, uint64_t n_frames, double* __restrict__ g) {
+  const int64_t total = (int64_t)n_hist * nbins;
+  const double dr = __ddiv_rn(r_max, (double)nbins);
+  const double c = __dmul_rn(__dmul_rn(4.0 * 3.14159265358979323846 / 3.0, dr), __dmul_rn(dr, dr));
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t h = (int32_t)(idx / nbins);
+    const double k = (double)(idx - (int64_t)h * nbins);
+    const double poly = __fma_rn(__dmul_rn(3.0, k), __dadd_rn(k, 1.0), 1.0);
+    const double per_frame = __ddiv_rn((double)counts[idx], (double)n_frames);
+    g[idx] = __ddiv_rn(per_frame, __dmul_rn(dens[h], __dmul_rn(c, poly)));
+  }
+}
+
+cudaError_t launch_rdf(const uint64_t* counts, int32_t n_hist, int32_t nbins, double r_max,
+                       const double* pair_density, uint64_t n_frames, double* g, cudaStream_t stream) {
+  int64_t total = (int64_t)n_hist * nbins;
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  rdf_kernel<<<blocks, 256, 0, stream>>>(counts, n_hist, nbins, r_max, pair_density, n_frames, g);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 
-size_t pair_kernel_smem(int hist_width, int depth) {
+size_t pair_kernel_smem(int hist_width, int depth, int block) {
   size_t stride = (size_t)((hist_width + 3) & ~3) + 2 * kGuard;
-  return (size_t)(depth > 1 ? depth : 1) * stride * 4 + (size_t)kTile * 12 + (size_t)kWarps * kQueueCap * 8;
+  size_t warps = (size_t)(block == kBlockLarge ? kBlockLarge : kBlockSmall) / 32;
+  return (size_t)(depth > 1 ? depth : 1) * stride * 4 + (size_t)kTile * 12 + warps * kQueueCap * 8;
 }
 
 int pair_kernel_max_width() {
@@ -1097,23 +1133,28 @@ int pair_kernel_max_width() {
   return (int)(((size_t)optin - fixed) / 4) & ~3;
 }
 
-template <int V>
-int blocks_per_sm_v(int hist_width, int depth) {
-  size_t smem = pair_kernel_smem(hist_width, depth);
+template <int V, int RI>
+int blocks_per_sm_vr(size_t smem) {
   int nb0 = 0, nb1 = 0;
-  cudaFuncSetAttribute(pair_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, pair_kernel<V, false>, kBlock, smem);
-  cudaFuncSetAttribute(pair_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, pair_kernel<V, true>, kBlock, smem);
+  cudaFuncSetAttribute(pair_kernel<V, false, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, pair_kernel<V, false, RI>, kTile / RI, smem);
+  cudaFuncSetAttribute(pair_kernel<V, true, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, pair_kernel<V, true, RI>, kTile / RI, smem);
   return nb0 < nb1 ? nb0 : nb1;
 }
 
-int pair_kernel_blocks_per_sm(int variant, int hist_width, int depth) {
+template <int V>
+int blocks_per_sm_v(int hist_width, int depth, int block) {
+  size_t smem = pair_kernel_smem(hist_width, depth, block);
+  return block == kBlockLarge ? blocks_per_sm_vr<V, 2>(smem) : blocks_per_sm_vr<V, 4>(smem);
+}
+
+int pair_kernel_blocks_per_sm(int variant, int hist_width, int depth, int block) {
   switch (variant) {
-    case V_NONE: return blocks_per_sm_v<V_NONE>(hist_width, depth);
-    case V_ORTHO: return blocks_per_sm_v<V_ORTHO>(hist_width, depth);
-    case V_TRIC: return blocks_per_sm_v<V_TRIC>(hist_width, depth);
-    default: return blocks_per_sm_v<V_TRIC_SEARCH>(hist_width, depth);
+    case V_NONE: return blocks_per_sm_v<V_NONE>(hist_width, depth, block);
+    case V_ORTHO: return blocks_per_sm_v<V_ORTHO>(hist_width, depth, block);
+    case V_TRIC: return blocks_per_sm_v<V_TRIC>(hist_width, depth, block);
+    default: return blocks_per_sm_v<V_TRIC_SEARCH>(hist_width, depth, block);
   }
 }
 
@@ -1137,13 +1178,19 @@ cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* s
   return cudaGetLastError();
 }
 
+template <int V, bool MULTI, int RI>
+cudaError_t launch_pairs_vmr(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
+  cudaError_t e =
+      cudaFuncSetAttribute(pair_kernel<V, MULTI, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  pair_kernel<V, MULTI, RI><<<grid, kTile / RI, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
 template <int V, bool MULTI>
 cudaError_t launch_pairs_vm(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
-  cudaError_t e =
-      cudaFuncSetAttribute(pair_kernel<V, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  pair_kernel<V, MULTI><<<grid, kBlock, smem, stream>>>(p);
-  return cudaGetLastError();
+  return p.block == kBlockLarge ? launch_pairs_vmr<V, MULTI, 2>(p, grid, smem, stream)
+                                : launch_pairs_vmr<V, MULTI, 4>(p, grid, smem, stream);
 }
 
 template <int V>

@@ -452,10 +452,14 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
     const int width = vsum[v].width;
     P.vmulti[v] = vsum[v].multi;
     LaunchParams& lp = P.vparams[v];
-    int bps_max = pair_kernel_blocks_per_sm(v, width, lp.depth);
+    int bps_max = pair_kernel_blocks_per_sm(v, width, lp.depth, lp.block);
     if (bps_max < 1 && lp.depth > 1) {
       lp.depth = 1;  // the copies do not fit: one copy
-      bps_max = pair_kernel_blocks_per_sm(v, width, 1);
+      bps_max = pair_kernel_blocks_per_sm(v, width, 1, lp.block);
+    }
+    if (bps_max < 1 && lp.block != kBlockSmall) {
+      lp.block = kBlockSmall;  // the larger block's queues do not fit either
+      bps_max = pair_kernel_blocks_per_sm(v, width, 1, kBlockSmall);
     }
     if (bps_max < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", width);
     lp.bps = lp.bps > 0 ? std::min(lp.bps, bps_max) : bps_max;
@@ -511,8 +515,10 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
       L.hist_width = P.vwidth[v];
       L.hist_depth = P.vparams[v].depth;
       L.multi = P.vmulti[v];
+      L.block = P.vparams[v].block;
       L.ctl = (Control*)c->ctl.p + v;
-      DH_CUDA_TRY(launch_pairs(L, v, P.vgrid[v], pair_kernel_smem(P.vwidth[v], P.vparams[v].depth), st));
+      DH_CUDA_TRY(launch_pairs(L, v, P.vgrid[v],
+                               pair_kernel_smem(P.vwidth[v], P.vparams[v].depth, P.vparams[v].block), st));
       ++launched;
       grid = std::max(grid, P.vgrid[v]);
       if (P.vitems[v] > top_items) {
@@ -535,6 +541,7 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
     S.tile_j = kTile / P.vparams[top].jm;
     S.hist_depth = P.vparams[top].depth;
     S.blocks_per_sm = P.vparams[top].bps;
+    S.block_threads = P.vparams[top].block;
   }
   return DH_OK;
 }
@@ -791,21 +798,23 @@ dh_status tune_variant(dh_ctx* c, int v, const VariantSummary& vs) {
   };
   double g = 0.0;
   s = measure(LaunchParams{}, &g);  // warm-up (first launches of a shape)
-  for (int jm = 1; jm <= 4 && s == DH_OK; jm *= 2)
-    for (int depth = 1; depth <= 4 && s == DH_OK; depth *= 2) {
-      int bmax = pair_kernel_blocks_per_sm(v, vs.width, depth);
-      for (int bps = bmax; bps >= 1 && bps >= bmax - 1 && s == DH_OK; --bps) {
-        LaunchParams p;
-        p.jm = jm;
-        p.depth = depth;
-        p.bps = bps;
-        s = measure(p, &g);
-        if (s == DH_OK && g > best.gpairs_s) {
-          best.p = p;
-          best.gpairs_s = g;
+  for (int block : {kBlockSmall, kBlockLarge})
+    for (int jm = 1; jm <= 4 && s == DH_OK; jm *= 2)
+      for (int depth = 1; depth <= 4 && s == DH_OK; depth *= 2) {
+        int bmax = pair_kernel_blocks_per_sm(v, vs.width, depth, block);
+        for (int bps = bmax; bps >= 1 && bps >= bmax - 1 && s == DH_OK; --bps) {
+          LaunchParams p;
+          p.jm = jm;
+          p.depth = depth;
+          p.bps = bps;
+          p.block = block;
+          s = measure(p, &g);
+          if (s == DH_OK && g > best.gpairs_s) {
+            best.p = p;
+            best.gpairs_s = g;
+          }
         }
       }
-    }
   c->tune_forced = false;
   if (own_events) {
     cudaEventDestroy(c->ev_pair0);
@@ -905,6 +914,26 @@ dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds) {
   return DH_OK;
 }
 
+dh_status dh_rdf(dh_ctx* c, const uint64_t* counts, int32_t n_hist, int32_t nbins, double r_max,
+                 const double* pair_density, uint64_t n_frames, double* g) {
+  if (!c || !counts || !pair_density || !g) return fail(DH_ERR_INVALID, "NULL argument");
+  if (n_hist < 1) return fail(DH_ERR_INVALID, "n_hist must be >= 1");
+  if (nbins < 1 || nbins > DH_MAX_BINS) return fail(DH_ERR_INVALID, "nbins out of range");
+  if (!(r_max > 0.0) || !std::isfinite(r_max)) return fail(DH_ERR_INVALID, "r_max must be > 0 and finite");
+  if (n_frames == 0) return fail(DH_ERR_INVALID, "n_frames must be >= 1");
+  for (int32_t h = 0; h < n_hist; ++h)
+    if (!(pair_density[h] > 0.0) || !std::isfinite(pair_density[h]))
+      return fail(DH_ERR_INVALID, "pair density %d must be > 0 and finite", h);
+  std::lock_guard<std::recursive_mutex> g_(c->mu);
+  DH_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream();
+  DH_CUDA_TRY(c->aux.ensure(sizeof(double) * (size_t)n_hist));
+  DH_CUDA_TRY(cudaMemcpyAsync(c->aux.p, pair_density, sizeof(double) * (size_t)n_hist, cudaMemcpyHostToDevice, st));
+  DH_CUDA_TRY(launch_rdf(counts, n_hist, nbins, r_max, (const double*)c->aux.p, n_frames, g, st));
+  DH_CUDA_TRY(cudaStreamSynchronize(st));
+  return DH_OK;
+}
+
 dh_status dh_create(const dh_config* config, dh_ctx** out) {
   if (!out) return fail(DH_ERR_INVALID, "out is NULL");
   *out = nullptr;
@@ -951,6 +980,7 @@ dh_status dh_destroy(dh_ctx* c) {
   c->meta.release();
   c->ctl.release();
   c->tstat.release();
+  c->aux.release();
   c->hmeta.release();
   c->hout.release();
   if (c->gexec) cudaGraphExecDestroy(c->gexec);

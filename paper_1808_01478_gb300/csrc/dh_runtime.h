@@ -95,9 +95,10 @@ int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::v
 
 // Launch shape of one pair-kernel launch.
 struct LaunchParams {
-  int32_t jm = 1;     // j tiles per i tile: tile_j = kTile / jm
-  int32_t depth = 1;  // private histogram copies per block
-  int32_t bps = 0;    // blocks per SM (0: as many as fit)
+  int32_t jm = 1;                // j tiles per i tile: tile_j = kTile / jm
+  int32_t depth = 1;             // private histogram copies per block
+  int32_t bps = 0;               // blocks per SM (0: as many as fit)
+  int32_t block = kBlockSmall;   // threads per block (kBlockSmall or kBlockLarge)
 };
 
 // Autotuner key of a launch: variant, histogram width, frame size, frame count (all bucketed).
@@ -160,6 +161,7 @@ struct dh_ctx {
   dh::HostBuf hmeta;   // pinned staging for meta
   dh::HostBuf hout;    // pinned staging for accumulate-on-host
   dh::DevBuf tstat;    // threshold build status
+  dh::DevBuf aux;      // small per-call arrays (g(r) pair densities)
   dh::ThresholdCache tcache;
   std::vector<const double*> held_tables;  // tables referenced by work not yet finished
 

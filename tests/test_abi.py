@@ -78,16 +78,17 @@ def test_tune_cache_file_parsing(lib, tmp_path):
     p = tmp_path / "tune.txt"
     p.write_text("\n".join([
         "# comment line",
-        "152 1 14 17 0 1024 1 3 1282.4",   # ortho, 10k bins, N ~ 2^17, one frame
-        "152 1 14 17 0 512 2 2 1290.0",    # same key again: replaces the line above
-        "152 0 12 13 3 256 4 1 900.5",     # none, 4096 bins, many frames
-        "148 2 15 19 0 1024 1 3 1000.0",   # another SM count
-        "152 2 15 19 0 1000 1 3 1000.0",   # tile_j not a power-of-two tile
-        "152 2 15 19 0 1024 3 3 1000.0",   # depth 3 not offered
-        "152 9 15 19 0 1024 1 3 1000.0",   # unknown variant
-        "152 2 15 19 0 1024 1 3 -1",       # non-positive throughput
-        "152 2 15 19",                     # truncated
-        "152 3 16 20 1 1024 1 2 500.0",
+        "152 1 14 17 0 1024 256 1 3 1282.4",   # ortho, 10k bins, N ~ 2^17, one frame
+        "152 1 14 17 0 512 512 2 2 1290.0",    # same key again: replaces the line above
+        "152 0 12 13 3 256 256 4 1 900.5",     # none, 4096 bins, many frames
+        "148 2 15 19 0 1024 256 1 3 1000.0",   # another SM count
+        "152 2 15 19 0 1000 256 1 3 1000.0",   # tile_j not a power-of-two tile
+        "152 2 15 19 0 1024 256 3 3 1000.0",   # depth 3 not offered
+        "152 2 15 19 0 1024 384 1 3 1000.0",   # block size not offered
+        "152 9 15 19 0 1024 256 1 3 1000.0",   # unknown variant
+        "152 2 15 19 0 1024 256 1 3 -1",       # non-positive throughput
+        "152 2 15 19 0 1024 1 3 1000.0",       # a field missing
+        "152 3 16 20 1 1024 512 1 2 500.0",
     ]) + "\n")
     assert dh.dh_tune_cache_count(str(p), 152) == 3
     assert dh.dh_tune_cache_count(str(p), 148) == 1

@@ -1,8 +1,8 @@
 """Autotuned launch shapes (DH_CFG_AUTOTUNE, dh_config.tune_cache).
 
-Every launch shape the autotuner may pick (j-tile length 256/512/1024, one to
-four private histogram copies per block, blocks per SM) must give the FP64
-oracle's histogram bin for bin; the shapes are forced through the tuner's own
+Every launch shape the autotuner may pick (j-tile length 256/512/1024, blocks
+of 256 or 512 threads, one to four private histogram copies per block, blocks
+per SM) must give the FP64 oracle's histogram bin for bin; the shapes are forced through the tuner's own
 cache file.  The autotuner must measure each new launch key once, record it in
 the file, and a context that reads the file must use it without measuring.
 """
@@ -50,10 +50,10 @@ def tune_key(frames):
     return variant_of(frames[0]), wl, nl, f4
 
 
-def write_cache(path, sms, keys, tile_j, depth, bps):
+def write_cache(path, sms, keys, tile_j, depth, bps, block=256):
     lines = ["# forced shapes"]
     for v, wl, nl, f4 in keys:
-        lines.append(f"{sms} {v} {wl} {nl} {f4} {tile_j} {depth} {bps} 1.0")
+        lines.append(f"{sms} {v} {wl} {nl} {f4} {tile_j} {block} {depth} {bps} 1.0")
     path.write_text("\n".join(lines) + "\n")
 
 
@@ -74,22 +74,23 @@ FRAMES = {
     "tric_2species": w.uniform_frame(33, 2600, w.BOX_TRICLINIC, TRIC, 9.0, 3000, n_species=2),
     "tric_search": w.uniform_frame(34, 1500, w.BOX_TRICLINIC, TRIC, 14.0, 2000),
 }
-SHAPES = [(256, 1, 3), (512, 2, 2), (256, 4, 1), (1024, 2, 3), (512, 4, 2), (1024, 1, 1)]
+SHAPES = [(256, 1, 3, 256), (512, 2, 2, 256), (256, 4, 1, 256), (1024, 2, 3, 256), (512, 4, 2, 256),
+          (1024, 1, 1, 256), (1024, 1, 1, 512), (256, 2, 1, 512), (512, 4, 1, 512)]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"tj{s[0]}_d{s[1]}_b{s[2]}")
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"tj{s[0]}_d{s[1]}_b{s[2]}_t{s[3]}")
 def test_forced_shapes_match_oracle(torch_mod, oracle_mod, tmp_path, shape):
-    tile_j, depth, bps = shape
+    tile_j, depth, bps, block = shape
     sms = sm_count(torch_mod)
     path = tmp_path / "tune.txt"
-    write_cache(path, sms, [tune_key([f]) for f in FRAMES.values()], tile_j, depth, bps)
+    write_cache(path, sms, [tune_key([f]) for f in FRAMES.values()], tile_j, depth, bps, block)
     assert dh.dh_tune_cache_count(str(path), sms) == len(FRAMES)
     with dh.Context(0, tune_cache=str(path)) as ctx:
         for name, f in FRAMES.items():
             x = torch_mod.from_numpy(f.coords).cuda()
             got = ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins).cpu().numpy().view(np.uint64)
             st = ctx.stats()
-            assert (st["tile_j"], st["hist_depth"]) == (tile_j, depth), name
+            assert (st["tile_j"], st["hist_depth"], st["block_threads"]) == (tile_j, depth, block), name
             assert 1 <= st["blocks_per_sm"] <= bps
             assert st["tune_runs"] == 0
             assert np.array_equal(got, oracle_mod.histogram_frame(f)), name
@@ -101,12 +102,12 @@ def test_forced_shape_multi_sweep(torch_mod, oracle_mod, tmp_path):
     sms = sm_count(torch_mod)
     v, _, nl, f4 = tune_key([f])
     path = tmp_path / "tune.txt"
-    write_cache(path, sms, [(v, wl, nl, f4) for wl in range(14, 18)], 512, 2, 2)
+    write_cache(path, sms, [(v, wl, nl, f4) for wl in range(14, 18)], 512, 2, 2, 512)
     with dh.Context(0, tune_cache=str(path)) as ctx:
         x = torch_mod.from_numpy(f.coords).cuda()
         got = ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins).cpu().numpy().view(np.uint64)
         st = ctx.stats()
-        assert st["sweeps"] >= 2 and st["tile_j"] == 512
+        assert st["sweeps"] >= 2 and st["tile_j"] == 512 and st["block_threads"] in (256, 512)
         assert np.array_equal(got, oracle_mod.histogram_frame(f))
 
 
@@ -120,8 +121,9 @@ def test_autotune_measures_once_and_reuses_the_file(torch_mod, oracle_mod, tmp_p
         ctx.histogram_batch(fas)
         st = ctx.stats()
         assert st["tune_runs"] > 1
-        shape = (st["tile_j"], st["hist_depth"], st["blocks_per_sm"])
+        shape = (st["tile_j"], st["hist_depth"], st["blocks_per_sm"], st["block_threads"])
         assert shape[0] in (256, 512, 1024) and shape[1] in (1, 2, 4) and shape[2] >= 1
+        assert shape[3] in (256, 512)
         for fa, f in zip(fas, frames):
             assert np.array_equal(result(fa), oracle_mod.histogram_frame(f)), f.name
         ctx.histogram_batch(fas)  # same key: no new measurement
@@ -132,6 +134,6 @@ def test_autotune_measures_once_and_reuses_the_file(torch_mod, oracle_mod, tmp_p
         ctx.histogram_batch(fas2)
         st = ctx.stats()
         assert st["tune_runs"] == 0
-        assert (st["tile_j"], st["hist_depth"], st["blocks_per_sm"]) == shape
+        assert (st["tile_j"], st["hist_depth"], st["blocks_per_sm"], st["block_threads"]) == shape
         for fa, fb in zip(fas, fas2):
             assert np.array_equal(result(fa), result(fb))
