@@ -439,11 +439,22 @@ def run_served_c5(dev_index, dev, args):
 # ---------------------------------------------------------------- GPU arm
 
 
+def scan_frame(box_name: str, n: int, nbins: int):
+    """One frame of the scan: uniform at density 0.1, orthorhombic cube (r_max = L/2)
+    or the 70/80/100-degree cell (r_max = 0.95 h_min/2)."""
+    if box_name == "triclinic":
+        box = w.scale_box(w.triclinic_box(1.0, 1.0, 1.0, *w.C3_ANGLES), n / 0.1)
+        return w.uniform_frame(101, n, w.BOX_TRICLINIC, box, 0.95 * float(w.box_heights(box).min()) / 2.0, nbins)
+    side = (n / 0.1) ** (1.0 / 3.0)
+    return w.uniform_frame(101, n, w.BOX_ORTHO, w.ortho_box(side), side / 2.0, nbins)
+
+
 def run_scan(args, world, rank, local):
-    """Throughput against histogram width and private-copy depth (plain path, one
-    orthorhombic frame, r_max = L/2): the shared-memory staircase (one more bin
-    sweep each time the width exceeds what a block holds) and the depth tradeoff.
-    One JSON line per point; not the bench contract line."""
+    """Throughput against histogram width, block shape and private copies (plain
+    path, one frame per point): the shared-memory staircase (one more bin sweep
+    each time the width exceeds what a block holds) and the block-shape and
+    depth tradeoffs.  Shapes are forced through the autotuner's cache file.  One
+    JSON line per point; not the bench contract line."""
     import tempfile
 
     import torch
@@ -456,40 +467,39 @@ def run_scan(args, world, rank, local):
     dev = torch.device("cuda", local)
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     tmp = tempfile.mkdtemp(prefix="dh_scan_")
-    for n in args.scan_particles:
-        side = (n / 0.1) ** (1.0 / 3.0)
-        for nbins in args.scan_bins:
-            f = w.uniform_frame(101, n, w.BOX_ORTHO, w.ortho_box(side), side / 2.0, nbins)
-            x = torch.from_numpy(f.coords).to(dev)
-            out = torch.zeros((1, nbins), dtype=torch.int64, device=dev)
-            with dh.Context(local) as c0:  # default shape: learn the sweep width of this frame
-                c0.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
-                sweeps = c0.stats()["sweeps"]
-            width = -(-nbins // sweeps)
-            key = (1, max(0, math.ceil(math.log2(width))),
-                   math.floor(math.log2(math.sqrt(2.0 * max(f.n_pairs(), 1))) + 0.5), 0)
-            ref = None
-            for block, depth in ((256, 1), (256, 2), (256, 4), (512, 1), (512, 2)):
-                path = os.path.join(tmp, f"t_{n}_{nbins}_{block}_{depth}.txt")
-                with open(path, "w") as fh:
-                    fh.write(f"{sms} {key[0]} {key[1]} {key[2]} {key[3]} 1024 {block} {depth} 32 1.0\n")
-                with dh.Context(local, flags=dh.DH_CFG_TIMING, tune_cache=path) as ctx:
+    points = [(b, n, k) for b in args.scan_boxes for n in args.scan_particles for k in args.scan_bins]
+    for box_name, n, nbins in points:
+        f = scan_frame(box_name, n, nbins)
+        x = torch.from_numpy(f.coords).to(dev)
+        out = torch.zeros((1, nbins), dtype=torch.int64, device=dev)
+        with dh.Context(local) as c0:  # default shape: learn the sweep width of this frame
+            c0.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
+            sweeps = c0.stats()["sweeps"]
+        width = -(-nbins // sweeps)
+        key = (1 if f.box_type == w.BOX_ORTHO else 2, max(0, math.ceil(math.log2(width))),
+               math.floor(math.log2(math.sqrt(2.0 * max(f.n_pairs(), 1))) + 0.5), 0)
+        ref = None
+        for block, depth in ((256, 1), (256, 2), (256, 4), (512, 1), (512, 2), (1024, 1)):
+            path = os.path.join(tmp, f"t_{box_name}_{n}_{nbins}_{block}_{depth}.txt")
+            with open(path, "w") as fh:
+                fh.write(f"{sms} {key[0]} {key[1]} {key[2]} {key[3]} 1024 {block} {depth} 32 1.0\n")
+            with dh.Context(local, flags=dh.DH_CFG_TIMING, tune_cache=path) as ctx:
+                ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
+                st = ctx.stats()
+                if (st["hist_depth"], st["block_threads"]) != (depth, block):
+                    continue  # the copies or the larger block do not fit in shared memory
+                ms = []
+                for _ in range(args.scan_reps):
                     ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
-                    st = ctx.stats()
-                    if (st["hist_depth"], st["block_threads"]) != (depth, block):
-                        continue  # the copies or the larger block do not fit in shared memory
-                    ms = []
-                    for _ in range(args.scan_reps):
-                        ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
-                        ms.append(ctx.stats()["pair_kernel_ms"])
-                    got = out.cpu()
-                    ref = got if ref is None else ref
-                    print(json.dumps({"scan": "bins x block x depth", "n": n, "nbins": nbins,
-                                      "sweeps": st["sweeps"], "block_threads": block,
-                                      "hist_depth": depth, "blocks_per_sm": st["blocks_per_sm"],
-                                      "pair_kernel_ms": round(min(ms), 3),
-                                      "gpairs_s": round(f.n_pairs() / (min(ms) / 1e3) / 1e9, 2),
-                                      "same_as_first_shape": bool(torch.equal(got, ref))}), flush=True)
+                    ms.append(ctx.stats()["pair_kernel_ms"])
+                got = out.cpu()
+                ref = got if ref is None else ref
+                print(json.dumps({"scan": "bins x block x depth", "box": box_name, "n": n, "nbins": nbins,
+                                  "sweeps": st["sweeps"], "block_threads": block,
+                                  "hist_depth": depth, "blocks_per_sm": st["blocks_per_sm"],
+                                  "pair_kernel_ms": round(min(ms), 3),
+                                  "gpairs_s": round(f.n_pairs() / (min(ms) / 1e3) / 1e9, 2),
+                                  "same_as_first_shape": bool(torch.equal(got, ref))}), flush=True)
     return 0
 
 
@@ -665,6 +675,7 @@ def main(argv=None) -> int:
     ap.add_argument("--scan-bins", type=int, nargs="*",
                     default=[1024, 4096, 16384, 32768, 50000, 60000, 100000, 160000, 250000])
     ap.add_argument("--scan-reps", type=int, default=3)
+    ap.add_argument("--scan-boxes", nargs="*", default=["ortho", "triclinic"], choices=["ortho", "triclinic"])
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -215,7 +215,7 @@ dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds);
  * 27-image search; width_log2 = ceil(log2 of the shared-memory histogram
  * width); n_log2 = round(log2 of the mean particles per frame); frames_log4 =
  * min(3, floor(log4 of the frames per launch)); tile_j in {256, 512, 1024};
- * block, the threads per block, in {256, 512}; depth in {1, 2, 4}; bps, the
+ * block, the threads per block, in {256, 512, 1024}; depth in {1, 2, 4}; bps, the
  * blocks per SM, >= 1 (at most what fits is used); gpairs_s > 0).  *n_entries receives the number
  * of distinct launch keys with a well-formed line for a GPU with sm_count SMs
  * (a later line replaces an earlier one of the same key); lines for other SM

@@ -16,9 +16,10 @@ enum Variant : int32_t {
 };
 
 constexpr int kTile = 1024;          // i particles per work item (and the longest j tile)
-// Pair-kernel blocks: 256 threads with 4 i particles each, or 512 threads with 2.
+// Pair-kernel blocks: 256 threads with 4 i particles each, 512 with 2, or 1024 with 1.
 constexpr int kBlockSmall = 256;
 constexpr int kBlockLarge = 512;
+constexpr int kBlockHuge = 1024;
 constexpr int kQueueCap = 64;        // deferred pairs per warp queue
 constexpr int kNumVariants = 4;
 
@@ -101,7 +102,7 @@ struct PairLaunch {
   Control* ctl;
   int32_t hist_depth;  // private histogram copies per block (warp w uses copy w mod depth); 0 means 1
   int32_t multi;       // nonzero when some sweep of the launch starts above bin 0
-  int32_t block;       // threads per block: kBlockSmall (0 means it) or kBlockLarge
+  int32_t block;       // threads per block: kBlockSmall (0 means it), kBlockLarge or kBlockHuge
   int32_t pad;
 };
 

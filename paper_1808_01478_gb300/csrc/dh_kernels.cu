@@ -336,7 +336,11 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
 
 // ------------------------------------------------------------------ A2-A8: pair kernel
 
-constexpr int kJU = 4;  // j particles per deferral-mask group (mask bit = u * RI + r)
+// j particles per deferral-mask group: 16 pairs per lane and group whatever the
+// i particles per thread (mask bit = u * RI + r); the j tile is padded to kJUMax
+template <int RI>
+constexpr int ju_of() { return 16 / RI; }
+constexpr int kJUMax = 16;
 
 struct FastParams {
   float S2;
@@ -687,19 +691,21 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P);
 // Decide the first `count` (<= 32) queued pairs, one per lane, move the
 // provisional count of each to its exact bin where they differ, and shift the
 // rest of the queue down.  Out of line so the hot loop keeps its registers.
-// i0 is the first i of the tile: lane (i - i0) mod 32 evaluated the pair.
+// A queue entry is (i - i0) | (j - j0) << 16 for the tile's first i and j;
+// lane (i - i0) mod 32 evaluated the pair.
 template <int V, bool MULTI>
-__device__ __noinline__ int drain_queue(const FrameDev* F, int pass, int i0, uint2* q, int qcount, uint32_t* sh,
-                                        int lane) {
+__device__ __noinline__ int drain_queue(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
+                                        uint32_t* sh, int lane) {
   const int count = qcount < 32 ? qcount : 32;
   unsigned nexact = 0;
   if (lane < count) {
-    uint2 e = q[lane];
-    float4 pi = __ldg(F->X + e.x);
-    float4 pj = __ldg(F->X + e.y);
+    const uint32_t e = q[lane];
+    const int il = (int)(e & 0xFFFFu), jl = (int)(e >> 16);
+    float4 pi = __ldg(F->X + i0 + il);
+    float4 pj = __ldg(F->X + j0 + jl);
     FastParams P;
     load_fast_params(*F, pass, P);
-    int relp = provisional_rel<V, MULTI>(P, pi, pj, (int)((e.x - (uint32_t)i0) & 31u));
+    int relp = provisional_rel<V, MULTI>(P, pi, pj, il & 31);
     int relx = deferred_bin<V>(*F, pi, pj, nexact) - P.lo;
     if (relx != relp) {
       atomicAdd(sh + relp, 0xFFFFFFFFu);  // relp lies in the histogram or its guard words
@@ -720,7 +726,7 @@ __device__ __noinline__ int drain_queue(const FrameDev* F, int pass, int i0, uin
 template <int V, bool MASKED, bool MULTI, int RI>
 __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
                                          const float4* __restrict__ sjA, const float2* __restrict__ sjZ,
-                                         uint32_t* sh, uint2* q, int tid, int lane, unsigned& ndeferred) {
+                                         uint32_t* sh, uint32_t* q, int tid, int lane, unsigned& ndeferred) {
   constexpr int BLOCK = kTile / RI;
   float2 xi[RI], yi[RI], zi[RI];  // i coordinates broadcast to both halves
   const int ibase = it.i0 + tid;
@@ -740,6 +746,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
   const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(sh) - 4u * (uint32_t)P.kb1;
   const float chi = (float)(P.hi + 1 + lane);
   const float clo = (float)(P.lo - lane);
+  constexpr int kJU = ju_of<RI>();
   const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);  // the j tile is padded with NaN particles
   int qcount = 0;
   for (int jj0 = 0; jj0 < nj4; jj0 += kJU) {
@@ -774,20 +781,20 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
         int b = __ffs(dmask) - 1;
         dmask &= dmask - 1u;
         int pos = qcount + __popc(bal & lt_mask);
-        q[pos] = make_uint2((unsigned)(ibase + (b % RI) * BLOCK), (unsigned)(it.j0 + jj0 + b / RI));
+        q[pos] = (uint32_t)(tid + (b % RI) * BLOCK) | ((uint32_t)(jj0 + b / RI) << 16);
       }
       int added = __popc(bal);
       qcount += added;
       ndeferred += added;
       if (qcount >= 32) {
         __syncwarp();
-        qcount = drain_queue<V, MULTI>(F, it.pass, it.i0, q, qcount, sh, lane);
+        qcount = drain_queue<V, MULTI>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane);
       }
       bal = __ballot_sync(kFull, dmask != 0u);
     }
   }
   __syncwarp();
-  if (qcount > 0) drain_queue<V, MULTI>(F, it.pass, it.i0, q, qcount, sh, lane);
+  if (qcount > 0) drain_queue<V, MULTI>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane);
   __syncwarp();
 }
 
@@ -797,7 +804,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
 // clamped from below (valid for every sweep, a separate kernel for registers).
 template <int V, bool MULTI, int RI>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
-                         uint2* q, int tid, int lane, unsigned& ndeferred) {
+                         uint32_t* q, int tid, int lane, unsigned& ndeferred) {
   FastParams P;
   load_fast_params(*F, it.pass, P);
   if (it.masked) run_tile<V, true, MULTI, RI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
@@ -889,7 +896,7 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
 // blocks per SM; 512-thread blocks, meant for wide histograms, one.
 template <int V, int RI>
 constexpr int min_blocks_per_sm() {
-  return RI == 2 ? 1 : ((V == V_NONE || V == V_ORTHO || V == V_TRIC) ? 3 : 2);
+  return RI < 4 ? 1 : ((V == V_NONE || V == V_ORTHO || V == V_TRIC) ? 3 : 2);
 }
 
 template <int V, bool MULTI, int RI>
@@ -903,11 +910,11 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
   uint32_t* hist0 = reinterpret_cast<uint32_t*>(smem_raw) + kGuard;
   float4* sjA = reinterpret_cast<float4*>(reinterpret_cast<uint32_t*>(smem_raw) + depth * stride);
   float2* sjZ = reinterpret_cast<float2*>(sjA + kTile / 2);
-  uint2* sq = reinterpret_cast<uint2*>(sjZ + kTile / 2);
+  uint32_t* sq = reinterpret_cast<uint32_t*>(sjZ + kTile / 2);
   __shared__ ItemDesc s_it;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint2* q = sq + warp * kQueueCap;
+  uint32_t* q = sq + warp * kQueueCap;
   uint32_t* sh = hist0 + (warp % depth) * stride;  // this warp's copy
   for (int k = tid; k < depth * stride; k += BLOCK) reinterpret_cast<uint32_t*>(smem_raw)[k] = 0u;
 
@@ -955,8 +962,8 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
         since = 0;
       }
       since += pairs;
-      // stage the j tile in pair layout, padded with NaN particles to a multiple of kJU
-      const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);
+      // stage the j tile in pair layout, padded with NaN particles to a multiple of kJUMax
+      const int nj4 = (it.nj + kJUMax - 1) & ~(kJUMax - 1);
       for (int k = tid; k < nj4; k += BLOCK) {
         float4 v;
         if (k < it.nj) v = __ldg(F.X + it.j0 + k);
@@ -1119,8 +1126,8 @@ cudaError_t launch_rdf(const uint64_t* counts, int32_t n_hist, int32_t nbins, do
 
 size_t pair_kernel_smem(int hist_width, int depth, int block) {
   size_t stride = (size_t)((hist_width + 3) & ~3) + 2 * kGuard;
-  size_t warps = (size_t)(block == kBlockLarge ? kBlockLarge : kBlockSmall) / 32;
-  return (size_t)(depth > 1 ? depth : 1) * stride * 4 + (size_t)kTile * 12 + warps * kQueueCap * 8;
+  size_t warps = (size_t)(block == kBlockHuge ? kBlockHuge : block == kBlockLarge ? kBlockLarge : kBlockSmall) / 32;
+  return (size_t)(depth > 1 ? depth : 1) * stride * 4 + (size_t)kTile * 12 + warps * kQueueCap * 4;
 }
 
 int pair_kernel_max_width() {
@@ -1146,7 +1153,8 @@ int blocks_per_sm_vr(size_t smem) {
 template <int V>
 int blocks_per_sm_v(int hist_width, int depth, int block) {
   size_t smem = pair_kernel_smem(hist_width, depth, block);
-  return block == kBlockLarge ? blocks_per_sm_vr<V, 2>(smem) : blocks_per_sm_vr<V, 4>(smem);
+  return block == kBlockHuge ? blocks_per_sm_vr<V, 1>(smem)
+         : block == kBlockLarge ? blocks_per_sm_vr<V, 2>(smem) : blocks_per_sm_vr<V, 4>(smem);
 }
 
 int pair_kernel_blocks_per_sm(int variant, int hist_width, int depth, int block) {
@@ -1189,8 +1197,9 @@ cudaError_t launch_pairs_vmr(const PairLaunch& p, int grid, size_t smem, cudaStr
 
 template <int V, bool MULTI>
 cudaError_t launch_pairs_vm(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
-  return p.block == kBlockLarge ? launch_pairs_vmr<V, MULTI, 2>(p, grid, smem, stream)
-                                : launch_pairs_vmr<V, MULTI, 4>(p, grid, smem, stream);
+  return p.block == kBlockHuge    ? launch_pairs_vmr<V, MULTI, 1>(p, grid, smem, stream)
+         : p.block == kBlockLarge ? launch_pairs_vmr<V, MULTI, 2>(p, grid, smem, stream)
+                                  : launch_pairs_vmr<V, MULTI, 4>(p, grid, smem, stream);
 }
 
 template <int V>

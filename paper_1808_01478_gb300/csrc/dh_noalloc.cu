@@ -164,17 +164,20 @@ extern "C" dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream_pt
   if (chunks > 0) DH_CUDA_TRY(launch_stage(job, 1, chunks, st));
   DH_CUDA_TRY(launch_frame_setup(fd, 1, 0, st));
   if (n_items > 0) {
-    int bps = pair_kernel_blocks_per_sm(pf.variant, pf.sweep_width);
+    const int block = default_block(pf.variant, pf.sweep_width);
+    int bps = pair_kernel_blocks_per_sm(pf.variant, pf.sweep_width, 1, block);
     if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", pf.sweep_width);
     PairLaunch L;
     std::memset(&L, 0, sizeof L);
+    L.block = block;
     L.segs = segs;
     L.n_segs = n_segs;
     L.n_items = n_items;
     L.hist_width = pf.sweep_width;
     L.multi = pf.sweeps > 1;
     L.ctl = ctl;
-    DH_CUDA_TRY(launch_pairs(L, pf.variant, pair_grid(num_sms, bps, n_items), pair_kernel_smem(pf.sweep_width), st));
+    DH_CUDA_TRY(launch_pairs(L, pf.variant, pair_grid(num_sms, bps, n_items),
+                             pair_kernel_smem(pf.sweep_width, 1, block), st));
   }
   // Read back the flags into stack memory and wait.
   int32_t status = 0, bad = 0;

@@ -266,6 +266,13 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   }
 }
 
+int default_block(int variant, int width) {
+  if (width < 16384) return kBlockSmall;
+  for (int block = kBlockHuge; block > kBlockSmall; block /= 2)
+    if (pair_kernel_blocks_per_sm(variant, width, 1, block) >= 1) return block;
+  return kBlockSmall;
+}
+
 // Tiles of one frame's species pairs for every bin sweep, appended to segs
 // (fd: the frame's device descriptor); returns the item count.
 int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::vector<Segment>& segs, int jm) {
@@ -345,7 +352,8 @@ LaunchParams launch_params(dh_ctx* c, const VariantSummary& s, int v) {
   if (c->tune_forced) return c->tune_force;
   LaunchParams p;
   if (c->tuner.lookup(variant_key(s, v), &p)) return p;
-  return LaunchParams{};
+  p.block = default_block(v, s.width);
+  return p;
 }
 
 // Host-side plan of one call: buffers sized, threshold tables referenced,
@@ -798,7 +806,7 @@ dh_status tune_variant(dh_ctx* c, int v, const VariantSummary& vs) {
   };
   double g = 0.0;
   s = measure(LaunchParams{}, &g);  // warm-up (first launches of a shape)
-  for (int block : {kBlockSmall, kBlockLarge})
+  for (int block : {kBlockSmall, kBlockLarge, kBlockHuge})
     for (int jm = 1; jm <= 4 && s == DH_OK; jm *= 2)
       for (int depth = 1; depth <= 4 && s == DH_OK; depth *= 2) {
         int bmax = pair_kernel_blocks_per_sm(v, vs.width, depth, block);

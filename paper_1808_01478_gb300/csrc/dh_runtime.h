@@ -98,7 +98,7 @@ struct LaunchParams {
   int32_t jm = 1;                // j tiles per i tile: tile_j = kTile / jm
   int32_t depth = 1;             // private histogram copies per block
   int32_t bps = 0;               // blocks per SM (0: as many as fit)
-  int32_t block = kBlockSmall;   // threads per block (kBlockSmall or kBlockLarge)
+  int32_t block = kBlockSmall;   // threads per block (kBlockSmall, kBlockLarge or kBlockHuge)
 };
 
 // Autotuner key of a launch: variant, histogram width, frame size, frame count (all bucketed).
@@ -116,6 +116,12 @@ struct TuneEntry {
   double gpairs_s = 0.0;
 };
 TuneKey make_tune_key(int variant, int width, double mean_pairs_per_frame, int frames);
+
+// Threads per block for a launch without a measured shape: from 16,384 bins on,
+// a 256-thread block's histogram leaves room for at most two blocks per SM, and
+// one 1024-thread block sharing one histogram keeps more warps resident (512
+// threads when the larger block's queues do not fit next to the histogram).
+int default_block(int variant, int width);
 
 // Measured launch shapes per key (dh_tune.cpp), optionally kept in a text file.
 class Tuner {

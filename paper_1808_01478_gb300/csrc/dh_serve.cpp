@@ -525,10 +525,12 @@ bool Server::launch_wave(int v) {
   L.n_items = witems;
   L.hist_width = width;
   L.multi = multi;
+  L.block = default_block(v, width);
   L.ctl = (Control*)W.ctl.p;
-  int bps = pair_kernel_blocks_per_sm(v, width);
+  int bps = pair_kernel_blocks_per_sm(v, width, 1, L.block);
   cudaEventRecord(W.ev0, ln.stream);
-  cudaError_t e = launch_pairs(L, v, pair_grid(ctx_->num_sms, bps, witems), pair_kernel_smem(width), ln.stream);
+  cudaError_t e = launch_pairs(L, v, pair_grid(ctx_->num_sms, bps, witems), pair_kernel_smem(width, 1, L.block),
+                               ln.stream);
   cudaEventRecord(W.ev1, ln.stream);
   if (e != cudaSuccess) thread_error_ = cudaGetErrorString(e);
   W.busy = true;

@@ -1,7 +1,7 @@
 """Autotuned launch shapes (DH_CFG_AUTOTUNE, dh_config.tune_cache).
 
 Every launch shape the autotuner may pick (j-tile length 256/512/1024, blocks
-of 256 or 512 threads, one to four private histogram copies per block, blocks
+of 256, 512 or 1024 threads, one to four private histogram copies per block, blocks
 per SM) must give the FP64 oracle's histogram bin for bin; the shapes are forced through the tuner's own
 cache file.  The autotuner must measure each new launch key once, record it in
 the file, and a context that reads the file must use it without measuring.
@@ -75,7 +75,8 @@ FRAMES = {
     "tric_search": w.uniform_frame(34, 1500, w.BOX_TRICLINIC, TRIC, 14.0, 2000),
 }
 SHAPES = [(256, 1, 3, 256), (512, 2, 2, 256), (256, 4, 1, 256), (1024, 2, 3, 256), (512, 4, 2, 256),
-          (1024, 1, 1, 256), (1024, 1, 1, 512), (256, 2, 1, 512), (512, 4, 1, 512)]
+          (1024, 1, 1, 256), (1024, 1, 1, 512), (256, 2, 1, 512), (512, 4, 1, 512), (1024, 1, 1, 1024),
+          (256, 2, 1, 1024)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"tj{s[0]}_d{s[1]}_b{s[2]}_t{s[3]}")
@@ -107,7 +108,7 @@ def test_forced_shape_multi_sweep(torch_mod, oracle_mod, tmp_path):
         x = torch_mod.from_numpy(f.coords).cuda()
         got = ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins).cpu().numpy().view(np.uint64)
         st = ctx.stats()
-        assert st["sweeps"] >= 2 and st["tile_j"] == 512 and st["block_threads"] in (256, 512)
+        assert st["sweeps"] >= 2 and st["tile_j"] == 512 and st["block_threads"] in (256, 512, 1024)
         assert np.array_equal(got, oracle_mod.histogram_frame(f))
 
 
@@ -123,7 +124,7 @@ def test_autotune_measures_once_and_reuses_the_file(torch_mod, oracle_mod, tmp_p
         assert st["tune_runs"] > 1
         shape = (st["tile_j"], st["hist_depth"], st["blocks_per_sm"], st["block_threads"])
         assert shape[0] in (256, 512, 1024) and shape[1] in (1, 2, 4) and shape[2] >= 1
-        assert shape[3] in (256, 512)
+        assert shape[3] in (256, 512, 1024)
         for fa, f in zip(fas, frames):
             assert np.array_equal(result(fa), oracle_mod.histogram_frame(f)), f.name
         ctx.histogram_batch(fas)  # same key: no new measurement
