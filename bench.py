@@ -515,7 +515,7 @@ def run_gpu(args, world, rank, local):
     pairs = [f.n_pairs() for f in frames]
     pairs_step = sum(pairs)
 
-    ctx = dh.Context(local, flags=dh.DH_CFG_TIMING | dh.DH_CFG_AUTOTUNE)
+    ctx = dh.Context(local, flags=dh.DH_CFG_TIMING | (0 if args.no_autotune else dh.DH_CFG_AUTOTUNE))
     stream = torch.cuda.Stream(device=dev)
     ctx.set_stream(stream)
     X = [torch.from_numpy(f.coords).to(dev) for f in frames]
@@ -594,6 +594,7 @@ def run_gpu(args, world, rank, local):
             "gpairs_s": round(pairs[k] / (statistics.mean(ts) / 1e3) / 1e9, 3),
             "ms": round(statistics.mean(ts), 3),
             "deferred_frac": round(st["deferred"] / max(1, st["pairs"]), 6),
+            "tile_image_frac": round(st["uniform_pairs"] / max(1, st["pairs"]), 4),
         }
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -666,6 +667,7 @@ def main(argv=None) -> int:
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of measured ones")
     ap.add_argument("--c4-frames", type=int, default=256)
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-loads", type=float, nargs="*", default=[0.5, 0.8])

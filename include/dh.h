@@ -124,6 +124,7 @@ typedef struct {
   int32_t hist_depth;      /*   private histogram copies per block, */
   int32_t blocks_per_sm;   /*   blocks per SM */
   int32_t block_threads;   /*   and threads per block */
+  uint64_t uniform_pairs;  /* pairs evaluated with one nearest image for their whole tile (no per-pair rounding) */
 } dh_stats;
 
 /* Create a context on config->device (NULL: device 0, defaults).  Owns a CUDA

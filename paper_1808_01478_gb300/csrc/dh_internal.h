@@ -58,6 +58,7 @@ struct FrameDev {
   float eps_s;       // search variant: fractional-coordinate ambiguity margin
   unsigned long long deferred;  // statistics: pairs queued for the double-float tier
   unsigned long long exact;     // pairs that also needed the binary64 replay
+  unsigned long long uniform_pairs;  // pairs of (warp i run, j tile) blocks with one nearest image for all
 };
 
 // One species pair (a,b) of one frame and one bin sweep, cut into kTile x kTile
@@ -88,6 +89,19 @@ struct StageJob {
 };
 constexpr int kStageChunk = 8192;
 
+// Spatial ordering of one species of one periodic frame: its particles are
+// grouped by cell of a 2^g x 2^g x 2^g grid over the fractional coordinates, in
+// Morton order, so that tiles of consecutive particles are compact in space.
+// The histogram does not depend on the order of particles within a species.
+struct SortSeg {
+  const FrameDev* fd;
+  int64_t x0;        // first particle (index into the packed coordinates)
+  int32_t n;         // particles
+  int32_t g;         // grid bits per axis
+  int64_t key0;      // first counter of this segment (2^(3g) counters)
+};
+constexpr int kSortChunk = 4096;
+
 struct Control {
   unsigned long long next_item;  // dynamic work counter (reset before each launch)
   int32_t status;                // 0 ok, else an error code
@@ -109,6 +123,9 @@ struct PairLaunch {
 // ---- launchers (dh_kernels.cu); all enqueue on `stream` and return the launch error
 cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cudaStream_t stream);
 cudaError_t launch_frame_setup(FrameDev* frames, int n_frames, int pass_hi_max, cudaStream_t stream);
+// counts: zeroed, sum of 2^(3g) over the segments; keys and Xs: one per particle
+cudaError_t launch_spatial_sort(const SortSeg* segs, int n_segs, int max_chunks, float4* X, float4* Xs,
+                                int32_t* keys, uint32_t* counts, cudaStream_t stream);
 cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* status,
                               cudaStream_t stream);
 // One pair-kernel launch over segments whose frames all have minimum-image variant `variant`.

@@ -178,6 +178,106 @@ __global__ void stage_kernel(const StageJob* __restrict__ jobs, int n_jobs) {
   }
 }
 
+// ------------------------------------------------------------------ spatial order (staging)
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // bit k of v -> bit 3k
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// Morton cell of a particle from its fractional coordinates in the box
+// (approximate float32; only the order depends on it).
+__device__ __forceinline__ uint32_t cell_key(const FrameDev& F, float4 p, int g) {
+  float s[3];
+  if (F.variant == V_ORTHO) {
+    s[0] = p.x * F.invf[0];
+    s[1] = p.y * F.invf[1];
+    s[2] = p.z * F.invf[2];
+  } else {
+    s[2] = p.z * F.invf[2];
+    s[1] = (p.y - F.Bf[5] * s[2]) * F.invf[1];
+    s[0] = (p.x - F.Bf[1] * s[1] - F.Bf[2] * s[2]) * F.invf[0];
+  }
+  const float G = (float)(1 << g);
+  uint32_t c[3];
+  for (int a = 0; a < 3; ++a) {
+    float f = s[a] - floorf(s[a]);
+    int ci = (int)(f * G);
+    c[a] = (uint32_t)min(max(ci, 0), (1 << g) - 1);
+  }
+  return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+}
+
+__global__ void sort_count_kernel(const SortSeg* segs, const float4* __restrict__ X, int32_t* keys,
+                                  uint32_t* counts) {
+  const SortSeg S = segs[blockIdx.y];
+  const int64_t i0 = (int64_t)blockIdx.x * kSortChunk;
+  const int64_t i1 = min((int64_t)S.n, i0 + kSortChunk);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    uint32_t k = cell_key(*S.fd, X[S.x0 + i], S.g);
+    keys[S.x0 + i] = (int32_t)k;
+    atomicAdd(counts + S.key0 + k, 1u);
+  }
+}
+
+// Exclusive prefix sum of each segment's counters, in place (one block per segment).
+__global__ void sort_scan_kernel(const SortSeg* segs, uint32_t* counts) {
+  const SortSeg S = segs[blockIdx.x];
+  const int64_t m = (int64_t)1 << (3 * S.g);
+  uint32_t* c = counts + S.key0;
+  const int64_t per = (m + blockDim.x - 1) / blockDim.x;
+  const int64_t b = min(m, (int64_t)threadIdx.x * per), e = min(m, b + per);
+  uint32_t local = 0;
+  for (int64_t k = b; k < e; ++k) local += c[k];
+  __shared__ uint32_t warp_sum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_sum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x / 32;
+    uint32_t v = lane < nw ? warp_sum[lane] : 0u, inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane < nw) warp_sum[lane] = inc - v;  // exclusive over warps
+  }
+  __syncthreads();
+  uint32_t run = warp_sum[warp] + incl - local;  // exclusive start of this thread's chunk
+  for (int64_t k = b; k < e; ++k) {
+    uint32_t v = c[k];
+    c[k] = run;
+    run += v;
+  }
+}
+
+__global__ void sort_scatter_kernel(const SortSeg* segs, const float4* __restrict__ X,
+                                    const int32_t* __restrict__ keys, uint32_t* cursors, float4* Xs) {
+  const SortSeg S = segs[blockIdx.y];
+  const int64_t i0 = (int64_t)blockIdx.x * kSortChunk;
+  const int64_t i1 = min((int64_t)S.n, i0 + kSortChunk);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    uint32_t pos = atomicAdd(cursors + S.key0 + (uint32_t)keys[S.x0 + i], 1u);
+    Xs[S.x0 + pos] = X[S.x0 + i];
+  }
+}
+
+__global__ void sort_copy_kernel(const SortSeg* segs, const float4* __restrict__ Xs, float4* X) {
+  const SortSeg S = segs[blockIdx.y];
+  const int64_t i0 = (int64_t)blockIdx.x * kSortChunk;
+  const int64_t i1 = min((int64_t)S.n, i0 + kSortChunk);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) X[S.x0 + i] = Xs[S.x0 + i];
+}
+
 // ------------------------------------------------------------------ per-frame error window
 
 // Largest rounding error (half an ulp) of a float32 result whose exact value
@@ -426,27 +526,31 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // float32 |d'|^2 of two pairs after the minimum image of the variant; each
-// component is rounded exactly as the scalar sequence of wrap_r2.
-template <int V>
+// component is rounded exactly as the scalar sequence of wrap_r2.  UNI: the
+// tile pair's nearest-image integers are known to be kt for every pair (see
+// tile_image), so only the subtractions of the image are left, with the same
+// operands in the same order: the result is bit for bit the one of the
+// per-pair path.
+template <int V, bool UNI = false>
 __device__ __forceinline__ float2 wrap_r2_2(float2 dx, float2 dy, float2 dz, const FastParams& P, bool& amb_a,
-                                            bool& amb_b) {
+                                            bool& amb_b, float3 kt = make_float3(0.f, 0.f, 0.f)) {
   const float2 M = bc2(kMagicRound), NM = bc2(-kMagicRound);
   if (V == V_ORTHO) {
-    float2 kx = add2(fma2(dx, bc2(P.inv[0]), M), NM);
-    float2 ky = add2(fma2(dy, bc2(P.inv[1]), M), NM);
-    float2 kz = add2(fma2(dz, bc2(P.inv[2]), M), NM);
+    float2 kx = UNI ? bc2(kt.x) : add2(fma2(dx, bc2(P.inv[0]), M), NM);
+    float2 ky = UNI ? bc2(kt.y) : add2(fma2(dy, bc2(P.inv[1]), M), NM);
+    float2 kz = UNI ? bc2(kt.z) : add2(fma2(dz, bc2(P.inv[2]), M), NM);
     dx = fma2(kx, bc2(-P.b[0]), dx);
     dy = fma2(ky, bc2(-P.b[4]), dy);
     dz = fma2(kz, bc2(-P.b[8]), dz);
   } else if (V == V_TRIC) {
-    float2 kz = add2(fma2(dz, bc2(P.inv[2]), M), NM);
+    float2 kz = UNI ? bc2(kt.z) : add2(fma2(dz, bc2(P.inv[2]), M), NM);
     dx = fma2(kz, bc2(-P.b[2]), dx);
     dy = fma2(kz, bc2(-P.b[5]), dy);
     dz = fma2(kz, bc2(-P.b[8]), dz);
-    float2 ky = add2(fma2(dy, bc2(P.inv[1]), M), NM);
+    float2 ky = UNI ? bc2(kt.y) : add2(fma2(dy, bc2(P.inv[1]), M), NM);
     dx = fma2(ky, bc2(-P.b[1]), dx);
     dy = fma2(ky, bc2(-P.b[4]), dy);
-    float2 kx = add2(fma2(dx, bc2(P.inv[0]), M), NM);
+    float2 kx = UNI ? bc2(kt.x) : add2(fma2(dx, bc2(P.inv[0]), M), NM);
     dx = fma2(kx, bc2(-P.b[0]), dx);
   } else if (V == V_TRIC_SEARCH) {
     return make_float2(wrap_r2<V>(dx.x, dy.x, dz.x, P, amb_a), wrap_r2<V>(dx.y, dy.y, dz.y, P, amb_b));
@@ -495,11 +599,12 @@ __device__ __forceinline__ void count_or_defer(float sm, float e, float bound, u
 // decide_arith2 returns sm = s_c + 1.5*2^23, e and the bound as float pairs
 // (search variant: ambiguous images force the bound to +inf so the pair is
 // deferred); count_or_defer acts on them.
-template <int V, bool MULTI>
+template <int V, bool MULTI, bool UNI = false>
 __device__ __forceinline__ void decide_arith2(float2 dx, float2 dy, float2 dz, const FastParams& P, float chi,
-                                              float clo, float2& sm, float2& e, float2& bound) {
+                                              float clo, float2& sm, float2& e, float2& bound,
+                                              float3 kt = make_float3(0.f, 0.f, 0.f)) {
   bool amb_a = false, amb_b = false;
-  float2 r2 = wrap_r2_2<V>(dx, dy, dz, P, amb_a, amb_b);
+  float2 r2 = wrap_r2_2<V, UNI>(dx, dy, dz, P, amb_a, amb_b, kt);
   float2 nq = mul2(r2, bc2(-P.S2));  // -q
   float2 sq = make_float2(sqrt_approx(-nq.x), sqrt_approx(-nq.y));
   float2 sc = make_float2(fminf(sq.x, chi), fminf(sq.y, chi));  // NaN -> chi
@@ -723,19 +828,20 @@ __device__ __noinline__ int drain_queue(const FrameDev* F, int pass, int i0, int
 
 // j tile in shared memory as pairs of particles: A[p] = {x_2p, x_2p+1, y_2p, y_2p+1},
 // Z[p] = {z_2p, z_2p+1}, so one LDS.128 + one LDS.64 feed two j particles.
-template <int V, bool MASKED, bool MULTI, int RI>
+template <int V, bool MASKED, bool MULTI, int RI, bool UNI>
 __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
                                          const float4* __restrict__ sjA, const float2* __restrict__ sjZ,
-                                         uint32_t* sh, uint32_t* q, int tid, int lane, unsigned& ndeferred) {
-  constexpr int BLOCK = kTile / RI;
+                                         uint32_t* sh, uint32_t* q, int tid, int lane, unsigned& ndeferred,
+                                         float3 kt) {
+  // each warp holds 32 * RI consecutive i particles: lane + 32 r of its run
+  const int ib = (tid >> 5) * (32 * RI) + lane;
   float2 xi[RI], yi[RI], zi[RI];  // i coordinates broadcast to both halves
-  const int ibase = it.i0 + tid;
 #pragma unroll
   for (int r = 0; r < RI; ++r) {
-    int li = tid + r * BLOCK;
+    int li = ib + 32 * r;
     float x = __int_as_float(0x7fffffff), y = x, z = x;
     if (li < it.ni) {
-      float4 p = __ldg(F->X + ibase + r * BLOCK);
+      float4 p = __ldg(F->X + it.i0 + li);
       x = p.x; y = p.y; z = p.z;
     }
     xi[r] = bc2(-x); yi[r] = bc2(-y); zi[r] = bc2(-z);  // negated: d = xj + (-xi)
@@ -764,12 +870,12 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
         float2 dz = add2(Z, zi[r]);
         if (MASKED) {
           // intra-species: only j > i; all three components so no later test sees a number
-          const int ig = ibase + r * BLOCK, jg = it.j0 + jj0 + u;
+          const int ig = it.i0 + ib + 32 * r, jg = it.j0 + jj0 + u;
           if (!(jg > ig)) { dx.x = qnan; dy.x = qnan; dz.x = qnan; }
           if (!(jg + 1 > ig)) { dx.y = qnan; dy.y = qnan; dz.y = qnan; }
         }
         float2 sm, e, bound;
-        decide_arith2<V, MULTI>(dx, dy, dz, P, chi, clo, sm, e, bound);
+        decide_arith2<V, MULTI, UNI>(dx, dy, dz, P, chi, clo, sm, e, bound, kt);
         count_or_defer(sm.x, e.x, bound.x, hbase, 1u << (u * RI + r), dmask);
         count_or_defer(sm.y, e.y, bound.y, hbase, 1u << ((u + 1) * RI + r), dmask);
       }
@@ -781,7 +887,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
         int b = __ffs(dmask) - 1;
         dmask &= dmask - 1u;
         int pos = qcount + __popc(bal & lt_mask);
-        q[pos] = (uint32_t)(tid + (b % RI) * BLOCK) | ((uint32_t)(jj0 + b / RI) << 16);
+        q[pos] = (uint32_t)(ib + 32 * (b % RI)) | ((uint32_t)(jj0 + b / RI) << 16);
       }
       int added = __popc(bal);
       qcount += added;
@@ -804,11 +910,59 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
 // clamped from below (valid for every sweep, a separate kernel for registers).
 template <int V, bool MULTI, int RI>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
-                         uint32_t* q, int tid, int lane, unsigned& ndeferred) {
+                         uint32_t* q, int tid, int lane, unsigned& ndeferred, float4 img) {
   FastParams P;
   load_fast_params(*F, it.pass, P);
-  if (it.masked) run_tile<V, true, MULTI, RI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
-  else run_tile<V, false, MULTI, RI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred);
+  const float3 kt = make_float3(img.x, img.y, img.z);
+  if (V == V_ORTHO || V == V_TRIC) {
+    if (img.w != 0.0f) {
+      if (it.masked) run_tile<V, true, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
+      else run_tile<V, false, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
+      return;
+    }
+  }
+  if (it.masked) run_tile<V, true, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
+  else run_tile<V, false, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
+}
+
+// The nearest-image integers of a tile pair, when the float32 per-pair path
+// would compute the same ones for every pair of it.  lo/hi bound the i and j
+// coordinates per axis.  The per-pair path rounds d = xj - xi, then k =
+// nint(d / L) (triclinic: along c, b, a, each after the previous images are
+// subtracted); every step is a correctly rounded monotone function of d, so
+// the tile's extreme differences fl(jmin - imax) and fl(jmax - imin) bound the
+// value of every pair at every step, and equal integers at both ends are the
+// integers of every pair.  Returns (kx, ky, kz, 1) in that case, w = 0 else.
+template <int V>
+__device__ float4 tile_image(const FrameDev& F, const float* imin, const float* imax, const float* jmin,
+                             const float* jmax) {
+  float lo[3], hi[3];
+  for (int c = 0; c < 3; ++c) {
+    lo[c] = __fsub_rn(jmin[c], imax[c]);
+    hi[c] = __fsub_rn(jmax[c], imin[c]);
+  }
+  const float* b = F.Bf;
+  if (V == V_ORTHO) {
+    float k[3];
+    for (int c = 0; c < 3; ++c) {
+      k[c] = nint_scaled(lo[c], F.invf[c]);
+      if (!(nint_scaled(hi[c], F.invf[c]) == k[c])) return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return make_float4(k[0], k[1], k[2], 1.0f);
+  } else {
+    // z, then y and x after the c image, then x after the b image
+    const float kz = nint_scaled(lo[2], F.invf[2]);
+    if (!(nint_scaled(hi[2], F.invf[2]) == kz)) return make_float4(0.f, 0.f, 0.f, 0.f);
+    float ylo = __fmaf_rn(kz, -b[5], lo[1]), yhi = __fmaf_rn(kz, -b[5], hi[1]);
+    float xlo = __fmaf_rn(kz, -b[2], lo[0]), xhi = __fmaf_rn(kz, -b[2], hi[0]);
+    const float ky = nint_scaled(ylo, F.invf[1]);
+    if (!(nint_scaled(yhi, F.invf[1]) == ky)) return make_float4(0.f, 0.f, 0.f, 0.f);
+    xlo = __fmaf_rn(ky, -b[1], xlo);
+    xhi = __fmaf_rn(ky, -b[1], xhi);
+    const float kx = nint_scaled(xlo, F.invf[0]);
+    if (!(nint_scaled(xhi, F.invf[0]) == kx)) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return make_float4(kx, ky, kz, 1.0f);
+  }
 }
 
 // Adds the `depth` private copies (stride words apart) bin by bin into the
@@ -912,6 +1066,8 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
   float2* sjZ = reinterpret_cast<float2*>(sjA + kTile / 2);
   uint32_t* sq = reinterpret_cast<uint32_t*>(sjZ + kTile / 2);
   __shared__ ItemDesc s_it;
+  constexpr bool kTileImage = (V == V_ORTHO || V == V_TRIC);
+  __shared__ float s_bnd[kTileImage ? BLOCK / 32 : 1][6];  // per warp: j min xyz, j max xyz
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* q = sq + warp * kQueueCap;
@@ -962,20 +1118,59 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
         since = 0;
       }
       since += pairs;
-      // stage the j tile in pair layout, padded with NaN particles to a multiple of kJUMax
+      // stage the j tile in pair layout, padded with NaN particles to a multiple of kJUMax;
+      // for the tile image, the coordinate bounds of the j and i tiles
+      float bnd[12];  // i min xyz, i max xyz, j min xyz, j max xyz
+      for (int c = 0; c < 12; ++c) bnd[c] = ((c / 3) & 1) ? -INFINITY : INFINITY;
       const int nj4 = (it.nj + kJUMax - 1) & ~(kJUMax - 1);
       for (int k = tid; k < nj4; k += BLOCK) {
         float4 v;
-        if (k < it.nj) v = __ldg(F.X + it.j0 + k);
-        else v = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff), __int_as_float(0x7fffffff), 0.f);
+        if (k < it.nj) {
+          v = __ldg(F.X + it.j0 + k);
+          if (kTileImage) {
+            bnd[6] = fminf(bnd[6], v.x); bnd[7] = fminf(bnd[7], v.y); bnd[8] = fminf(bnd[8], v.z);
+            bnd[9] = fmaxf(bnd[9], v.x); bnd[10] = fmaxf(bnd[10], v.y); bnd[11] = fmaxf(bnd[11], v.z);
+          }
+        } else {
+          v = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff), __int_as_float(0x7fffffff), 0.f);
+        }
         float* a = reinterpret_cast<float*>(sjA + (k >> 1));
         a[k & 1] = v.x;
         a[2 + (k & 1)] = v.y;
         reinterpret_cast<float*>(sjZ + (k >> 1))[k & 1] = v.z;
       }
+      float4 img = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (kTileImage) {
+        // this warp's i run (the particles run_tile gives it) and the block's j tile
+        const int ib = warp * (32 * RI) + lane;
+        for (int r = 0; r < RI; ++r) {
+          const int li = ib + 32 * r;
+          if (li < it.ni) {
+            float4 v = __ldg(F.X + it.i0 + li);
+            bnd[0] = fminf(bnd[0], v.x); bnd[1] = fminf(bnd[1], v.y); bnd[2] = fminf(bnd[2], v.z);
+            bnd[3] = fmaxf(bnd[3], v.x); bnd[4] = fmaxf(bnd[4], v.y); bnd[5] = fmaxf(bnd[5], v.z);
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1)
+          for (int c = 0; c < 12; ++c) {
+            float other = __shfl_xor_sync(kFull, bnd[c], o);
+            bnd[c] = ((c / 3) & 1) ? fmaxf(bnd[c], other) : fminf(bnd[c], other);
+          }
+        if (lane == 0)
+          for (int c = 6; c < 12; ++c) s_bnd[warp][c - 6] = bnd[c];
+      }
       __syncthreads();
+      if (kTileImage) {
+        for (int w = 0; w < BLOCK / 32; ++w)
+          for (int c = 6; c < 12; ++c)
+            bnd[c] = ((c / 3) & 1) ? fmaxf(bnd[c], s_bnd[w][c - 6]) : fminf(bnd[c], s_bnd[w][c - 6]);
+        const int ni_w = min(32 * RI, it.ni - warp * 32 * RI);  // i particles of this warp
+        if (ni_w > 0) img = tile_image<V>(F, bnd, bnd + 3, bnd + 6, bnd + 9);
+        if (lane == 0 && img.w != 0.0f)
+          atomicAdd(&it.fd->uniform_pairs, (unsigned long long)ni_w * (unsigned long long)it.nj);
+      }
       unsigned ndef = 0;
-      run_item<V, MULTI, RI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef);
+      run_item<V, MULTI, RI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, img);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();
@@ -1169,6 +1364,17 @@ int pair_kernel_blocks_per_sm(int variant, int hist_width, int depth, int block)
 cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cudaStream_t stream) {
   if (n_jobs <= 0 || n_chunks <= 0) return cudaSuccess;
   stage_kernel<<<(unsigned)n_chunks, 256, 0, stream>>>(jobs, n_jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spatial_sort(const SortSeg* segs, int n_segs, int max_chunks, float4* X, float4* Xs,
+                                int32_t* keys, uint32_t* counts, cudaStream_t stream) {
+  if (n_segs <= 0 || max_chunks <= 0) return cudaSuccess;
+  dim3 grid((unsigned)max_chunks, (unsigned)n_segs);
+  sort_count_kernel<<<grid, 256, 0, stream>>>(segs, X, keys, counts);
+  sort_scan_kernel<<<n_segs, 1024, 0, stream>>>(segs, counts);
+  sort_scatter_kernel<<<grid, 256, 0, stream>>>(segs, X, keys, counts, Xs);
+  sort_copy_kernel<<<grid, 256, 0, stream>>>(segs, Xs, X);
   return cudaGetLastError();
 }
 

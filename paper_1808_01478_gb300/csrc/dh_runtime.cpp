@@ -375,7 +375,22 @@ struct CallPlan {
   std::vector<size_t> raw_off;  // per frame, offset in c->raw (host coordinates)
   int max_pass = 1;
   int launched = 0;
+  size_t seg_bytes = 0;          // Segment array in the metadata
+  int n_sort = 0;                // spatial-order segments (after the Segments in the metadata)
+  int sort_chunks = 0;           // most staging chunks of one of them
+  int64_t sort_keys = 0;         // counters over all of them
+  int64_t sort_particles = 0;    // particles of the frames (index space of keys and the scratch copy)
 };
+
+// Species of orthorhombic and triclinic frames are put in spatial (Morton) order
+// before the pair kernel, from this many particles on.
+constexpr int32_t kSortMinParticles = 2048;
+
+// Grid bits per axis for a species of n particles: about 16 particles per cell.
+int sort_grid_bits(int64_t n) {
+  int g = (int)std::floor(std::log2(std::cbrt((double)n / 16.0)));
+  return std::min(6, std::max(1, g));
+}
 
 dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const std::vector<uint64_t*>& dev_out,
                          bool host_coords, bool with_pairs, CallPlan& P) {
@@ -416,14 +431,51 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
     }
     P.vseg0[kNumVariants] = segs.size();
   };
+  // spatial order of the species of periodic frames without the 27-image search
+  std::vector<SortSeg> sorts;
+  auto plan_sorts = [&](FrameDev* dF) {
+    sorts.clear();
+    P.sort_keys = 0;
+    P.sort_chunks = 0;
+    for (int f = 0; f < k; ++f) {
+      if (pfs[f].variant != V_ORTHO && pfs[f].variant != V_TRIC) continue;
+      const int64_t* o = pfs[f].src->species_offsets;
+      for (int a = 0; a < pfs[f].src->n_species; ++a) {
+        const int64_t na = o[a + 1] - o[a];
+        if (na < kSortMinParticles) continue;
+        SortSeg g;
+        std::memset(&g, 0, sizeof g);
+        g.fd = dF + f;
+        g.x0 = xoff[f] + o[a];
+        g.n = (int32_t)na;
+        g.g = sort_grid_bits(na);
+        g.key0 = P.sort_keys;
+        P.sort_keys += (int64_t)1 << (3 * g.g);
+        P.sort_chunks = std::max<int>(P.sort_chunks, (int)((na + kSortChunk - 1) / kSortChunk));
+        sorts.push_back(g);
+      }
+    }
+    P.n_sort = (int)sorts.size();
+    P.sort_particles = xoff[k];
+  };
   DH_CUDA_TRY(c->meta.ensure(sizeof(FrameDev) * (size_t)k + sizeof(StageJob) * (size_t)k));
   plan_segments((FrameDev*)c->meta.p);
-  P.meta_bytes = sizeof(FrameDev) * (size_t)k + sizeof(StageJob) * (size_t)k +
-                 sizeof(Segment) * std::max<size_t>(segs.size(), 1);
+  plan_sorts((FrameDev*)c->meta.p);
+  P.seg_bytes = sizeof(Segment) * std::max<size_t>(segs.size(), 1);
+  P.meta_bytes = sizeof(FrameDev) * (size_t)k + sizeof(StageJob) * (size_t)k + P.seg_bytes +
+                 sizeof(SortSeg) * sorts.size();
   void* before = c->meta.p;
   DH_CUDA_TRY(c->meta.ensure(P.meta_bytes));
   DH_CUDA_TRY(c->hmeta.ensure(P.meta_bytes));
-  if (c->meta.p != before) plan_segments((FrameDev*)c->meta.p);  // buffer moved
+  if (c->meta.p != before) {  // buffer moved
+    plan_segments((FrameDev*)c->meta.p);
+    plan_sorts((FrameDev*)c->meta.p);
+  }
+  if (P.n_sort > 0) {
+    DH_CUDA_TRY(c->sortX.ensure(sizeof(float4) * (size_t)P.sort_particles));
+    DH_CUDA_TRY(c->sortK.ensure(sizeof(int32_t) * (size_t)P.sort_particles));
+    DH_CUDA_TRY(c->sortC.ensure(sizeof(uint32_t) * (size_t)P.sort_keys));
+  }
   FrameDev* dF = (FrameDev*)c->meta.p;
   FrameDev* hF = (FrameDev*)c->hmeta.p;
   StageJob* hJ = (StageJob*)(hF + k);
@@ -453,6 +505,8 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
     P.n_chunks += (fr->n + kStageChunk - 1) / kStageChunk;
   }
   if (!segs.empty()) std::memcpy(hS, segs.data(), sizeof(Segment) * segs.size());
+  if (!sorts.empty())
+    std::memcpy((unsigned char*)hS + P.seg_bytes, sorts.data(), sizeof(SortSeg) * sorts.size());
   // launch shapes (occupancy queries and kernel attributes stay outside any stream capture)
   for (int v = 0; v < kNumVariants; ++v) {
     P.vgrid[v] = 0;
@@ -499,6 +553,13 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
     DH_CUDA_TRY(launch_stage(dJ, P.n_jobs, P.n_chunks, st));
     ++launched;
   }
+  if (P.n_sort > 0) {
+    const SortSeg* dSort = (const SortSeg*)((unsigned char*)dS + P.seg_bytes);
+    DH_CUDA_TRY(cudaMemsetAsync(c->sortC.p, 0, sizeof(uint32_t) * (size_t)P.sort_keys, st));
+    DH_CUDA_TRY(launch_spatial_sort(dSort, P.n_sort, P.sort_chunks, (float4*)c->X.p, (float4*)c->sortX.p,
+                                    (int32_t*)c->sortK.p, (uint32_t*)c->sortC.p, st));
+    launched += 4;
+  }
   DH_CUDA_TRY(launch_frame_setup(dF, k, 0, st));
   ++launched;
   // A2-A8: per variant, one persistent launch over its frames, species pairs and bin sweeps
@@ -520,6 +581,10 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
       L.segs = dS + P.vseg0[v];
       L.n_segs = (int32_t)(P.vseg0[v + 1] - P.vseg0[v]);
       L.n_items = P.vitems[v];
+      if (c->tune_forced && c->tune_cap_pairs > 0.0) {  // a measurement: the first items only
+        const double per_item = (double)kTile * (double)(kTile / P.vparams[v].jm);
+        L.n_items = std::min<int64_t>(L.n_items, (int64_t)std::ceil(c->tune_cap_pairs / per_item));
+      }
       L.hist_width = P.vwidth[v];
       L.hist_depth = P.vparams[v].depth;
       L.multi = P.vmulti[v];
@@ -580,6 +645,7 @@ dh_status finish_frames(dh_ctx* c, int k) {
   for (int f = 0; f < k; ++f) {
     c->stats.deferred += hF[f].deferred;
     c->stats.exact_fallback += hF[f].exact;
+    c->stats.uniform_pairs += hF[f].uniform_pairs;
     if (hF[f].bad) return fail(DH_ERR_INVALID, "frame %d has non-finite coordinates", f);
   }
   return DH_OK;
@@ -712,18 +778,22 @@ uint64_t splitmix64(uint64_t& z) {
 }
 
 // Measures every launch shape on a synthetic batch shaped like the frames of
-// variant v in the call (same histogram width and sweeps, the mean frame size,
-// up to 64 frames, about 6e9 pairs): uniform particles at density 0.1 in a
+// variant v in the call (same histogram width and sweeps, the mean frame size
+// up to 2^21 particles, up to 64 frames): uniform particles at density 0.1 in a
 // cube (none: every pair in range; orthorhombic: r_max = L/2) or in the
 // 70/80/100-degree cell (r_max = 0.95 h_min/2, or 0.75 h_min for the 27-image
-// search).  The fastest shape is stored under the variant's launch key.
+// search).  Each measurement covers about 6e9 pairs: whole frames, or the
+// first work items of a larger one (the same tile geometry as the whole).  The
+// fastest shape is stored under the variant's launch key.
 dh_status tune_variant(dh_ctx* c, int v, const VariantSummary& vs) {
   const double mean_pairs = vs.pairs / std::max(vs.frames, 1);
   int64_t n = (int64_t)std::llround(std::sqrt(2.0 * std::max(mean_pairs, 1.0)));
-  n = std::min<int64_t>(std::max<int64_t>(n, 64), 110000);
+  n = std::min<int64_t>(std::max<int64_t>(n, 64), (int64_t)1 << 21);
   const double pairs_one = 0.5 * (double)n * (double)(n - 1);
-  const int nf = (int)std::min<int64_t>(std::max<int64_t>(std::llround(6e9 / pairs_one), 1),
+  const double target = 6e9;
+  const int nf = (int)std::min<int64_t>(std::max<int64_t>(std::llround(target / pairs_one), 1),
                                         std::min(vs.frames, 64));
+  c->tune_cap_pairs = (nf * pairs_one > 1.5 * target) ? target : 0.0;
   const int nbins = vs.multi ? 2 * vs.width : vs.width;
   const double vol = (double)n / 0.1;
   double box[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -801,11 +871,25 @@ dh_status tune_variant(dh_ctx* c, int v, const VariantSummary& vs) {
     if (r != DH_OK) return r;
     ++c->tune_runs;
     double ms = c->stats.pair_kernel_ms;
-    *gps = ms > 0.0 ? pairs_one * nf / (ms * 1e6) : 0.0;
+    double pairs = pairs_one * nf;
+    if (c->tune_cap_pairs > 0.0) {  // whole items of the capped launch
+      const double per_item = (double)kTile * (double)(kTile / p.jm);
+      pairs = std::min(pairs, std::ceil(c->tune_cap_pairs / per_item) * per_item);
+    }
+    *gps = ms > 0.0 ? pairs / (ms * 1e6) : 0.0;
     return DH_OK;
   };
+  // the shape used without a measurement is the reference; another shape must
+  // beat it by 1 % (single measurements differ by about that much)
+  LaunchParams def;
+  def.block = default_block(v, vs.width);
+  def.bps = pair_kernel_blocks_per_sm(v, vs.width, 1, def.block);
   double g = 0.0;
-  s = measure(LaunchParams{}, &g);  // warm-up (first launches of a shape)
+  s = measure(def, &g);  // warm-up (first launches of a shape)
+  if (s == DH_OK) s = measure(def, &g);
+  best.p = def;
+  best.gpairs_s = g;
+  const double g_def = g;
   for (int block : {kBlockSmall, kBlockLarge, kBlockHuge})
     for (int jm = 1; jm <= 4 && s == DH_OK; jm *= 2)
       for (int depth = 1; depth <= 4 && s == DH_OK; depth *= 2) {
@@ -817,13 +901,14 @@ dh_status tune_variant(dh_ctx* c, int v, const VariantSummary& vs) {
           p.bps = bps;
           p.block = block;
           s = measure(p, &g);
-          if (s == DH_OK && g > best.gpairs_s) {
+          if (s == DH_OK && g > best.gpairs_s && g > 1.01 * g_def) {
             best.p = p;
             best.gpairs_s = g;
           }
         }
       }
   c->tune_forced = false;
+  c->tune_cap_pairs = 0.0;
   if (own_events) {
     cudaEventDestroy(c->ev_pair0);
     cudaEventDestroy(c->ev_pair1);
@@ -989,6 +1074,9 @@ dh_status dh_destroy(dh_ctx* c) {
   c->ctl.release();
   c->tstat.release();
   c->aux.release();
+  c->sortX.release();
+  c->sortK.release();
+  c->sortC.release();
   c->hmeta.release();
   c->hout.release();
   if (c->gexec) cudaGraphExecDestroy(c->gexec);

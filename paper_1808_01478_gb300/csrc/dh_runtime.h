@@ -168,6 +168,9 @@ struct dh_ctx {
   dh::HostBuf hout;    // pinned staging for accumulate-on-host
   dh::DevBuf tstat;    // threshold build status
   dh::DevBuf aux;      // small per-call arrays (g(r) pair densities)
+  dh::DevBuf sortX;    // spatial order: scratch copy of the coordinates,
+  dh::DevBuf sortK;    //   cell keys,
+  dh::DevBuf sortC;    //   and cell counters
   dh::ThresholdCache tcache;
   std::vector<const double*> held_tables;  // tables referenced by work not yet finished
 
@@ -176,6 +179,7 @@ struct dh_ctx {
   bool tune_forced = false;        // measurement in progress: every launch uses tune_force
   dh::LaunchParams tune_force;
   int32_t tune_runs = 0;           // measurement launches made for the current call
+  double tune_cap_pairs = 0.0;     // measurement: stop each pair-kernel launch after about this many pairs
 
   dh_stats stats{};
   cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;  // pair-kernel timing (DH_CFG_TIMING)

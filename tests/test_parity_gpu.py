@@ -181,3 +181,53 @@ def test_repeat_calls_identical_and_threshold_cache(ctx, torch_mod, oracle_mod):
     want = oracle_mod.histogram_frame(f)
     for _ in range(3):
         assert_same(gpu_hist(ctx, torch_mod, f), want, "repeat")
+
+
+# Species of periodic frames are put in spatial order before the pair kernel,
+# and tile pairs whose float32 nearest images are provably the same for every
+# pair skip the per-pair rounding; both must leave every bin unchanged.
+SPATIAL = {
+    "ortho_sorted_species": w.frame_from(
+        w.uniform_frame(61, 30000, w.BOX_ORTHO, w.ortho_box(60.0, 50.0, 70.0), 25.0, 6000).coords,
+        [0, 1500, 21000, 30000], w.BOX_ORTHO, w.ortho_box(60.0, 50.0, 70.0), 25.0, 6000, "ortho_sorted"),
+    "tric_sorted": w.uniform_frame(62, 24000, w.BOX_TRICLINIC, w.triclinic_box(64, 64, 64, *w.C3_ANGLES),
+                                   28.0, 8000, n_species=2),
+    "ortho_unwrapped": w.frame_from(
+        (w.uniform_frame(63, 12000, w.BOX_ORTHO, w.ortho_box(40.0), 19.0, 3000).coords
+         + np.float32(40.0) * w.rng_for(64).integers(-2, 3, size=(12000, 3)).astype(np.float32)),
+        [0, 12000], w.BOX_ORTHO, w.ortho_box(40.0), 19.0, 3000, "ortho_unwrapped"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SPATIAL))
+def test_spatial_order_and_tile_images(ctx, torch_mod, oracle_mod, name):
+    f = SPATIAL[name]
+    got = gpu_hist(ctx, torch_mod, f)
+    assert_same(got, oracle_mod.histogram_frame(f), name)
+    st = ctx.stats()
+    if name == "ortho_sorted_species":
+        assert st["uniform_pairs"] > 0, st
+    assert st["uniform_pairs"] <= st["pairs"]
+
+
+@pytest.mark.parametrize("box_type", [w.BOX_ORTHO, w.BOX_TRICLINIC])
+def test_tile_images_at_larger_n_match_the_unsorted_path(ctx, torch_mod, box_type):
+    # N = 131,072 (too many pairs for the oracle here): the sorted path with tile
+    # images against dh_histogram_noalloc, which neither sorts nor uses tile
+    # images (and is itself compared with the oracle); both must agree bin for bin
+    n = dh.DH_NOALLOC_MAX_N
+    if box_type == w.BOX_ORTHO:
+        box = w.ortho_box((n / 0.1) ** (1.0 / 3.0))
+        r_max = box[0] / 2.0
+    else:
+        box = w.scale_box(w.triclinic_box(1.0, 1.0, 1.0, *w.C3_ANGLES), n / 0.1)
+        r_max = 0.95 * float(w.box_heights(box).min()) / 2.0
+    f = w.uniform_frame(65, n, box_type, box, r_max, 10_000)
+    x = torch_mod.from_numpy(f.coords).cuda()
+    got = ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins).cpu().numpy().view(np.uint64)
+    st = ctx.stats()
+    assert 0 < st["uniform_pairs"] <= st["pairs"], st
+    out = torch_mod.zeros((1, f.nbins), dtype=torch_mod.int64, device="cuda")
+    fa = dh.FrameArgs(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
+    dh.dh_histogram_noalloc(fa.frame)
+    assert_same(got, out.cpu().numpy().view(np.uint64), "noalloc")
