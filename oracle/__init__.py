@@ -60,12 +60,16 @@ class OracleLib:
         lib.dh_oracle_histogram.argtypes = [P, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int32,
                                             P, ctypes.c_double, ctypes.c_int32, P, ctypes.c_int32]
         lib.dh_oracle_histogram.restype = ctypes.c_int
+        lib.dh_oracle_histogram_f64.argtypes = lib.dh_oracle_histogram.argtypes
+        lib.dh_oracle_histogram_f64.restype = ctypes.c_int
         lib.dh_oracle_pair_r2.argtypes = [P, P, ctypes.c_int32, P]
         lib.dh_oracle_pair_r2.restype = ctypes.c_double
         lib.dh_oracle_bin.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32]
         lib.dh_oracle_bin.restype = ctypes.c_int64
         lib.dh_oracle_pairs_r2.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int32, P, P]
         lib.dh_oracle_pairs_r2.restype = None
+        lib.dh_oracle_pairs_r2_f64.argtypes = lib.dh_oracle_pairs_r2.argtypes
+        lib.dh_oracle_pairs_r2_f64.restype = None
         lib.dh_oracle_rdf.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P, ctypes.c_uint64, P]
         lib.dh_oracle_rdf.restype = None
         lib.dh_oracle_max_threads.argtypes = []
@@ -78,15 +82,17 @@ class OracleLib:
 
     def histogram(self, coords, offsets, box_type, box, r_max, nbins,
                   nthreads: int | None = None) -> np.ndarray:
-        """All S(S+1)/2 species-pair histograms, shape (S(S+1)/2, nbins), uint64."""
-        x = np.ascontiguousarray(coords, dtype=np.float32).reshape(-1, 3)
+        """All S(S+1)/2 species-pair histograms, shape (S(S+1)/2, nbins), uint64.
+        float64 coordinates use the binary64-input definition, anything else float32."""
+        f64 = np.asarray(coords).dtype == np.float64
+        x = np.ascontiguousarray(coords, dtype=np.float64 if f64 else np.float32).reshape(-1, 3)
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         bx = _box9(box)
         s = off.shape[0] - 1
         out = np.zeros((s * (s + 1) // 2, int(nbins)), dtype=np.uint64)
         nt = self.max_threads() if nthreads is None else int(nthreads)
-        rc = self.lib.dh_oracle_histogram(_ptr(x), x.shape[0], _ptr(off), s, int(box_type),
-                                          _ptr(bx), float(r_max), int(nbins), _ptr(out), nt)
+        fn = self.lib.dh_oracle_histogram_f64 if f64 else self.lib.dh_oracle_histogram
+        rc = fn(_ptr(x), x.shape[0], _ptr(off), s, int(box_type), _ptr(bx), float(r_max), int(nbins), _ptr(out), nt)
         if rc != 0:
             raise ValueError(f"oracle rejected the frame (code {rc})")
         return out
@@ -102,13 +108,14 @@ class OracleLib:
         return float(self.lib.dh_oracle_pair_r2(_ptr(a), _ptr(b), int(box_type), _ptr(bx)))
 
     def pairs_r2(self, coords, ii, jj, box_type, box) -> np.ndarray:
-        x = np.ascontiguousarray(coords, dtype=np.float32).reshape(-1, 3)
+        f64 = np.asarray(coords).dtype == np.float64
+        x = np.ascontiguousarray(coords, dtype=np.float64 if f64 else np.float32).reshape(-1, 3)
         i = np.ascontiguousarray(ii, dtype=np.int64)
         j = np.ascontiguousarray(jj, dtype=np.int64)
         bx = _box9(box)
         out = np.empty(i.shape[0], dtype=np.float64)
-        self.lib.dh_oracle_pairs_r2(_ptr(x), _ptr(i), _ptr(j), i.shape[0], int(box_type), _ptr(bx),
-                                    _ptr(out))
+        fn = self.lib.dh_oracle_pairs_r2_f64 if f64 else self.lib.dh_oracle_pairs_r2
+        fn(_ptr(x), _ptr(i), _ptr(j), i.shape[0], int(box_type), _ptr(bx), _ptr(out))
         return out
 
     def bin_of(self, r2: float, r_max: float, nbins: int) -> int:

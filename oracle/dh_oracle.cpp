@@ -17,7 +17,8 @@
 // design notes):
 //   * all arithmetic in IEEE binary64, round to nearest even, no contraction
 //     (built with -ffp-contract=off); explicit fma only where written;
-//   * coordinates are float32 and promoted exactly to binary64;
+//   * coordinates are float32, promoted exactly to binary64 (so d is exact),
+//     or binary64 (the distance vector is then rounded once per component);
 //   * nint of Eq. 5 is nearbyint (round half to even), as the CPU kernels of
 //     the paper use nearbyint (Sec. 4.1);
 //   * orthorhombic (Sec. 2.3, diagonal B): k = nearbyint(d * (1/L)),
@@ -78,7 +79,9 @@ inline double norm2(double dx, double dy, double dz) {
 }
 
 // Minimum-image squared distance of the pair (i, j): Alg. 1 steps 1-3 with Eq. 5.
-double pair_r2(const float* xi, const float* xj, const Box& box) {
+// T is the coordinate type (float or double).
+template <typename T>
+double pair_r2(const T* xi, const T* xj, const Box& box) {
   // distance vector between the two particles (Alg. 1)
   double dx = (double)xj[0] - (double)xi[0];
   double dy = (double)xj[1] - (double)xi[1];
@@ -135,7 +138,8 @@ inline int64_t hist_index(int64_t a, int64_t b, int64_t S) {
 
 // Histogram of one species pair into hist[0..nbins): Alg. 1 (inter) or its
 // single-species variant with j > i (intra).
-void histogram_pair(const float* x, int64_t a0, int64_t a1, int64_t b0, int64_t b1, bool intra,
+template <typename T>
+void histogram_pair(const T* x, int64_t a0, int64_t a1, int64_t b0, int64_t b1, bool intra,
                     const Box& box, double r_max, int32_t nbins, uint64_t* hist, int nthreads) {
   int64_t na = a1 - a0;
   if (na <= 0 || b1 - b0 <= 0) return;
@@ -159,14 +163,10 @@ void histogram_pair(const float* x, int64_t a0, int64_t a1, int64_t b0, int64_t 
     for (int32_t k = 0; k < nbins; ++k) hist[k] += priv[(size_t)t][(size_t)k];
 }
 
-}  // namespace
-
-extern "C" {
-
-// Return codes: 0 ok, -1 invalid argument.
-int dh_oracle_histogram(const float* coords, int64_t n, const int64_t* offsets, int32_t n_species,
-                        int32_t box_type, const double* box, double r_max, int32_t nbins,
-                        uint64_t* out, int32_t nthreads) {
+// All S(S+1)/2 species-pair histograms of one frame.  Return codes: 0 ok, -1 invalid argument.
+template <typename T>
+int histogram_all(const T* coords, int64_t n, const int64_t* offsets, int32_t n_species, int32_t box_type,
+                  const double* box, double r_max, int32_t nbins, uint64_t* out, int32_t nthreads) {
   if (n < 0 || n_species < 1 || nbins < 1 || !(r_max > 0.0)) return -1;
   if (box_type < BOX_NONE || box_type > BOX_TRICLINIC) return -1;
   if (offsets[0] != 0 || offsets[n_species] != n) return -1;
@@ -183,6 +183,24 @@ int dh_oracle_histogram(const float* coords, int64_t n, const int64_t* offsets, 
                      r_max, nbins, h, nthreads);
     }
   return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+// float32 coordinates (n x 3)
+int dh_oracle_histogram(const float* coords, int64_t n, const int64_t* offsets, int32_t n_species,
+                        int32_t box_type, const double* box, double r_max, int32_t nbins,
+                        uint64_t* out, int32_t nthreads) {
+  return histogram_all(coords, n, offsets, n_species, box_type, box, r_max, nbins, out, nthreads);
+}
+
+// binary64 coordinates (n x 3)
+int dh_oracle_histogram_f64(const double* coords, int64_t n, const int64_t* offsets, int32_t n_species,
+                            int32_t box_type, const double* box, double r_max, int32_t nbins,
+                            uint64_t* out, int32_t nthreads) {
+  return histogram_all(coords, n, offsets, n_species, box_type, box, r_max, nbins, out, nthreads);
 }
 
 double dh_oracle_pair_r2(const float* xi, const float* xj, int32_t box_type, const double* box) {
@@ -219,6 +237,14 @@ void dh_oracle_rdf(const uint64_t* counts, int32_t n_hist, int32_t nbins, double
       double per_frame = (double)counts[(size_t)h * nbins + k] / (double)n_frames;
       g[(size_t)h * nbins + k] = per_frame / (pair_density[h] * shell);
     }
+}
+
+// The same for binary64 coordinates.
+void dh_oracle_pairs_r2_f64(const double* coords, const int64_t* ii, const int64_t* jj, int64_t m,
+                            int32_t box_type, const double* box, double* out) {
+  double zero[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  Box b = make_box(box_type, box ? box : zero);
+  for (int64_t p = 0; p < m; ++p) out[p] = pair_r2(coords + 3 * ii[p], coords + 3 * jj[p], b);
 }
 
 int dh_oracle_max_threads(void) {

@@ -36,6 +36,8 @@ MUTANTS = {
     "rdf_ignores_frames": ("double per_frame = (double)counts[(size_t)h * nbins + k] / (double)n_frames;",
                            "double per_frame = (double)counts[(size_t)h * nbins + k];"),
     "rdf_upper_edge_only": ("double r0 = (double)k * dr;", "double r0 = 0.0;"),
+    "f64_coordinates_rounded_to_float": ("double dx = (double)xj[0] - (double)xi[0];",
+                                         "double dx = (double)(float)xj[0] - (double)(float)xi[0];"),
     "hist_order_swapped": ("return a * S - a * (a - 1) / 2 + (b - a);",
                            "return (S * (S + 1) / 2 - 1) - (a * S - a * (a - 1) / 2 + (b - a));"),
 }
@@ -55,6 +57,7 @@ PIN_TESTS = [
     (pins.test_exact_rational_recomputation, {"box_type": pins.ORTHO}),
     (pins.test_exact_rational_recomputation, {"box_type": pins.TRIC}),
     (pins.test_ideal_gas_closed_form, {"box_type": pins.ORTHO}),
+    (pins.test_f64_input_exact_rational_bins, {"box_type": pins.NONE}),
     (pins.test_rdf_hand_shells, {}),
     (pins.test_rdf_frames_and_density_scale, {}),
     (pins.test_rdf_ideal_gas_is_one, {}),

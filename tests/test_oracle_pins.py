@@ -432,3 +432,75 @@ def test_rdf_ideal_gas_is_one(oracle_mod):
         z = (g[hh] - 1.0) * np.sqrt(expect)  # Poisson: sd of g is 1/sqrt(expected count)
         assert np.all(np.abs(z) < 6.0), np.abs(z).max()
         assert abs((g[hh] * expect).sum() / expect.sum() - 1.0) < 0.01
+
+
+# ---------------------------------------------------------------- binary64 input coordinates
+
+
+@pytest.mark.parametrize("box_type", [NONE, ORTHO, TRIC])
+def test_f64_input_equals_f32_input_on_float_values(oracle_mod, box_type):
+    # binary64 coordinates that hold float32 values: the distance vector is exact in
+    # both definitions, so every bin agrees with the (pinned) float32-input oracle
+    box = {NONE: None, ORTHO: w.ortho_box(9.0, 7.5, 11.0), TRIC: w.triclinic_box(9.0, 9.0, 9.0, *w.C3_ANGLES)}
+    f = w.uniform_frame(70 + box_type, 700, box_type, box[box_type] if box_type != NONE else w.ortho_box(8.0),
+                        3.9, 777, n_species=3)
+    h32 = oracle_mod.histogram(f.coords, f.offsets, box_type, box[box_type], f.r_max, f.nbins, nthreads=4)
+    h64 = oracle_mod.histogram(f.coords.astype(np.float64), f.offsets, box_type, box[box_type], f.r_max, f.nbins,
+                               nthreads=4)
+    assert np.array_equal(h32, h64)
+
+
+@pytest.mark.parametrize("box_type", [NONE, ORTHO, TRIC])
+def test_f64_input_exact_rational_bins(oracle_mod, box_type):
+    # binary64 coordinates with all 53 bits used: the histogram equals the exact
+    # rational bins (pairs within 1e-9 of an edge, where rounding may decide either
+    # way, are avoided by construction)
+    rng = np.random.default_rng(80 + box_type)
+    if box_type == ORTHO:
+        box = w.ortho_box(7.3, 5.9, 9.1)
+        x = (rng.random((70, 3)) * 2.0 - 0.5) * np.array([7.3, 5.9, 9.1])
+        r_max, nbins = 2.9, 1000
+    elif box_type == TRIC:
+        box = w.triclinic_box(7.0, 8.0, 6.5, 75.0, 105.0, 95.0)
+        x = (w.box_matrix(box) @ (rng.random((70, 3)) * 2.0 - 0.5).T).T
+        r_max, nbins = 0.95 * w.box_heights(box).min() / 2, 997
+    else:
+        box = None
+        x = rng.random((70, 3)) * 5.0 - 2.5
+        r_max, nbins = 4.1, 1001
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert np.any(x.astype(np.float32).astype(np.float64) != x)  # not float32 values
+    # r^2 itself against the exact rational value: each component of the distance
+    # vector now carries rounding errors of the coordinate magnitude X (the
+    # subtraction and, with a box, the image steps): |dr^2| <= 2 |d'| e + e^2 per
+    # component with e <= 8 * 2^-53 * X, plus a few relative roundings of the sum.
+    # Coordinates rounded to float32 (errors 2^-24 X) fail this by far.
+    iu, ju = np.triu_indices(len(x), 1)
+    ours = oracle_mod.pairs_r2(x, iu, ju, box_type, box)
+    X = float(np.abs(x).max()) + (0.0 if box is None else float(np.abs(box).sum()))
+    e = 8.0 * 2.0 ** -53 * X
+    for p in range(len(iu)):
+        ex = float(_exact_r2(x[iu[p]], x[ju[p]], box_type, box))
+        tol = 2.0 * math.sqrt(3.0 * ex) * e + 3.0 * e * e + 4e-16 * ex
+        assert abs(ours[p] - ex) <= tol, (p, ours[p], ex)
+    direct = np.zeros(nbins, dtype=np.uint64)
+    for i in range(len(x)):
+        for j in range(i + 1, len(x)):
+            kb, t = _exact_bin(_exact_r2(x[i], x[j], box_type, box), r_max, nbins)
+            assert abs(t - round(t)) > 1e-9 or t > nbins + 1
+            if kb < nbins:
+                direct[kb] += 1
+    h = oracle_mod.histogram(x, [0, len(x)], box_type, box, r_max, nbins, nthreads=4)[0]
+    assert np.array_equal(h, direct)
+
+
+def test_f64_input_dyadic_translation(oracle_mod):
+    # multiples of 2^-30 below 2^8: every difference is exact in binary64, so a
+    # translation by a dyadic box vector leaves every bin unchanged
+    rng = np.random.default_rng(90)
+    box = w.ortho_box(64.0, 48.0, 80.0)
+    x = np.floor(rng.random((600, 3)) * np.array([64.0, 48.0, 80.0]) * 2.0 ** 30) / 2.0 ** 30
+    h0 = oracle_mod.histogram(x, [0, 200, 600], ORTHO, box, 23.0, 900, nthreads=4)
+    h1 = oracle_mod.histogram(x + np.array([64.0, -48.0, 160.0]), [0, 200, 600], ORTHO, box, 23.0, 900,
+                              nthreads=4)
+    assert np.array_equal(h0, h1)
