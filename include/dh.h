@@ -68,6 +68,10 @@ typedef enum { DH_BOX_NONE = 0, DH_BOX_ORTHO = 1, DH_BOX_TRICLINIC = 2 } dh_box_
 #define DH_DEVICE_PTRS 0x1u /* coords and out are device pointers (same device as the context) */
 #define DH_ACCUMULATE 0x2u  /* add into out instead of overwriting it */
 #define DH_COORDS_F4 0x4u   /* coords are n x 4 floats (x,y,z,ignored) instead of n x 3 */
+#define DH_COORDS_F64 0x8u  /* coords point to binary64 values (cast the pointer): the distance vector
+                               is then rounded once per component, as the binary64 definition does;
+                               plain and batched paths only (dh_submit and dh_histogram_noalloc
+                               return DH_ERR_INVALID) */
 
 /* dh_config.flags */
 #define DH_CFG_NO_GRAPH 0x1u /* batched path: launch directly instead of replaying a CUDA graph */
@@ -92,7 +96,8 @@ typedef struct {
 } dh_config;
 
 typedef struct {
-  const float* coords;             /* n x 3 (or n x 4 with DH_COORDS_F4) float32, species contiguous */
+  const float* coords;             /* n x 3 (or n x 4 with DH_COORDS_F4) float32 (binary64 with
+                                      DH_COORDS_F64), species contiguous */
   int64_t n;                       /* number of particles, >= 0 */
   const int64_t* species_offsets;  /* HOST array of n_species+1 entries: 0 = o[0] <= o[1] <= ... <= o[S] = n */
   int32_t n_species;               /* S >= 1 */
@@ -101,7 +106,7 @@ typedef struct {
   double r_max;                    /* upper end of the histogram, > 0 and finite */
   int32_t nbins;                   /* number of bins, 1 <= nbins <= DH_MAX_BINS */
   uint64_t* out;                   /* S(S+1)/2 x nbins counts */
-  uint32_t flags;                  /* DH_DEVICE_PTRS | DH_ACCUMULATE | DH_COORDS_F4 */
+  uint32_t flags;                  /* DH_DEVICE_PTRS | DH_ACCUMULATE | DH_COORDS_F4 | DH_COORDS_F64 */
 } dh_frame;
 
 /* 2^22 - 64: the float32 bin coordinate, clamped a few bins beyond the last

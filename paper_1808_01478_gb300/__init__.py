@@ -34,6 +34,7 @@ DH_BOX_TRICLINIC = 2
 DH_DEVICE_PTRS = 0x1
 DH_ACCUMULATE = 0x2
 DH_COORDS_F4 = 0x4
+DH_COORDS_F64 = 0x8
 DH_CFG_NO_GRAPH = 0x1
 DH_CFG_TIMING = 0x2
 DH_CFG_AUTOTUNE = 0x4
@@ -255,7 +256,8 @@ def n_hist(n_species: int) -> int:
 
 
 class FrameArgs:
-    """Keeps the buffers referenced by one dh_frame alive."""
+    """Keeps the buffers referenced by one dh_frame alive.  float64 coordinates
+    (numpy or torch) are passed as binary64 (DH_COORDS_F64), anything else as float32."""
 
     def __init__(self, coords, offsets, box_type, box, r_max, nbins, out=None, accumulate=False):
         offs = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -265,7 +267,9 @@ class FrameArgs:
         flags = 0
         if _is_torch(coords) and coords.is_cuda:
             import torch
-            assert coords.dtype == torch.float32 and coords.is_contiguous()
+            assert coords.dtype in (torch.float32, torch.float64) and coords.is_contiguous()
+            if coords.dtype == torch.float64:
+                flags |= DH_COORDS_F64
             if coords.dim() == 2 and coords.shape[1] == 4:
                 flags |= DH_COORDS_F4
             n = coords.shape[0]
@@ -276,7 +280,10 @@ class FrameArgs:
             cptr, optr = coords.data_ptr(), out.data_ptr()
             self.keep += [coords, out]  # the library reads these buffers until the call (or request) ends
         else:
-            c = np.ascontiguousarray(coords, dtype=np.float32)
+            f64 = np.asarray(coords).dtype == np.float64
+            c = np.ascontiguousarray(coords, dtype=np.float64 if f64 else np.float32)
+            if f64:
+                flags |= DH_COORDS_F64
             if c.ndim == 2 and c.shape[1] == 4:
                 flags |= DH_COORDS_F4
             n = c.shape[0]

@@ -27,6 +27,7 @@ constexpr int kNumVariants = 4;
 // setup kernels fill the second.
 struct FrameDev {
   const float4* X;   // packed coordinates (x,y,z,0), frame-local index
+  const double4* X64;  // binary64 input coordinates (x,y,z,0), or null for float32 input
   uint64_t* out;     // S(S+1)/2 x nbins histograms of this frame
   const double* T;   // binary64 thresholds T[0..nbins]
   const float2* Tf;  // the same thresholds as float pairs (hi, lo), hi + lo = T to ~2^-48
@@ -79,8 +80,9 @@ struct Segment {
 
 // Staging job: one frame's coordinates (n x stride floats) -> float4.
 struct StageJob {
-  const float* src;
+  const float* src;  // n x stride float32, or binary64 when dst64 is set
   float4* dst;
+  double4* dst64;    // binary64 input: the values themselves (dst gets them rounded to float32)
   FrameDev* fd;
   int64_t n;
   int32_t stride;
@@ -124,8 +126,10 @@ struct PairLaunch {
 cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cudaStream_t stream);
 cudaError_t launch_frame_setup(FrameDev* frames, int n_frames, int pass_hi_max, cudaStream_t stream);
 // counts: zeroed, sum of 2^(3g) over the segments; keys and Xs: one per particle
+// X64 and Xs64 (binary64 copies, same indexing) may be null
 cudaError_t launch_spatial_sort(const SortSeg* segs, int n_segs, int max_chunks, float4* X, float4* Xs,
-                                int32_t* keys, uint32_t* counts, cudaStream_t stream);
+                                double4* X64, double4* Xs64, int32_t* keys, uint32_t* counts,
+                                cudaStream_t stream);
 cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* status,
                               cudaStream_t stream);
 // One pair-kernel launch over segments whose frames all have minimum-image variant `variant`.

@@ -133,8 +133,9 @@ __global__ void thresholds_kernel(double r_max, int32_t nbins, double* T, int32_
 // ------------------------------------------------------------------ A1: staging
 
 // Staging of several frames at once: block b handles chunk b of the job whose
-// chunk range contains it; coords (n x stride floats) -> float4, per-axis
-// min/max (for the error window) and finiteness.
+// chunk range contains it; coords (n x stride floats, or doubles) -> float4
+// (and double4 for binary64 input), per-axis min/max of the float32 values (for
+// the error window) and finiteness.
 __global__ void stage_kernel(const StageJob* __restrict__ jobs, int n_jobs) {
   const long long chunk = blockIdx.x;
   int lo = 0, hi = n_jobs - 1;
@@ -150,8 +151,20 @@ __global__ void stage_kernel(const StageJob* __restrict__ jobs, int n_jobs) {
   int bad = 0;
   const float* __restrict__ src = J.src;
   const int stride = J.stride;
+  const double* __restrict__ src64 = reinterpret_cast<const double*>(src);
   for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    float x = src[i * stride], y = src[i * stride + 1], z = src[i * stride + 2];
+    float x, y, z;
+    if (J.dst64) {  // binary64 input: kept as given, and rounded to float32 for the fast path
+      double a = src64[i * stride], b = src64[i * stride + 1], c = src64[i * stride + 2];
+      J.dst64[i] = make_double4(a, b, c, 0.0);
+      x = __double2float_rn(a);
+      y = __double2float_rn(b);
+      z = __double2float_rn(c);
+    } else {
+      x = src[i * stride];
+      y = src[i * stride + 1];
+      z = src[i * stride + 2];
+    }
     bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
     J.dst[i] = make_float4(x, y, z, 0.0f);
     mn0 = fminf(mn0, x); mn1 = fminf(mn1, y); mn2 = fminf(mn2, z);
@@ -261,21 +274,27 @@ __global__ void sort_scan_kernel(const SortSeg* segs, uint32_t* counts) {
 }
 
 __global__ void sort_scatter_kernel(const SortSeg* segs, const float4* __restrict__ X,
-                                    const int32_t* __restrict__ keys, uint32_t* cursors, float4* Xs) {
+                                    const double4* __restrict__ X64, const int32_t* __restrict__ keys,
+                                    uint32_t* cursors, float4* Xs, double4* Xs64) {
   const SortSeg S = segs[blockIdx.y];
   const int64_t i0 = (int64_t)blockIdx.x * kSortChunk;
   const int64_t i1 = min((int64_t)S.n, i0 + kSortChunk);
   for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     uint32_t pos = atomicAdd(cursors + S.key0 + (uint32_t)keys[S.x0 + i], 1u);
     Xs[S.x0 + pos] = X[S.x0 + i];
+    if (X64) Xs64[S.x0 + pos] = X64[S.x0 + i];
   }
 }
 
-__global__ void sort_copy_kernel(const SortSeg* segs, const float4* __restrict__ Xs, float4* X) {
+__global__ void sort_copy_kernel(const SortSeg* segs, const float4* __restrict__ Xs, float4* X,
+                                 const double4* __restrict__ Xs64, double4* X64) {
   const SortSeg S = segs[blockIdx.y];
   const int64_t i0 = (int64_t)blockIdx.x * kSortChunk;
   const int64_t i1 = min((int64_t)S.n, i0 + kSortChunk);
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) X[S.x0 + i] = Xs[S.x0 + i];
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    X[S.x0 + i] = Xs[S.x0 + i];
+    if (X64) X64[S.x0 + i] = Xs64[S.x0 + i];
+  }
 }
 
 // ------------------------------------------------------------------ per-frame error window
@@ -321,10 +340,14 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   FrameDev& F = frames[f];
   const double u = 1.0 / 16777216.0;
   double R[3] = {0, 0, 0};
+  // binary64 input: the float32 path starts from coordinates rounded to float32,
+  // each within half an ulp of the largest magnitude on its axis
+  double conv[3] = {0, 0, 0};
   if (F.n > 0 && F.cmin[0] <= F.cmax[0]) {
     for (int c = 0; c < 3; ++c) {
       double lo = float_of_ord(F.cmin[c]), hi = float_of_ord(F.cmax[c]);
       R[c] = hi - lo;
+      if (F.X64) conv[c] = 2.0 * half_ulp_below(fmax(fabs(lo), fabs(hi)));
     }
   }
   double S = (double)F.nbins / F.r_max;
@@ -342,13 +365,14 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     for (int c = 0; c < 3; ++c) {
       double L = B[4 * c];
       double K = floor(R[c] / L * (1.0 + 1e-9) + 0.5);  // largest |k| = nint(d/L) over |d| <= R_c
-      a[c] = half_ulp_below(R[c]) + K * dB[4 * c];
+      a[c] = half_ulp_below(R[c]) + K * dB[4 * c] + conv[c];
       I[c] = R[c] + K * L;
       if (R[c] / L > 1048576.0) all_defer = 1;  // nearest integer via the 1.5*2^23 trick needs |d/L| < 2^22
       Lmin = fmin(Lmin, L);
       // float32 and binary64 can round d/L to different images only within eta of a
       // half integer; both images then have |d'_c| within eta L of L/2
-      double eta = (half_ulp_below(R[c]) + R[c] * fabs((double)F.invf[c] - 1.0 / L)) / L + 1e-15 * (R[c] / L + 1.0);
+      double eta = (half_ulp_below(R[c]) + conv[c] + R[c] * fabs((double)F.invf[c] - 1.0 / L)) / L +
+                   1e-15 * (R[c] / L + 1.0);
       tie_c[c] = 2.0 * eta * L;
     }
     // components that can sit at L_c/2 while t <= nbins + 1 (r <= r_max (1 + 1/nbins))
@@ -369,15 +393,16 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     double Ky = floor(D1y / by * (1.0 + 1e-9) + 0.5);
     double D2x = D1x + Ky * fabs(bx);
     double Kx = floor(D2x / ax * (1.0 + 1e-9) + 0.5);
-    a[0] = half_ulp_below(R[0]) + half_ulp_below(D1x) + half_ulp_below(D2x) + Kz * dB[2] + Ky * dB[1] + Kx * dB[0];
-    a[1] = half_ulp_below(R[1]) + half_ulp_below(D1y) + Kz * dB[5] + Ky * dB[4];
-    a[2] = half_ulp_below(R[2]) + Kz * dB[8];
+    a[0] = half_ulp_below(R[0]) + half_ulp_below(D1x) + half_ulp_below(D2x) + Kz * dB[2] + Ky * dB[1] + Kx * dB[0] +
+           conv[0];
+    a[1] = half_ulp_below(R[1]) + half_ulp_below(D1y) + Kz * dB[5] + Ky * dB[4] + conv[1];
+    a[2] = half_ulp_below(R[2]) + Kz * dB[8] + conv[2];
     I[0] = D2x + Kx * ax;
     I[1] = D1y + Ky * by;
     I[2] = R[2] + Kz * cz;
     // the three nearest-integer decisions must be exact for every pair closer
     // than r_max: their float32 errors must stay below a quarter of the margin
-    double ez = (2.0 * u * R[2] + R[2] * fabs((double)F.invf[2] * cz - 1.0)) / cz;
+    double ez = (2.0 * u * R[2] + conv[2] + R[2] * fabs((double)F.invf[2] * cz - 1.0)) / cz;
     double ey = (2.0 * (a[1] + u * D1y) + D1y * fabs((double)F.invf[1] * by - 1.0)) / by;
     double ex = (2.0 * (a[0] + u * D2x) + D2x * fabs((double)F.invf[0] * ax - 1.0)) / ax;
     double emax = fmax(ex, fmax(ey, ez));
@@ -393,17 +418,21 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     double ey = (3.0 * u * (R[1] + fabs(cy) * Sz) + fabs(cy) * ez) / by + 2.0 * u * Sy;
     double ex = (3.0 * u * (R[0] + fabs(bx) * Sy + fabs(cx) * Sz) + fabs(bx) * ey + fabs(cx) * ez) / ax +
                 2.0 * u * Sx;
-    eps_s = (float)(2.0 * fmax(ex, fmax(ey, ez)) + 1e-12);
+    // binary64 input: the converted coordinates move every fractional coordinate by
+    // at most the sum of the conversion errors over the plane spacings
+    eps_s = (float)(2.0 * fmax(ex, fmax(ey, ez)) + 4.0 * (conv[0] / ax + conv[1] / by + conv[2] / cz) + 1e-12);
     double Kx = floor(Sx + 0.5) + 1.0, Ky = floor(Sy + 0.5) + 1.0, Kz = floor(Sz + 0.5) + 1.0;
     double Ix = R[0] + Kx * ax + Ky * fabs(bx) + Kz * fabs(cx) + ax + fabs(bx) + fabs(cx);
     double Iy = R[1] + Ky * by + Kz * fabs(cy) + by + fabs(cy);
     double Iz = R[2] + Kz * cz + cz;
-    a[0] = u * (R[0] + 7.0 * Ix) + (Kx + 1) * dB[0] + (Ky + 1) * dB[1] + (Kz + 1) * dB[2];
-    a[1] = u * (R[1] + 6.0 * Iy) + (Ky + 1) * dB[4] + (Kz + 1) * dB[5];
-    a[2] = u * (R[2] + 3.0 * Iz) + (Kz + 1) * dB[8];
+    a[0] = u * (R[0] + 7.0 * Ix) + (Kx + 1) * dB[0] + (Ky + 1) * dB[1] + (Kz + 1) * dB[2] + conv[0];
+    a[1] = u * (R[1] + 6.0 * Iy) + (Ky + 1) * dB[4] + (Kz + 1) * dB[5] + conv[1];
+    a[2] = u * (R[2] + 3.0 * Iz) + (Kz + 1) * dB[8] + conv[2];
     I[0] = Ix; I[1] = Iy; I[2] = Iz;
     if (Sx > 1048576.0 || Sy > 1048576.0 || Sz > 1048576.0 || eps_s > 0.05f) all_defer = 1;
   }
+  if (F.variant == V_NONE)
+    for (int c = 0; c < 3; ++c) a[c] = conv[c];  // d = xj - xi itself rounds relative to |d| (alpha)
   double beta = S * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * (1.0 + 64.0 * u) + tie + 1.0 / 268435456.0;
   alpha = alpha * (1.0 + 1.0 / 1024.0) + 1e-12;
   double delta = alpha * ((double)F.nbins + 1.0) + beta;
@@ -728,12 +757,13 @@ __device__ int mid_bin(const FrameDev& F, float4 pi, float4 pj) {
 // ---- binary64 last resort
 
 // Squared minimum-image distance in binary64, the same operations in the same
-// order as the definition (Alg. 1, Eq. 5, 27 neighbouring shifts).
+// order as the definition (Alg. 1, Eq. 5, 27 neighbouring shifts); the
+// coordinates are the caller's (float32 promoted exactly, or binary64).
 template <int V>
-__device__ double exact_r2(const FrameDev& F, float4 pi, float4 pj) {
-  double dx = __dsub_rn((double)pj.x, (double)pi.x);
-  double dy = __dsub_rn((double)pj.y, (double)pi.y);
-  double dz = __dsub_rn((double)pj.z, (double)pi.z);
+__device__ double exact_r2(const FrameDev& F, double3 pi, double3 pj) {
+  double dx = __dsub_rn(pj.x, pi.x);
+  double dy = __dsub_rn(pj.y, pi.y);
+  double dz = __dsub_rn(pj.z, pi.z);
   const double* B = F.B;
   if (V == V_ORTHO) {
     double kx = rint(__dmul_rn(dx, F.Linv[0]));
@@ -780,12 +810,26 @@ __device__ __forceinline__ int bin_from_thresholds(const double* __restrict__ T,
   return lo;
 }
 
-// Exact bin of one deferred pair: double-float tier, then binary64 replay.
+// The caller's coordinates of particle i of a frame, in binary64.
+__device__ __forceinline__ double3 coords64(const FrameDev& F, int i) {
+  if (F.X64) {
+    double4 p = F.X64[i];
+    return make_double3(p.x, p.y, p.z);
+  }
+  float4 p = __ldg(F.X + i);
+  return make_double3((double)p.x, (double)p.y, (double)p.z);
+}
+
+// Exact bin of one deferred pair (frame-local indices i, j; float32 copies pi,
+// pj): the double-float tier, then the binary64 replay.  With binary64 input
+// the double-float tier does not apply (its coordinate differences are exact
+// only for float32 input): the replay decides directly.
 template <int V>
-__device__ __forceinline__ int deferred_bin(const FrameDev& F, float4 pi, float4 pj, unsigned& nexact) {
-  int k = mid_bin<V>(F, pi, pj);
+__device__ __forceinline__ int deferred_bin(const FrameDev& F, int i, int j, float4 pi, float4 pj,
+                                            unsigned& nexact) {
+  int k = F.X64 ? -1 : mid_bin<V>(F, pi, pj);
   if (k < 0) {
-    k = bin_from_thresholds(F.T, F.nbins, exact_r2<V>(F, pi, pj));
+    k = bin_from_thresholds(F.T, F.nbins, exact_r2<V>(F, coords64(F, i), coords64(F, j)));
     ++nexact;
   }
   return k;
@@ -811,7 +855,7 @@ __device__ __noinline__ int drain_queue(const FrameDev* F, int pass, int i0, int
     FastParams P;
     load_fast_params(*F, pass, P);
     int relp = provisional_rel<V, MULTI>(P, pi, pj, il & 31);
-    int relx = deferred_bin<V>(*F, pi, pj, nexact) - P.lo;
+    int relx = deferred_bin<V>(*F, i0 + il, j0 + jl, pi, pj, nexact) - P.lo;
     if (relx != relp) {
       atomicAdd(sh + relp, 0xFFFFFFFFu);  // relp lies in the histogram or its guard words
       if ((uint32_t)relx < P.width) atomicAdd(sh + relx, 1u);
@@ -1223,7 +1267,7 @@ __device__ void check_window_pair(const FrameDev& F, const FastParams& P, int i,
   fast_decide2<V>(dx, dy, dz, P, nearedge, nb_unused, rel, rb_unused);
   bool amb0 = false, amb1 = false;
   float q = __fmul_rn(wrap_r2_2<V>(dx, dy, dz, P, amb0, amb1).x, P.S2);
-  double r2 = exact_r2<V>(F, pi, pj);
+  double r2 = exact_r2<V>(F, coords64(F, i), coords64(F, j));
   int k64 = bin_from_thresholds(F.T, F.nbins, r2);
   double t64 = __dmul_rn(__dsqrt_rn(r2), (double)F.nbins / F.r_max);
   if (t64 < (double)F.nbins + 1.0 && isfinite(q)) {
@@ -1235,7 +1279,7 @@ __device__ void check_window_pair(const FrameDev& F, const FastParams& P, int i,
     int k32 = (int)rel;  // lo = 0 here
     if (rel > (uint32_t)F.nbins) k32 = F.nbins;
     if (k32 != k64) ++*viol;
-  } else {
+  } else if (!F.X64) {
     int km = mid_bin<V>(F, pi, pj);
     if (km >= 0 && km != k64) ++*viol;
   }
@@ -1368,13 +1412,14 @@ cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cud
 }
 
 cudaError_t launch_spatial_sort(const SortSeg* segs, int n_segs, int max_chunks, float4* X, float4* Xs,
-                                int32_t* keys, uint32_t* counts, cudaStream_t stream) {
+                                double4* X64, double4* Xs64, int32_t* keys, uint32_t* counts,
+                                cudaStream_t stream) {
   if (n_segs <= 0 || max_chunks <= 0) return cudaSuccess;
   dim3 grid((unsigned)max_chunks, (unsigned)n_segs);
   sort_count_kernel<<<grid, 256, 0, stream>>>(segs, X, keys, counts);
   sort_scan_kernel<<<n_segs, 1024, 0, stream>>>(segs, counts);
-  sort_scatter_kernel<<<grid, 256, 0, stream>>>(segs, X, keys, counts, Xs);
-  sort_copy_kernel<<<grid, 256, 0, stream>>>(segs, Xs, X);
+  sort_scatter_kernel<<<grid, 256, 0, stream>>>(segs, X, X64, keys, counts, Xs, Xs64);
+  sort_copy_kernel<<<grid, 256, 0, stream>>>(segs, Xs, X, Xs64, X64);
   return cudaGetLastError();
 }
 

@@ -78,6 +78,8 @@ extern "C" dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream_pt
   if (!frame) return fail(DH_ERR_INVALID, "frame is NULL");
   if (!(frame->flags & DH_DEVICE_PTRS))
     return fail(DH_ERR_INVALID, "dh_histogram_noalloc needs DH_DEVICE_PTRS (device coords and out)");
+  if (frame->flags & DH_COORDS_F64)
+    return fail(DH_ERR_INVALID, "dh_histogram_noalloc takes float32 coordinates");
   if (frame->n > DH_NOALLOC_MAX_N)
     return fail(DH_ERR_INVALID, "n = %lld exceeds the allocation-free limit of %d particles",
                 (long long)frame->n, DH_NOALLOC_MAX_N);

@@ -266,6 +266,11 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   }
 }
 
+size_t coord_bytes(const dh_frame* f) {
+  const size_t elem = (f->flags & DH_COORDS_F64) ? sizeof(double) : sizeof(float);
+  return elem * (size_t)f->n * ((f->flags & DH_COORDS_F4) ? 4 : 3);
+}
+
 int default_block(int variant, int width) {
   if (width < 16384) return kBlockSmall;
   for (int block = kBlockHuge; block > kBlockSmall; block /= 2)
@@ -372,7 +377,8 @@ struct CallPlan {
   int vmulti[kNumVariants] = {0, 0, 0, 0};
   LaunchParams vparams[kNumVariants];
   int vgrid[kNumVariants] = {0, 0, 0, 0};
-  std::vector<size_t> raw_off;  // per frame, offset in c->raw (host coordinates)
+  std::vector<size_t> raw_off;  // per frame, byte offset in c->raw (host coordinates)
+  bool any_f64 = false;         // some frame has binary64 coordinates
   int max_pass = 1;
   int launched = 0;
   size_t seg_bytes = 0;          // Segment array in the metadata
@@ -400,15 +406,19 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
   P.host_coords = host_coords;
   P.with_pairs = with_pairs;
   std::vector<int64_t> xoff(k + 1, 0);
-  size_t raw_floats = 0;
+  size_t raw_bytes = 0;
   P.raw_off.assign((size_t)k, 0);
+  P.any_f64 = false;
   for (int f = 0; f < k; ++f) {
-    xoff[f + 1] = xoff[f] + pfs[f].src->n;
-    P.raw_off[f] = raw_floats;
-    if (host_coords) raw_floats += (size_t)pfs[f].src->n * ((pfs[f].src->flags & DH_COORDS_F4) ? 4 : 3);
+    const dh_frame* fr = pfs[f].src;
+    xoff[f + 1] = xoff[f] + fr->n;
+    P.raw_off[f] = raw_bytes;
+    P.any_f64 |= (fr->flags & DH_COORDS_F64) != 0;
+    if (host_coords) raw_bytes += (coord_bytes(fr) + 15) & ~(size_t)15;
   }
   DH_CUDA_TRY(c->X.ensure(sizeof(float4) * (size_t)std::max<int64_t>(xoff[k], 1)));
-  if (host_coords) DH_CUDA_TRY(c->raw.ensure(sizeof(float) * std::max<size_t>(raw_floats, 1)));
+  if (P.any_f64) DH_CUDA_TRY(c->X64.ensure(sizeof(double4) * (size_t)std::max<int64_t>(xoff[k], 1)));
+  if (host_coords) DH_CUDA_TRY(c->raw.ensure(std::max<size_t>(raw_bytes, 16)));
   DH_CUDA_TRY(c->ctl.ensure(sizeof(Control) * kNumVariants));
   // device metadata: FrameDev[k] | StageJob[k] | Segment[m], uploaded in one copy;
   // segments are grouped by minimum-image variant (one pair-kernel launch each)
@@ -473,6 +483,7 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
   }
   if (P.n_sort > 0) {
     DH_CUDA_TRY(c->sortX.ensure(sizeof(float4) * (size_t)P.sort_particles));
+    if (P.any_f64) DH_CUDA_TRY(c->sortX64.ensure(sizeof(double4) * (size_t)P.sort_particles));
     DH_CUDA_TRY(c->sortK.ensure(sizeof(int32_t) * (size_t)P.sort_particles));
     DH_CUDA_TRY(c->sortC.ensure(sizeof(uint32_t) * (size_t)P.sort_keys));
   }
@@ -486,6 +497,7 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
     if (s != DH_OK) return s;
     c->held_tables.push_back(T);
     fill_frame_dev(pfs[f], hF[f], (const float4*)c->X.p + xoff[f], dev_out[f], T);
+    if (pfs[f].src->flags & DH_COORDS_F64) hF[f].X64 = (const double4*)c->X64.p + xoff[f];
     P.max_pass = std::max(P.max_pass, pfs[f].sweeps);
   }
   // A1 staging jobs
@@ -497,8 +509,9 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
     StageJob& J = hJ[P.n_jobs++];
     std::memset(&J, 0, sizeof J);
     J.stride = (fr->flags & DH_COORDS_F4) ? 4 : 3;
-    J.src = host_coords ? (const float*)c->raw.p + P.raw_off[f] : fr->coords;
+    J.src = host_coords ? (const float*)((const unsigned char*)c->raw.p + P.raw_off[f]) : fr->coords;
     J.dst = (float4*)c->X.p + xoff[f];
+    J.dst64 = (fr->flags & DH_COORDS_F64) ? (double4*)c->X64.p + xoff[f] : nullptr;
     J.fd = dF + f;
     J.n = fr->n;
     J.chunk0 = P.n_chunks;
@@ -544,8 +557,7 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
     for (int f = 0; f < k; ++f) {
       const dh_frame* fr = pfs[f].src;
       if (fr->n == 0) continue;
-      int stride = (fr->flags & DH_COORDS_F4) ? 4 : 3;
-      DH_CUDA_TRY(cudaMemcpyAsync((float*)c->raw.p + P.raw_off[f], fr->coords, sizeof(float) * (size_t)fr->n * stride,
+      DH_CUDA_TRY(cudaMemcpyAsync((unsigned char*)c->raw.p + P.raw_off[f], fr->coords, coord_bytes(fr),
                                   cudaMemcpyHostToDevice, st));
     }
   DH_CUDA_TRY(cudaMemcpyAsync(dF, c->hmeta.p, P.meta_bytes, cudaMemcpyHostToDevice, st));
@@ -557,7 +569,9 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
     const SortSeg* dSort = (const SortSeg*)((unsigned char*)dS + P.seg_bytes);
     DH_CUDA_TRY(cudaMemsetAsync(c->sortC.p, 0, sizeof(uint32_t) * (size_t)P.sort_keys, st));
     DH_CUDA_TRY(launch_spatial_sort(dSort, P.n_sort, P.sort_chunks, (float4*)c->X.p, (float4*)c->sortX.p,
-                                    (int32_t*)c->sortK.p, (uint32_t*)c->sortC.p, st));
+                                    P.any_f64 ? (double4*)c->X64.p : nullptr,
+                                    P.any_f64 ? (double4*)c->sortX64.p : nullptr, (int32_t*)c->sortK.p,
+                                    (uint32_t*)c->sortC.p, st));
     launched += 4;
   }
   DH_CUDA_TRY(launch_frame_setup(dF, k, 0, st));
@@ -1075,6 +1089,8 @@ dh_status dh_destroy(dh_ctx* c) {
   c->tstat.release();
   c->aux.release();
   c->sortX.release();
+  c->sortX64.release();
+  c->X64.release();
   c->sortK.release();
   c->sortC.release();
   c->hmeta.release();

@@ -117,6 +117,9 @@ struct TuneEntry {
 };
 TuneKey make_tune_key(int variant, int width, double mean_pairs_per_frame, int frames);
 
+// Bytes of a frame's coordinate array (float32 or binary64, 3 or 4 per particle).
+size_t coord_bytes(const dh_frame* f);
+
 // Threads per block for a launch without a measured shape: from 16,384 bins on,
 // a 256-thread block's histogram leaves room for at most two blocks per SM, and
 // one 1024-thread block sharing one histogram keeps more warps resident (512
@@ -168,7 +171,9 @@ struct dh_ctx {
   dh::HostBuf hout;    // pinned staging for accumulate-on-host
   dh::DevBuf tstat;    // threshold build status
   dh::DevBuf aux;      // small per-call arrays (g(r) pair densities)
-  dh::DevBuf sortX;    // spatial order: scratch copy of the coordinates,
+  dh::DevBuf X64;      // binary64 input coordinates (double4), when a frame has them
+  dh::DevBuf sortX64;  // spatial order: scratch copy of those,
+  dh::DevBuf sortX;    // of the float32 coordinates,
   dh::DevBuf sortK;    //   cell keys,
   dh::DevBuf sortC;    //   and cell counters
   dh::ThresholdCache tcache;

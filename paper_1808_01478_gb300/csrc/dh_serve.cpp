@@ -268,6 +268,8 @@ dh_status Server::submit(const dh_frame* f, uint64_t* ticket) {
   r->frame = *f;
   r->offs.assign(f->species_offsets, f->species_offsets + f->n_species + 1);
   r->frame.species_offsets = r->offs.data();
+  if (f->flags & DH_COORDS_F64)
+    return fail(DH_ERR_INVALID, "the served path takes float32 coordinates (DH_COORDS_F64: use dh_histogram)");
   dh_status s = check_frame(&r->frame, r->pf, ctx_->max_width);
   if (s != DH_OK) return s;
   r->pf.src = &r->frame;

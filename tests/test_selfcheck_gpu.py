@@ -50,3 +50,25 @@ def test_window_bound_holds(ctx, name):
     assert res["checked"] > 1 << 20
     assert res["violations"] == 0, res
     assert res["max_ratio"] < 1.0, res
+
+
+def _f64(f):
+    # the same frame with binary64 coordinates that are not float32 values
+    x = f.coords.astype(np.float64) + w.rng_for(5).random(f.coords.shape) * 1e-5
+    return x, f
+
+
+F64_FRAMES = {
+    "f64_ortho": lambda: _f64(w.headline_frame(w.BOX_ORTHO, seed=14, n=300_000)),
+    "f64_tric": lambda: _f64(w.headline_frame(w.BOX_TRICLINIC, seed=15, n=300_000)),
+    "f64_none": lambda: _f64(w.headline_frame(w.BOX_NONE, seed=16, n=300_000)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(F64_FRAMES))
+def test_window_bound_holds_for_binary64_input(ctx, name):
+    x, f = F64_FRAMES[name]()
+    res = ctx.check_window(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, n_samples=1 << 23, seed=8)
+    assert res["checked"] > 1 << 20
+    assert res["violations"] == 0, res
+    assert res["max_ratio"] < 1.0, res
