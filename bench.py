@@ -597,6 +597,32 @@ def run_gpu(args, world, rank, local):
             "tile_image_frac": round(st["uniform_pairs"] / max(1, st["pairs"]), 4),
         }
 
+    # ---- binary64 input coordinates (the same frames, coordinates perturbed below
+    # float32 resolution so that they are not float32 values)
+    f64 = {}
+    if args.f64_steps > 0:
+        for k, f in enumerate(frames):
+            x64 = torch.from_numpy(f.coords.astype(np.float64)
+                                   + w.rng_for(31 + k).random(f.coords.shape) * 1e-5).to(dev)
+            ctx.histogram(x64, f.offsets, f.box_type, f.box, f.r_max, f.nbins, OUT[k])
+            ts = []
+            for _ in range(args.f64_steps):
+                flush_l2()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.histogram(x64, f.offsets, f.box_type, f.box, f.r_max, f.nbins, OUT[k])
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            st = ctx.stats()
+            f64[w.BOX_NAMES[f.box_type]] = {
+                "gpairs_s": round(pairs[k] / (statistics.mean(ts) / 1e3) / 1e9, 3),
+                "deferred_frac": round(st["deferred"] / max(1, st["pairs"]), 6),
+                "binary64_frac": round(st["exact_fallback"] / max(1, st["pairs"]), 6),
+            }
+            del x64
+
     # ---- end to end through the C ABI with pinned host buffers
     hx = [torch.from_numpy(f.coords).pin_memory() for f in frames]
     ho = [torch.zeros((1, f.nbins), dtype=torch.int64).pin_memory() for f in frames]
@@ -628,6 +654,7 @@ def run_gpu(args, world, rank, local):
         "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "matches_device_result": e2e_ok},
         "plain": plain,
+        "f64_input": f64 or None,
         "batched": {"gpairs_s": round(value, 3), "deferred_frac": round(stats_b["deferred"] / max(1, stats_b["pairs"]), 6),
                     "cuda_graph": bool(stats_b["graph_replays"]),
                     "launch_shape": {"tile_j": stats_b["tile_j"], "hist_depth": stats_b["hist_depth"],
@@ -664,6 +691,7 @@ def main(argv=None) -> int:
     ap.add_argument("--nbins", type=int, default=10_000)
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--f64-steps", type=int, default=1, help="timed calls per frame with binary64 coordinates")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -439,9 +439,11 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   if (!(delta < 0.25)) all_defer = 1;
   const double slack = 1.0 + 1.0 / 1024.0;
   // One-FMA forms of the q-space bound 2 alpha q + (alpha + 2 beta) t' + beta:
-  //  no box: t' <= (q + 1)/2 gives (2.5 alpha + beta) q + (alpha/2 + 2 beta);
-  //  periodic: for t' <= nbins + 2 (pairs beyond are never counted whatever the
-  //  decision), 2 alpha q <= 2 alpha (nbins + 2) t' and t' <= s (1 + 2^-18).
+  //  no box (float32 input only, so beta is tiny): t' <= (q + 1)/2 gives
+  //  (2.5 alpha + beta) q + (alpha/2 + 2 beta);
+  //  otherwise: for t' <= nbins + 2 (pairs beyond are never counted whatever the
+  //  decision, thanks to the clamp of the root), 2 alpha q <= 2 alpha (nbins + 2) t'
+  //  and t' <= s (1 + 2^-18).
   if (all_defer) {
     F.qb1 = F.qb0 = 1e30f;
   } else if (F.variant == V_NONE) {
@@ -453,6 +455,9 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   }
   double Imax = fmax(I[0], fmax(I[1], I[2]));
   double amid = 1.7320508075688772 * (R[0] + R[1] + R[2] + 4.0 * Imax) / 1099511627776.0;  // 2^-40
+  if (F.X64)  // binary64 input: the split coordinates (2^-48 of the magnitude each) and d rounded in binary64
+    amid += 1.7320508075688772 * 4.0 * fmax(conv[0], fmax(conv[1], conv[2])) / 16777216.0 +
+            1.7320508075688772 * (R[0] + R[1] + R[2]) / 4503599627370496.0;
   F.mid2 = (float)(1.0 / 274877906944.0);                                                   // 2^-38
   F.mid1 = (float)(2.0 * amid / S * 1.01);
   F.tie_eps = (float)tie_eps;
@@ -712,14 +717,36 @@ __device__ __forceinline__ DF df_norm2(DF x, DF y, DF z) {
   return {s2.h, low};
 }
 
+// xj - xi for binary64 values, as a double-float: each value split into float32
+// high and low parts (x = h + l to about 2^-48 |x|), the high parts subtracted
+// exactly and the low parts added to the error term.
+__device__ __forceinline__ DF df_diff64(double xj, double xi) {
+  const float hj = __double2float_rn(xj), hi = __double2float_rn(xi);
+  const float lj = __double2float_rn(__dsub_rn(xj, (double)hj)), li = __double2float_rn(__dsub_rn(xi, (double)hi));
+  DF s = two_sum(hj, -hi);
+  return {s.h, __fadd_rn(s.l, __fsub_rn(lj, li))};
+}
+
 // Bin of a deferred pair from r^2 evaluated in double-float arithmetic (about
-// 44 bits, with the exact coordinate differences and the same nearest images
+// 44 bits, with the exact coordinate differences (float32 input; binary64
+// input to about 2^-47 of the coordinate magnitude) and the same nearest images
 // as the float32 path), compared with the split binary64 threshold of the
-// nearest edge.  Returns -1 when even this is too close to call.
+// nearest edge.  Returns -1 when even this is too close to call.  i, j:
+// frame-local indices; pi, pj: the float32 coordinates.
 template <int V>
-__device__ int mid_bin(const FrameDev& F, float4 pi, float4 pj) {
+__device__ int mid_bin(const FrameDev& F, int i, int j, float4 pi, float4 pj) {
   if (V == V_TRIC_SEARCH) return -1;
-  DF dx = two_sum(pj.x, -pi.x), dy = two_sum(pj.y, -pi.y), dz = two_sum(pj.z, -pi.z);
+  DF dx, dy, dz;
+  if (F.X64) {
+    const double4 a = F.X64[i], b = F.X64[j];
+    dx = df_diff64(b.x, a.x);
+    dy = df_diff64(b.y, a.y);
+    dz = df_diff64(b.z, a.z);
+  } else {
+    dx = two_sum(pj.x, -pi.x);
+    dy = two_sum(pj.y, -pi.y);
+    dz = two_sum(pj.z, -pi.z);
+  }
   if (V == V_ORTHO) {
     float kx = nint_scaled(dx.h, F.invf[0]), ky = nint_scaled(dy.h, F.invf[1]), kz = nint_scaled(dz.h, F.invf[2]);
     dx = df_sub_kb(dx, kx, F.Bf[0], F.Bl[0]);
@@ -821,13 +848,11 @@ __device__ __forceinline__ double3 coords64(const FrameDev& F, int i) {
 }
 
 // Exact bin of one deferred pair (frame-local indices i, j; float32 copies pi,
-// pj): the double-float tier, then the binary64 replay.  With binary64 input
-// the double-float tier does not apply (its coordinate differences are exact
-// only for float32 input): the replay decides directly.
+// pj): the double-float tier, then the binary64 replay.
 template <int V>
 __device__ __forceinline__ int deferred_bin(const FrameDev& F, int i, int j, float4 pi, float4 pj,
                                             unsigned& nexact) {
-  int k = F.X64 ? -1 : mid_bin<V>(F, pi, pj);
+  int k = mid_bin<V>(F, i, j, pi, pj);
   if (k < 0) {
     k = bin_from_thresholds(F.T, F.nbins, exact_r2<V>(F, coords64(F, i), coords64(F, j)));
     ++nexact;
@@ -965,6 +990,7 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
       return;
     }
   }
+
   if (it.masked) run_tile<V, true, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
   else run_tile<V, false, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
 }
@@ -1279,8 +1305,8 @@ __device__ void check_window_pair(const FrameDev& F, const FastParams& P, int i,
     int k32 = (int)rel;  // lo = 0 here
     if (rel > (uint32_t)F.nbins) k32 = F.nbins;
     if (k32 != k64) ++*viol;
-  } else if (!F.X64) {
-    int km = mid_bin<V>(F, pi, pj);
+  } else {
+    int km = mid_bin<V>(F, i, j, pi, pj);
     if (km >= 0 && km != k64) ++*viol;
   }
 }

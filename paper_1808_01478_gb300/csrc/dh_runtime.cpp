@@ -182,6 +182,8 @@ dh_status check_frame(const dh_frame* f, PlannedFrame& pf, int max_width) {
   switch (f->box_type) {
     case DH_BOX_NONE:
       pf.variant = V_NONE;
+      pf.big_box = (f->flags & DH_COORDS_F64) != 0;
+      if (pf.big_box) pf.variant = V_ORTHO;
       break;
     case DH_BOX_ORTHO:
       for (int q = 0; q < 9; ++q) {
@@ -239,6 +241,7 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   F.r_max = f->r_max;
   for (int q = 0; q < 9; ++q) {
     F.B[q] = (f->box_type == DH_BOX_NONE) ? 0.0 : f->box[q];
+    if (pf.big_box) F.B[q] = (q == 0 || q == 4 || q == 8) ? 0x1p60 : 0.0;
     F.Bf[q] = (float)F.B[q];
     F.Bl[q] = (float)(F.B[q] - (double)F.Bf[q]);
   }
@@ -448,7 +451,7 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
     P.sort_keys = 0;
     P.sort_chunks = 0;
     for (int f = 0; f < k; ++f) {
-      if (pfs[f].variant != V_ORTHO && pfs[f].variant != V_TRIC) continue;
+      if ((pfs[f].variant != V_ORTHO && pfs[f].variant != V_TRIC) || pfs[f].big_box) continue;
       const int64_t* o = pfs[f].src->species_offsets;
       for (int a = 0; a < pfs[f].src->n_species; ++a) {
         const int64_t na = o[a + 1] - o[a];

@@ -86,6 +86,11 @@ struct PlannedFrame {
   int32_t sweep_width;
   double margin;
   uint64_t pairs;
+  // binary64 input without a box runs as an orthorhombic box of side 2^60: every
+  // nearest image is 0 and each wrap step an exact identity, so the histogram is
+  // the no-box one, with the orthorhombic error window (linear in the root) that
+  // suits the absolute error of the rounded input
+  bool big_box = false;
 };
 
 dh_status check_frame(const dh_frame* f, PlannedFrame& pf, int max_width);
