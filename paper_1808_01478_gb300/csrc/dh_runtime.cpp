@@ -269,6 +269,35 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   }
 }
 
+int sort_grid_bits(int64_t n) {
+  int g = (int)std::floor(std::log2(std::cbrt((double)n / 16.0)));
+  return std::min(6, std::max(1, g));
+}
+
+std::vector<SortSeg> plan_spatial_order(const PlannedFrame& pf, const FrameDev* fd, int64_t x0, int64_t key0,
+                                        int64_t* keys, int* chunks) {
+  std::vector<SortSeg> out;
+  *keys = 0;
+  *chunks = 0;
+  if ((pf.variant != V_ORTHO && pf.variant != V_TRIC) || pf.big_box) return out;
+  const int64_t* o = pf.src->species_offsets;
+  for (int a = 0; a < pf.src->n_species; ++a) {
+    const int64_t na = o[a + 1] - o[a];
+    if (na < kSortMinParticles) continue;
+    SortSeg g;
+    std::memset(&g, 0, sizeof g);
+    g.fd = fd;
+    g.x0 = x0 + o[a];
+    g.n = (int32_t)na;
+    g.g = sort_grid_bits(na);
+    g.key0 = key0 + *keys;
+    *keys += (int64_t)1 << (3 * g.g);
+    *chunks = std::max<int>(*chunks, (int)((na + kSortChunk - 1) / kSortChunk));
+    out.push_back(g);
+  }
+  return out;
+}
+
 size_t coord_bytes(const dh_frame* f) {
   const size_t elem = (f->flags & DH_COORDS_F64) ? sizeof(double) : sizeof(float);
   return elem * (size_t)f->n * ((f->flags & DH_COORDS_F4) ? 4 : 3);
@@ -391,15 +420,7 @@ struct CallPlan {
   int64_t sort_particles = 0;    // particles of the frames (index space of keys and the scratch copy)
 };
 
-// Species of orthorhombic and triclinic frames are put in spatial (Morton) order
-// before the pair kernel, from this many particles on.
-constexpr int32_t kSortMinParticles = 2048;
 
-// Grid bits per axis for a species of n particles: about 16 particles per cell.
-int sort_grid_bits(int64_t n) {
-  int g = (int)std::floor(std::log2(std::cbrt((double)n / 16.0)));
-  return std::min(6, std::max(1, g));
-}
 
 dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const std::vector<uint64_t*>& dev_out,
                          bool host_coords, bool with_pairs, CallPlan& P) {
@@ -451,22 +472,12 @@ dh_status prepare_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, const 
     P.sort_keys = 0;
     P.sort_chunks = 0;
     for (int f = 0; f < k; ++f) {
-      if ((pfs[f].variant != V_ORTHO && pfs[f].variant != V_TRIC) || pfs[f].big_box) continue;
-      const int64_t* o = pfs[f].src->species_offsets;
-      for (int a = 0; a < pfs[f].src->n_species; ++a) {
-        const int64_t na = o[a + 1] - o[a];
-        if (na < kSortMinParticles) continue;
-        SortSeg g;
-        std::memset(&g, 0, sizeof g);
-        g.fd = dF + f;
-        g.x0 = xoff[f] + o[a];
-        g.n = (int32_t)na;
-        g.g = sort_grid_bits(na);
-        g.key0 = P.sort_keys;
-        P.sort_keys += (int64_t)1 << (3 * g.g);
-        P.sort_chunks = std::max<int>(P.sort_chunks, (int)((na + kSortChunk - 1) / kSortChunk));
-        sorts.push_back(g);
-      }
+      int64_t keys = 0;
+      int chunks = 0;
+      std::vector<SortSeg> fs = plan_spatial_order(pfs[f], dF + f, xoff[f], P.sort_keys, &keys, &chunks);
+      sorts.insert(sorts.end(), fs.begin(), fs.end());
+      P.sort_keys += keys;
+      P.sort_chunks = std::max(P.sort_chunks, chunks);
     }
     P.n_sort = (int)sorts.size();
     P.sort_particles = xoff[k];

@@ -125,6 +125,16 @@ TuneKey make_tune_key(int variant, int width, double mean_pairs_per_frame, int f
 // Bytes of a frame's coordinate array (float32 or binary64, 3 or 4 per particle).
 size_t coord_bytes(const dh_frame* f);
 
+// Species of orthorhombic and triclinic frames are put in spatial (Morton)
+// order before the pair kernel, from this many particles on, with about 16
+// particles per cell.  plan_spatial_order lists the species of one frame (its
+// particles from x0 in the packed coordinates, its counters from key0) and
+// returns the counters and most staging chunks they need.
+constexpr int32_t kSortMinParticles = 2048;
+int sort_grid_bits(int64_t n);
+std::vector<SortSeg> plan_spatial_order(const PlannedFrame& pf, const FrameDev* fd, int64_t x0, int64_t key0,
+                                        int64_t* keys, int* chunks);
+
 // Threads per block for a launch without a measured shape: from 16,384 bins on,
 // a 256-thread block's histogram leaves room for at most two blocks per SM, and
 // one 1024-thread block sharing one histogram keeps more warps resident (512

@@ -118,6 +118,15 @@ struct Request {
   size_t res_count = 0;
   double* T = nullptr;
   std::vector<Segment> segs;     // all segments, items numbered from 0
+  // spatial order of the species (periodic frames): plan, device scratch, pinned upload
+  std::vector<SortSeg> sorts;
+  int64_t sort_keys = 0;
+  int sort_chunks = 0;
+  SortSeg* sort_dev = nullptr;
+  SortSeg* sort_pin = nullptr;
+  float4* sort_X = nullptr;
+  int32_t* sort_K = nullptr;
+  uint32_t* sort_C = nullptr;
   int64_t n_items = 0, next = 0;
   bool prepped = false, finalize_enqueued = false, cancel = false;
   uint64_t last_wave = 0;        // sequence number of the last wave carrying its work
@@ -279,6 +288,12 @@ dh_status Server::submit(const dh_frame* f, uint64_t* ticket) {
   size_t n = (size_t)f->n;
   r->dev_bytes = align_up(sizeof(FrameDev)) + align_up(sizeof(StageJob)) + align_up(16 * std::max<size_t>(n, 1));
   r->pin_bytes = align_up(sizeof(FrameDev)) + align_up(sizeof(StageJob));
+  r->sorts = plan_spatial_order(r->pf, nullptr, 0, 0, &r->sort_keys, &r->sort_chunks);
+  if (!r->sorts.empty()) {
+    r->dev_bytes += align_up(sizeof(SortSeg) * r->sorts.size()) + align_up(16 * n) + align_up(4 * n) +
+                    align_up(4 * (size_t)r->sort_keys);
+    r->pin_bytes += align_up(sizeof(SortSeg) * r->sorts.size());
+  }
   if (!r->dev_ptrs) {
     r->dev_bytes += align_up(4 * (size_t)r->stride * n) + align_up(8 * r->res_count);
     r->pin_bytes += align_up(4 * (size_t)r->stride * n) + align_up(8 * r->res_count);
@@ -384,6 +399,18 @@ void Server::admit() {
     p += align_up(sizeof(FrameDev));
     r.job_pin = (StageJob*)p;
     p += align_up(sizeof(StageJob));
+    if (!r.sorts.empty()) {
+      r.sort_dev = (SortSeg*)d;
+      d += align_up(sizeof(SortSeg) * r.sorts.size());
+      r.sort_X = (float4*)d;
+      d += align_up(16 * (size_t)r.frame.n);
+      r.sort_K = (int32_t*)d;
+      d += align_up(4 * (size_t)r.frame.n);
+      r.sort_C = (uint32_t*)d;
+      d += align_up(4 * (size_t)r.sort_keys);
+      r.sort_pin = (SortSeg*)p;
+      p += align_up(sizeof(SortSeg) * r.sorts.size());
+    }
     if (!r.dev_ptrs) {
       r.raw = (float*)d;
       d += align_up(4 * (size_t)r.stride * (size_t)r.frame.n);
@@ -429,6 +456,17 @@ dh_status Server::prep(Request& r) {
     DH_CUDA_TRY(cudaMemsetAsync(r.hist, 0, 8 * r.res_count, st));
   int64_t chunks = (r.frame.n + kStageChunk - 1) / kStageChunk;
   if (chunks > 0) DH_CUDA_TRY(launch_stage(r.job_dev, 1, chunks, st));
+  if (!r.sorts.empty()) {
+    for (size_t q = 0; q < r.sorts.size(); ++q) {
+      r.sort_pin[q] = r.sorts[q];
+      r.sort_pin[q].fd = r.fd;
+    }
+    DH_CUDA_TRY(cudaMemcpyAsync(r.sort_dev, r.sort_pin, sizeof(SortSeg) * r.sorts.size(), cudaMemcpyHostToDevice,
+                                st));
+    DH_CUDA_TRY(cudaMemsetAsync(r.sort_C, 0, 4 * (size_t)r.sort_keys, st));
+    DH_CUDA_TRY(launch_spatial_sort(r.sort_dev, (int)r.sorts.size(), r.sort_chunks, r.X, r.sort_X, nullptr, nullptr,
+                                    r.sort_K, r.sort_C, st));
+  }
   DH_CUDA_TRY(launch_frame_setup(r.fd, 1, 0, st));
   r.prepped = true;
   return DH_OK;
