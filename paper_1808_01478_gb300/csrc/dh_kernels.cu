@@ -864,11 +864,10 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P);
 
 // Decide the first `count` (<= 32) queued pairs, one per lane, move the
 // provisional count of each to its exact bin where they differ, and shift the
-// rest of the queue down.  Out of line so the hot loop keeps its registers.
-// A queue entry is (i - i0) | (j - j0) << 16 for the tile's first i and j;
-// lane (i - i0) mod 32 evaluated the pair.
+// rest of the queue down.  A queue entry is (i - i0) | (j - j0) << 16 for the
+// tile's first i and j; lane (i - i0) mod 32 evaluated the pair.
 template <int V, bool MULTI>
-__device__ __noinline__ int drain_queue(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
+__device__ __forceinline__ int drain_queue_body(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
                                         uint32_t* sh, int lane) {
   const int count = qcount < 32 ? qcount : 32;
   unsigned nexact = 0;
@@ -893,6 +892,24 @@ __device__ __noinline__ int drain_queue(const FrameDev* F, int pass, int i0, int
   for (int o = 16; o > 0; o >>= 1) nexact += __shfl_xor_sync(kFull, nexact, o);
   if (lane == 0 && nexact) atomicAdd(&const_cast<FrameDev*>(F)->exact, (unsigned long long)nexact);
   return rest;
+}
+
+template <int V, bool MULTI>
+__device__ __noinline__ int drain_queue_call(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
+                                             uint32_t* sh, int lane) {
+  return drain_queue_body<V, MULTI>(F, pass, i0, j0, q, qcount, sh, lane);
+}
+
+// The register allocation of the hot loop decides which form is faster
+// (measured): the periodic variants keep fewer live values across an inlined
+// drain than across a call, the no-box variant the other way round.
+template <int V, bool MULTI>
+__device__ __forceinline__ int drain_queue(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
+                                           uint32_t* sh, int lane) {
+  if constexpr (V == V_ORTHO || V == V_TRIC)
+    return drain_queue_body<V, MULTI>(F, pass, i0, j0, q, qcount, sh, lane);
+  else
+    return drain_queue_call<V, MULTI>(F, pass, i0, j0, q, qcount, sh, lane);
 }
 
 // j tile in shared memory as pairs of particles: A[p] = {x_2p, x_2p+1, y_2p, y_2p+1},
