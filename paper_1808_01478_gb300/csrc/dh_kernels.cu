@@ -562,17 +562,19 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // float32 |d'|^2 of two pairs after the minimum image of the variant; each
 // component is rounded exactly as the scalar sequence of wrap_r2.  UNI: the
 // tile pair's nearest-image integers are known to be kt for every pair (see
-// tile_image), so only the subtractions of the image are left, with the same
-// operands in the same order: the result is bit for bit the one of the
-// per-pair path.
+// tile_image).  Triclinic: only the subtractions of the image are left, with
+// the same operands in the same order, so the result is bit for bit the one of
+// the per-pair path.  Orthorhombic: the caller has already subtracted the
+// images from the coordinates themselves (exactly), so d is the image vector
+// rounded once.
 template <int V, bool UNI = false>
 __device__ __forceinline__ float2 wrap_r2_2(float2 dx, float2 dy, float2 dz, const FastParams& P, bool& amb_a,
                                             bool& amb_b, float3 kt = make_float3(0.f, 0.f, 0.f)) {
   const float2 M = bc2(kMagicRound), NM = bc2(-kMagicRound);
-  if (V == V_ORTHO) {
-    float2 kx = UNI ? bc2(kt.x) : add2(fma2(dx, bc2(P.inv[0]), M), NM);
-    float2 ky = UNI ? bc2(kt.y) : add2(fma2(dy, bc2(P.inv[1]), M), NM);
-    float2 kz = UNI ? bc2(kt.z) : add2(fma2(dz, bc2(P.inv[2]), M), NM);
+  if (V == V_ORTHO && !UNI) {  // (UNI: the coordinates were shifted by the images already)
+    float2 kx = add2(fma2(dx, bc2(P.inv[0]), M), NM);
+    float2 ky = add2(fma2(dy, bc2(P.inv[1]), M), NM);
+    float2 kz = add2(fma2(dz, bc2(P.inv[2]), M), NM);
     dx = fma2(kx, bc2(-P.b[0]), dx);
     dy = fma2(ky, bc2(-P.b[4]), dy);
     dz = fma2(kz, bc2(-P.b[8]), dz);
@@ -669,10 +671,20 @@ __device__ __forceinline__ void fast_decide2(float2 dx, float2 dy, float2 dz, co
 // The relative bin at which the float32 path counted a pair (provisionally,
 // if it deferred it): the scalar replay of decide_arith2 and count_or_defer,
 // operation for operation, for the lane `src_lane` that evaluated the pair.
-template <int V, bool MULTI>
-__device__ __forceinline__ int provisional_rel(const FastParams& P, float4 pi, float4 pj, int src_lane) {
+template <int V, bool MULTI, bool UNI = false>
+__device__ __forceinline__ int provisional_rel(const FastParams& P, float4 pi, float4 pj, int src_lane,
+                                               float3 ti = make_float3(0.f, 0.f, 0.f),
+                                               float3 sj = make_float3(0.f, 0.f, 0.f)) {
   bool amb = false;
-  float r2 = wrap_r2<V>(__fadd_rn(pj.x, -pi.x), __fadd_rn(pj.y, -pi.y), __fadd_rn(pj.z, -pi.z), P, amb);
+  float r2;
+  if (V == V_ORTHO && UNI) {  // the coordinates shifted by the tile's images (exact), no wrap
+    const float dx = __fsub_rn(__fsub_rn(pj.x, sj.x), __fsub_rn(pi.x, ti.x));
+    const float dy = __fsub_rn(__fsub_rn(pj.y, sj.y), __fsub_rn(pi.y, ti.y));
+    const float dz = __fsub_rn(__fsub_rn(pj.z, sj.z), __fsub_rn(pi.z, ti.z));
+    r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+  } else {
+    r2 = wrap_r2<V>(__fadd_rn(pj.x, -pi.x), __fadd_rn(pj.y, -pi.y), __fadd_rn(pj.z, -pi.z), P, amb);
+  }
   float nq = __fmul_rn(r2, -P.S2);
   float sc = fminf(sqrt_approx(-nq), (float)(P.hi + 1 + src_lane));
   if (MULTI) sc = fmaxf(sc, (float)(P.lo - src_lane));
@@ -866,9 +878,10 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P);
 // provisional count of each to its exact bin where they differ, and shift the
 // rest of the queue down.  A queue entry is (i - i0) | (j - j0) << 16 for the
 // tile's first i and j; lane (i - i0) mod 32 evaluated the pair.
-template <int V, bool MULTI>
+template <int V, bool MULTI, bool UNI = false>
 __device__ __forceinline__ int drain_queue_body(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
-                                        uint32_t* sh, int lane) {
+                                                uint32_t* sh, int lane, float3 ti = make_float3(0.f, 0.f, 0.f),
+                                                float3 sj = make_float3(0.f, 0.f, 0.f)) {
   const int count = qcount < 32 ? qcount : 32;
   unsigned nexact = 0;
   if (lane < count) {
@@ -878,7 +891,7 @@ __device__ __forceinline__ int drain_queue_body(const FrameDev* F, int pass, int
     float4 pj = __ldg(F->X + j0 + jl);
     FastParams P;
     load_fast_params(*F, pass, P);
-    int relp = provisional_rel<V, MULTI>(P, pi, pj, il & 31);
+    int relp = provisional_rel<V, MULTI, UNI>(P, pi, pj, il & 31, ti, sj);
     int relx = deferred_bin<V>(*F, i0 + il, j0 + jl, pi, pj, nexact) - P.lo;
     if (relx != relp) {
       atomicAdd(sh + relp, 0xFFFFFFFFu);  // relp lies in the histogram or its guard words
@@ -903,11 +916,11 @@ __device__ __noinline__ int drain_queue_call(const FrameDev* F, int pass, int i0
 // The register allocation of the hot loop decides which form is faster
 // (measured): the periodic variants keep fewer live values across an inlined
 // drain than across a call, the no-box variant the other way round.
-template <int V, bool MULTI>
+template <int V, bool MULTI, bool UNI>
 __device__ __forceinline__ int drain_queue(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
-                                           uint32_t* sh, int lane) {
+                                           uint32_t* sh, int lane, float3 ti, float3 sj) {
   if constexpr (V == V_ORTHO || V == V_TRIC)
-    return drain_queue_body<V, MULTI>(F, pass, i0, j0, q, qcount, sh, lane);
+    return drain_queue_body<V, MULTI, UNI>(F, pass, i0, j0, q, qcount, sh, lane, ti, sj);
   else
     return drain_queue_call<V, MULTI>(F, pass, i0, j0, q, qcount, sh, lane);
 }
@@ -921,6 +934,13 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
                                          float3 kt) {
   // each warp holds 32 * RI consecutive i particles: lane + 32 r of its run
   const int ib = (tid >> 5) * (32 * RI) + lane;
+  // orthorhombic tile images: the image is subtracted from the coordinates
+  // (k = -1: L from the i's, k = +1: L from the j's; exact, see tile_image)
+  float3 ti = make_float3(0.f, 0.f, 0.f), sj = make_float3(0.f, 0.f, 0.f);
+  if (V == V_ORTHO && UNI) {
+    ti = make_float3(kt.x < 0.f ? P.b[0] : 0.f, kt.y < 0.f ? P.b[4] : 0.f, kt.z < 0.f ? P.b[8] : 0.f);
+    sj = make_float3(kt.x > 0.f ? P.b[0] : 0.f, kt.y > 0.f ? P.b[4] : 0.f, kt.z > 0.f ? P.b[8] : 0.f);
+  }
   float2 xi[RI], yi[RI], zi[RI];  // i coordinates broadcast to both halves
 #pragma unroll
   for (int r = 0; r < RI; ++r) {
@@ -929,6 +949,11 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
     if (li < it.ni) {
       float4 p = __ldg(F->X + it.i0 + li);
       x = p.x; y = p.y; z = p.z;
+      if (V == V_ORTHO && UNI) {
+        x = __fsub_rn(x, ti.x);
+        y = __fsub_rn(y, ti.y);
+        z = __fsub_rn(z, ti.z);
+      }
     }
     xi[r] = bc2(-x); yi[r] = bc2(-y); zi[r] = bc2(-z);  // negated: d = xj + (-xi)
   }
@@ -947,8 +972,13 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
 #pragma unroll
     for (int u = 0; u < kJU; u += 2) {
       const float4 A = sjA[(jj0 + u) >> 1];
-      const float2 Z = sjZ[(jj0 + u) >> 1];
-      const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+      float2 Z = sjZ[(jj0 + u) >> 1];
+      float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+      if (V == V_ORTHO && UNI) {
+        xj = add2(xj, bc2(-sj.x));
+        yj = add2(yj, bc2(-sj.y));
+        Z = add2(Z, bc2(-sj.z));
+      }
 #pragma unroll
       for (int r = 0; r < RI; ++r) {
         float2 dx = add2(xj, xi[r]);
@@ -980,13 +1010,13 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
       ndeferred += added;
       if (qcount >= 32) {
         __syncwarp();
-        qcount = drain_queue<V, MULTI>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane);
+        qcount = drain_queue<V, MULTI, UNI>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane, ti, sj);
       }
       bal = __ballot_sync(kFull, dmask != 0u);
     }
   }
   __syncwarp();
-  if (qcount > 0) drain_queue<V, MULTI>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane);
+  if (qcount > 0) drain_queue<V, MULTI, UNI>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane, ti, sj);
   __syncwarp();
 }
 
@@ -1030,10 +1060,18 @@ __device__ float4 tile_image(const FrameDev& F, const float* imin, const float* 
   }
   const float* b = F.Bf;
   if (V == V_ORTHO) {
+    // and each image must be exactly subtractable from the coordinates it moves:
+    // k = +1 from the j's, k = -1 from the i's, which Sterbenz's lemma grants when
+    // they lie in [L/2, 2L]
     float k[3];
     for (int c = 0; c < 3; ++c) {
       k[c] = nint_scaled(lo[c], F.invf[c]);
       if (!(nint_scaled(hi[c], F.invf[c]) == k[c])) return make_float4(0.f, 0.f, 0.f, 0.f);
+      const float L = b[4 * c];
+      bool ok = (k[c] == 0.0f) ||
+                (k[c] == 1.0f && jmin[c] >= 0.5f * L && jmax[c] <= 2.0f * L) ||
+                (k[c] == -1.0f && imin[c] >= 0.5f * L && imax[c] <= 2.0f * L);
+      if (!ok) return make_float4(0.f, 0.f, 0.f, 0.f);
     }
     return make_float4(k[0], k[1], k[2], 1.0f);
   } else {
