@@ -343,11 +343,13 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   // binary64 input: the float32 path starts from coordinates rounded to float32,
   // each within half an ulp of the largest magnitude on its axis
   double conv[3] = {0, 0, 0};
+  double Xm[3] = {0, 0, 0};  // largest coordinate magnitude per axis
   if (F.n > 0 && F.cmin[0] <= F.cmax[0]) {
     for (int c = 0; c < 3; ++c) {
       double lo = float_of_ord(F.cmin[c]), hi = float_of_ord(F.cmax[c]);
       R[c] = hi - lo;
-      if (F.X64) conv[c] = 2.0 * half_ulp_below(fmax(fabs(lo), fabs(hi)));
+      Xm[c] = fmax(fabs(lo), fabs(hi));
+      if (F.X64) conv[c] = 2.0 * half_ulp_below(Xm[c]);
     }
   }
   double S = (double)F.nbins / F.r_max;
@@ -397,6 +399,14 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
            conv[0];
     a[1] = half_ulp_below(R[1]) + half_ulp_below(D1y) + Kz * dB[5] + Ky * dB[4] + conv[1];
     a[2] = half_ulp_below(R[2]) + Kz * dB[8] + conv[2];
+    // tile images (|k| <= 1): the i's move by B k, summed in float32 (two
+    // roundings below half an ulp of the row sum) from exact products of the
+    // float32 entries (|Bf - B| per entry), then rounded once (half an ulp of the
+    // largest |x + B k|); d = xj - x'i itself rounds relative to |d| (alpha)
+    const double Sx = ax + fabs(bx) + fabs(cx), Sy = by + fabs(cy), Sz = cz;
+    a[0] = fmax(a[0], half_ulp_below(Xm[0] + Sx) + 2.0 * half_ulp_below(Sx) + dB[0] + dB[1] + dB[2] + conv[0]);
+    a[1] = fmax(a[1], half_ulp_below(Xm[1] + Sy) + half_ulp_below(Sy) + dB[4] + dB[5] + conv[1]);
+    a[2] = fmax(a[2], half_ulp_below(Xm[2] + Sz) + dB[8] + conv[2]);
     I[0] = D2x + Kx * ax;
     I[1] = D1y + Ky * by;
     I[2] = R[2] + Kz * cz;
@@ -487,6 +497,15 @@ struct FastParams {
   float amb_thr;        // search variant: 0.5 - eps_s
 };
 
+// Triclinic tile image: the vector B k (|k| <= 1 per component, so each product
+// is exact) in a fixed operation order, negated: the i's of the tile move by it.
+__device__ __forceinline__ float3 tric_image_shift(const FastParams& P, float3 k) {
+  const float sx = __fadd_rn(__fadd_rn(__fmul_rn(k.x, P.b[0]), __fmul_rn(k.y, P.b[1])), __fmul_rn(k.z, P.b[2]));
+  const float sy = __fadd_rn(__fmul_rn(k.y, P.b[4]), __fmul_rn(k.z, P.b[5]));
+  const float sz = __fmul_rn(k.z, P.b[8]);
+  return make_float3(-sx, -sy, -sz);
+}
+
 // Guard words on each side of a shared-memory histogram copy: the increments
 // of pairs outside [lo, hi) land there (see count_or_defer).
 constexpr int kGuard = 36;
@@ -561,17 +580,16 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 
 // float32 |d'|^2 of two pairs after the minimum image of the variant; each
 // component is rounded exactly as the scalar sequence of wrap_r2.  UNI: the
-// tile pair's nearest-image integers are known to be kt for every pair (see
-// tile_image).  Triclinic: only the subtractions of the image are left, with
-// the same operands in the same order, so the result is bit for bit the one of
-// the per-pair path.  Orthorhombic: the caller has already subtracted the
-// images from the coordinates themselves (exactly), so d is the image vector
-// rounded once.
+// tile pair's nearest-image integers are known for every pair (see tile_image)
+// and the caller has already subtracted the image from the coordinates, so d
+// is the image vector itself.
 template <int V, bool UNI = false>
 __device__ __forceinline__ float2 wrap_r2_2(float2 dx, float2 dy, float2 dz, const FastParams& P, bool& amb_a,
                                             bool& amb_b, float3 kt = make_float3(0.f, 0.f, 0.f)) {
   const float2 M = bc2(kMagicRound), NM = bc2(-kMagicRound);
-  if (V == V_ORTHO && !UNI) {  // (UNI: the coordinates were shifted by the images already)
+  if (UNI && (V == V_ORTHO || V == V_TRIC)) {
+    // the coordinates were shifted by the images already
+  } else if (V == V_ORTHO) {
     float2 kx = add2(fma2(dx, bc2(P.inv[0]), M), NM);
     float2 ky = add2(fma2(dy, bc2(P.inv[1]), M), NM);
     float2 kz = add2(fma2(dz, bc2(P.inv[2]), M), NM);
@@ -579,14 +597,14 @@ __device__ __forceinline__ float2 wrap_r2_2(float2 dx, float2 dy, float2 dz, con
     dy = fma2(ky, bc2(-P.b[4]), dy);
     dz = fma2(kz, bc2(-P.b[8]), dz);
   } else if (V == V_TRIC) {
-    float2 kz = UNI ? bc2(kt.z) : add2(fma2(dz, bc2(P.inv[2]), M), NM);
+    float2 kz = add2(fma2(dz, bc2(P.inv[2]), M), NM);
     dx = fma2(kz, bc2(-P.b[2]), dx);
     dy = fma2(kz, bc2(-P.b[5]), dy);
     dz = fma2(kz, bc2(-P.b[8]), dz);
-    float2 ky = UNI ? bc2(kt.y) : add2(fma2(dy, bc2(P.inv[1]), M), NM);
+    float2 ky = add2(fma2(dy, bc2(P.inv[1]), M), NM);
     dx = fma2(ky, bc2(-P.b[1]), dx);
     dy = fma2(ky, bc2(-P.b[4]), dy);
-    float2 kx = UNI ? bc2(kt.x) : add2(fma2(dx, bc2(P.inv[0]), M), NM);
+    float2 kx = add2(fma2(dx, bc2(P.inv[0]), M), NM);
     dx = fma2(kx, bc2(-P.b[0]), dx);
   } else if (V == V_TRIC_SEARCH) {
     return make_float2(wrap_r2<V>(dx.x, dy.x, dz.x, P, amb_a), wrap_r2<V>(dx.y, dy.y, dz.y, P, amb_b));
@@ -677,7 +695,7 @@ __device__ __forceinline__ int provisional_rel(const FastParams& P, float4 pi, f
                                                float3 sj = make_float3(0.f, 0.f, 0.f)) {
   bool amb = false;
   float r2;
-  if (V == V_ORTHO && UNI) {  // the coordinates shifted by the tile's images (exact), no wrap
+  if ((V == V_ORTHO || V == V_TRIC) && UNI) {  // the coordinates shifted by the tile's images, no wrap
     const float dx = __fsub_rn(__fsub_rn(pj.x, sj.x), __fsub_rn(pi.x, ti.x));
     const float dy = __fsub_rn(__fsub_rn(pj.y, sj.y), __fsub_rn(pi.y, ti.y));
     const float dz = __fsub_rn(__fsub_rn(pj.z, sj.z), __fsub_rn(pi.z, ti.z));
@@ -934,12 +952,16 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
                                          float3 kt) {
   // each warp holds 32 * RI consecutive i particles: lane + 32 r of its run
   const int ib = (tid >> 5) * (32 * RI) + lane;
-  // orthorhombic tile images: the image is subtracted from the coordinates
-  // (k = -1: L from the i's, k = +1: L from the j's; exact, see tile_image)
+  // tile images: the image is subtracted from the coordinates, ti from the i's and
+  // sj from the j's.  Orthorhombic (exact, see tile_image): k = -1 takes L from
+  // the i's, k = +1 from the j's.  Triclinic: the i's move by the image vector
+  // B k, rounded once (|k| <= 1, so the products are exact).
   float3 ti = make_float3(0.f, 0.f, 0.f), sj = make_float3(0.f, 0.f, 0.f);
   if (V == V_ORTHO && UNI) {
     ti = make_float3(kt.x < 0.f ? P.b[0] : 0.f, kt.y < 0.f ? P.b[4] : 0.f, kt.z < 0.f ? P.b[8] : 0.f);
     sj = make_float3(kt.x > 0.f ? P.b[0] : 0.f, kt.y > 0.f ? P.b[4] : 0.f, kt.z > 0.f ? P.b[8] : 0.f);
+  } else if (V == V_TRIC && UNI) {
+    ti = tric_image_shift(P, kt);
   }
   float2 xi[RI], yi[RI], zi[RI];  // i coordinates broadcast to both halves
 #pragma unroll
@@ -949,7 +971,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
     if (li < it.ni) {
       float4 p = __ldg(F->X + it.i0 + li);
       x = p.x; y = p.y; z = p.z;
-      if (V == V_ORTHO && UNI) {
+      if ((V == V_ORTHO || V == V_TRIC) && UNI) {
         x = __fsub_rn(x, ti.x);
         y = __fsub_rn(y, ti.y);
         z = __fsub_rn(z, ti.z);
@@ -1086,6 +1108,7 @@ __device__ float4 tile_image(const FrameDev& F, const float* imin, const float* 
     xhi = __fmaf_rn(ky, -b[1], xhi);
     const float kx = nint_scaled(xlo, F.invf[0]);
     if (!(nint_scaled(xhi, F.invf[0]) == kx)) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (fabsf(kx) > 1.0f || fabsf(ky) > 1.0f || fabsf(kz) > 1.0f) return make_float4(0.f, 0.f, 0.f, 0.f);
     return make_float4(kx, ky, kz, 1.0f);
   }
 }
