@@ -945,11 +945,12 @@ __device__ __forceinline__ int drain_queue(const FrameDev* F, int pass, int i0, 
 
 // j tile in shared memory as pairs of particles: A[p] = {x_2p, x_2p+1, y_2p, y_2p+1},
 // Z[p] = {z_2p, z_2p+1}, so one LDS.128 + one LDS.64 feed two j particles.
+// j particles [jb, je) of the staged tile (jb a multiple of kSubJ).
 template <int V, bool MASKED, bool MULTI, int RI, bool UNI>
 __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
                                          const float4* __restrict__ sjA, const float2* __restrict__ sjZ,
                                          uint32_t* sh, uint32_t* q, int tid, int lane, unsigned& ndeferred,
-                                         float3 kt) {
+                                         float3 kt, int jb, int je) {
   // each warp holds 32 * RI consecutive i particles: lane + 32 r of its run
   const int ib = (tid >> 5) * (32 * RI) + lane;
   // tile images: the image is subtracted from the coordinates, ti from the i's and
@@ -986,9 +987,9 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
   const float chi = (float)(P.hi + 1 + lane);
   const float clo = (float)(P.lo - lane);
   constexpr int kJU = ju_of<RI>();
-  const int nj4 = (it.nj + kJU - 1) & ~(kJU - 1);  // the j tile is padded with NaN particles
+  const int nj4 = (je + kJU - 1) & ~(kJU - 1);  // the j tile is padded with NaN particles
   int qcount = 0;
-  for (int jj0 = 0; jj0 < nj4; jj0 += kJU) {
+  for (int jj0 = jb; jj0 < nj4; jj0 += kJU) {
     uint32_t dmask = 0u;
     // (u, r) are compile-time constants after unrolling: they name the mask bit
 #pragma unroll
@@ -1046,22 +1047,31 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
 // descriptor) so that only the fields of this variant are live in the loop.
 // MULTI: some sweep of the launch starts above bin 0, so the root is also
 // clamped from below (valid for every sweep, a separate kernel for registers).
+// For the periodic variants the j tile is taken in sub-chunks of kSubJ
+// particles; img[c] is this warp's tile image for sub-chunk c (w = 0: none).
 template <int V, bool MULTI, int RI>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
-                         uint32_t* q, int tid, int lane, unsigned& ndeferred, float4 img) {
+                         uint32_t* q, int tid, int lane, unsigned& ndeferred, const float4* img) {
   FastParams P;
   load_fast_params(*F, it.pass, P);
-  const float3 kt = make_float3(img.x, img.y, img.z);
   if (V == V_ORTHO || V == V_TRIC) {
-    if (img.w != 0.0f) {
-      if (it.masked) run_tile<V, true, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
-      else run_tile<V, false, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
-      return;
+    for (int c = 0; c * kSubJ < it.nj; ++c) {
+      const int jb = c * kSubJ, je = min(it.nj, jb + kSubJ);
+      const float4 im = img[c];
+      const float3 kt = make_float3(im.x, im.y, im.z);
+      if (im.w != 0.0f) {
+        if (it.masked) run_tile<V, true, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
+        else run_tile<V, false, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
+      } else {
+        if (it.masked) run_tile<V, true, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
+        else run_tile<V, false, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
+      }
     }
+    return;
   }
-
-  if (it.masked) run_tile<V, true, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
-  else run_tile<V, false, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt);
+  const float3 k0 = make_float3(0.f, 0.f, 0.f);
+  if (it.masked) run_tile<V, true, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+  else run_tile<V, false, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
 }
 
 // The nearest-image integers of a tile pair, when the float32 per-pair path
@@ -1215,7 +1225,10 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
   uint32_t* sq = reinterpret_cast<uint32_t*>(sjZ + kTile / 2);
   __shared__ ItemDesc s_it;
   constexpr bool kTileImage = (V == V_ORTHO || V == V_TRIC);
-  __shared__ float s_bnd[kTileImage ? BLOCK / 32 : 1][6];  // per warp: j min xyz, j max xyz
+  // per j sub-chunk: j min xyz, j max xyz; per warp and sub-chunk: the tile image
+  __shared__ float s_bnd[kTileImage ? kTile / kSubJ : 1][6];
+  __shared__ float4 s_img[kTileImage ? BLOCK / 32 : 1][kTileImage ? kTile / kSubJ : 1];
+  static_assert(!kTileImage || BLOCK / 32 >= kTile / kSubJ, "one warp per j sub-chunk");
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* q = sq + warp * kQueueCap;
@@ -1266,59 +1279,72 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
         since = 0;
       }
       since += pairs;
-      // stage the j tile in pair layout, padded with NaN particles to a multiple of kJUMax;
-      // for the tile image, the coordinate bounds of the j and i tiles
-      float bnd[12];  // i min xyz, i max xyz, j min xyz, j max xyz
-      for (int c = 0; c < 12; ++c) bnd[c] = ((c / 3) & 1) ? -INFINITY : INFINITY;
+      // stage the j tile in pair layout, padded with NaN particles to a multiple of kJUMax
       const int nj4 = (it.nj + kJUMax - 1) & ~(kJUMax - 1);
       for (int k = tid; k < nj4; k += BLOCK) {
-        float4 v;
-        if (k < it.nj) {
-          v = __ldg(F.X + it.j0 + k);
-          if (kTileImage) {
-            bnd[6] = fminf(bnd[6], v.x); bnd[7] = fminf(bnd[7], v.y); bnd[8] = fminf(bnd[8], v.z);
-            bnd[9] = fmaxf(bnd[9], v.x); bnd[10] = fmaxf(bnd[10], v.y); bnd[11] = fmaxf(bnd[11], v.z);
-          }
-        } else {
-          v = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff), __int_as_float(0x7fffffff), 0.f);
-        }
+        float4 v = k < it.nj ? __ldg(F.X + it.j0 + k)
+                             : make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff),
+                                           __int_as_float(0x7fffffff), 0.f);
         float* a = reinterpret_cast<float*>(sjA + (k >> 1));
         a[k & 1] = v.x;
         a[2 + (k & 1)] = v.y;
         reinterpret_cast<float*>(sjZ + (k >> 1))[k & 1] = v.z;
       }
-      float4 img = make_float4(0.f, 0.f, 0.f, 0.f);
+      // tile images: the bounds of this warp's i run against those of each
+      // j sub-chunk of kSubJ particles (warp c reduces sub-chunk c)
+      float ib_[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
       if (kTileImage) {
-        // this warp's i run (the particles run_tile gives it) and the block's j tile
-        const int ib = warp * (32 * RI) + lane;
+        const int ib = warp * (32 * RI) + lane;  // this warp's i run (the particles run_tile gives it)
         for (int r = 0; r < RI; ++r) {
           const int li = ib + 32 * r;
           if (li < it.ni) {
             float4 v = __ldg(F.X + it.i0 + li);
-            bnd[0] = fminf(bnd[0], v.x); bnd[1] = fminf(bnd[1], v.y); bnd[2] = fminf(bnd[2], v.z);
-            bnd[3] = fmaxf(bnd[3], v.x); bnd[4] = fmaxf(bnd[4], v.y); bnd[5] = fmaxf(bnd[5], v.z);
+            ib_[0] = fminf(ib_[0], v.x); ib_[1] = fminf(ib_[1], v.y); ib_[2] = fminf(ib_[2], v.z);
+            ib_[3] = fmaxf(ib_[3], v.x); ib_[4] = fmaxf(ib_[4], v.y); ib_[5] = fmaxf(ib_[5], v.z);
           }
         }
         for (int o = 16; o > 0; o >>= 1)
-          for (int c = 0; c < 12; ++c) {
-            float other = __shfl_xor_sync(kFull, bnd[c], o);
-            bnd[c] = ((c / 3) & 1) ? fmaxf(bnd[c], other) : fminf(bnd[c], other);
+          for (int a = 0; a < 6; ++a) {
+            float other = __shfl_xor_sync(kFull, ib_[a], o);
+            ib_[a] = a < 3 ? fminf(ib_[a], other) : fmaxf(ib_[a], other);
           }
-        if (lane == 0)
-          for (int c = 6; c < 12; ++c) s_bnd[warp][c - 6] = bnd[c];
       }
       __syncthreads();
       if (kTileImage) {
-        for (int w = 0; w < BLOCK / 32; ++w)
-          for (int c = 6; c < 12; ++c)
-            bnd[c] = ((c / 3) & 1) ? fmaxf(bnd[c], s_bnd[w][c - 6]) : fminf(bnd[c], s_bnd[w][c - 6]);
+        if (warp * kSubJ < it.nj) {
+          float jm[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+          const int ke = min(it.nj, (warp + 1) * kSubJ);
+          for (int k = warp * kSubJ + lane; k < ke; k += 32) {
+            const float* a = reinterpret_cast<const float*>(sjA + (k >> 1));
+            const float x = a[k & 1], y = a[2 + (k & 1)];
+            const float z = reinterpret_cast<const float*>(sjZ + (k >> 1))[k & 1];
+            jm[0] = fminf(jm[0], x); jm[1] = fminf(jm[1], y); jm[2] = fminf(jm[2], z);
+            jm[3] = fmaxf(jm[3], x); jm[4] = fmaxf(jm[4], y); jm[5] = fmaxf(jm[5], z);
+          }
+          for (int o = 16; o > 0; o >>= 1)
+            for (int a = 0; a < 6; ++a) {
+              float other = __shfl_xor_sync(kFull, jm[a], o);
+              jm[a] = a < 3 ? fminf(jm[a], other) : fmaxf(jm[a], other);
+            }
+          if (lane == 0)
+            for (int a = 0; a < 6; ++a) s_bnd[warp][a] = jm[a];
+        }
+        __syncthreads();
         const int ni_w = min(32 * RI, it.ni - warp * 32 * RI);  // i particles of this warp
-        if (ni_w > 0) img = tile_image<V>(F, bnd, bnd + 3, bnd + 6, bnd + 9);
-        if (lane == 0 && img.w != 0.0f)
-          atomicAdd(&it.fd->uniform_pairs, (unsigned long long)ni_w * (unsigned long long)it.nj);
+        for (int c = 0; c * kSubJ < it.nj; ++c) {
+          float4 img = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (ni_w > 0) img = tile_image<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3);
+          if (lane == 0) {
+            s_img[warp][c] = img;
+            if (img.w != 0.0f)
+              atomicAdd(&it.fd->uniform_pairs,
+                        (unsigned long long)ni_w * (unsigned long long)(min(it.nj, (c + 1) * kSubJ) - c * kSubJ));
+          }
+        }
+        __syncwarp();
       }
       unsigned ndef = 0;
-      run_item<V, MULTI, RI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, img);
+      run_item<V, MULTI, RI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, s_img[kTileImage ? warp : 0]);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();
