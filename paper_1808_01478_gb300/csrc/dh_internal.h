@@ -16,7 +16,7 @@ enum Variant : int32_t {
 };
 
 constexpr int kTile = 1024;          // i particles per work item (and the longest j tile)
-constexpr int kSubJ = 256;           // j sub-chunk with its own tile image per warp
+constexpr int kSubJ = 128;           // j sub-chunk with its own tile image per warp
 // Pair-kernel blocks: 256 threads with 4 i particles each, 512 with 2, or 1024 with 1.
 constexpr int kBlockSmall = 256;
 constexpr int kBlockLarge = 512;
