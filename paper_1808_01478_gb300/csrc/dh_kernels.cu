@@ -1204,11 +1204,13 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
 
 // One instance per minimum-image variant V (every segment of the launch has a
 // frame of that variant) and per MULTI.
-// Register budgets: 256-thread blocks keep three (two for the search variant)
-// blocks per SM; 512-thread blocks, meant for wide histograms, one.
+// Register budgets: 256-thread blocks keep three blocks per SM (80 registers)
+// for the no-box and orthorhombic variants, two (128 registers: the triclinic
+// loop spills at 80, which costs more than the third block gains); 512- and
+// 1024-thread blocks, meant for wide histograms, one.
 template <int V, int RI>
 constexpr int min_blocks_per_sm() {
-  return RI < 4 ? 1 : ((V == V_NONE || V == V_ORTHO || V == V_TRIC) ? 3 : 2);
+  return RI < 4 ? 1 : ((V == V_NONE || V == V_ORTHO) ? 3 : 2);
 }
 
 template <int V, bool MULTI, int RI>
