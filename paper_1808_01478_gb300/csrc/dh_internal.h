@@ -52,11 +52,12 @@ struct FrameDev {
   int32_t cmax[3];
   int32_t bad;       // a non-finite coordinate was seen
   int32_t all_defer; // float32 decisions are not safe for this frame: every pair is deferred
-  float qb1, qb0;    // near-edge test: |n^2 - q| <= qb1*q + qb0 (no box) or qb1*s + qb0 (q = t^2, s ~ t)
+  float beta_u;      // beta of tiles that take a uniform image (orthorhombic, triclinic)
+  float tie_m[3];    // orthorhombic: margin of the uniform-image test (0: not needed)
   float mid2, mid1;  // double-float tier: |r2 - T[n]| <= mid2*r2 + mid1*s decides nothing
   float tie_eps;     // orthorhombic: | |d'_c| - L_c/2 | <= tie_eps is re-decided in binary64
   float delta;       // float32 window half-width in bin units at t = nbins (reported)
-  float alpha_t, beta_t;  // the t-space bound alpha*t + beta behind the q-space test
+  float alpha_t, beta_t;  // the t-space bound alpha*t + beta behind the q-space test (per-pair images)
   float eps_s;       // search variant: fractional-coordinate ambiguity margin
   unsigned long long deferred;  // statistics: pairs queued for the double-float tier
   unsigned long long exact;     // pairs that also needed the binary64 replay

@@ -326,8 +326,12 @@ __device__ inline double half_ulp_below(double D) {
 //          then have |d'_c| within eta L of L_c/2), S*2 eta L for as many
 //          components as can reach L_c/2 below r_max (1 + 2/nbins).
 //  q-space test: with n the integer nearest to sqrt(q32), floor(t) is decided
-//  when |q32 - n^2| > (alpha t' + beta)(2 t' + 1) = 2 alpha q + (alpha + 2 beta) t' + beta,
-//  with t' <= s (1 + 2^-18) for s = sqrt.approx(q32).
+//  when |q32 - n^2| > (alpha t' + beta)(2 t' + 1) = 2 alpha q + (alpha + 2 beta) t' + beta;
+//  load_fast_params turns it into one FMA in q (t' <= (q/tau + tau)/2 for any
+//  tau > 0).
+//  Tiles with a uniform image (tile_image) take beta_u: the same with their
+//  own absolute errors (the image subtracted exactly, orthorhombic; the i's
+//  moved by a rounded B k, triclinic).
 //  double-float tier: |r2_df - r2_64| <= 2^-38 r2 + 2 r |a_mid| with |a_mid|
 //  from 2^-40 times the wrap magnitudes (binary64 oracle rounding and the
 //  float pair arithmetic, both far below it).
@@ -357,6 +361,8 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   double a[3] = {0, 0, 0};
   double I[3] = {R[0], R[1], R[2]};  // magnitudes of the wrap intermediates (for the double-float tier)
   double tie = 0.0, tie_eps = 0.0;
+  double au[3] = {0, 0, 0};  // absolute error of d'_c in tiles with a uniform image
+  for (int c = 0; c < 3; ++c) F.tie_m[c] = 0.0f;
   int all_defer = 0;
   float eps_s = 0.0f;
   const double* B = F.B;
@@ -386,6 +392,13 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
       tie = S * (m >= 3 ? t3 : (m == 2 ? fmin(t3, 1.4142135623730951 * t1) : t1)) * 1.01;
     }
     tie_eps = 2.0 * fmax(tie_c[0], fmax(tie_c[1], tie_c[2])) + 1e-12 * Lmin;
+    // uniform-image tiles: the image is subtracted exactly (|k| <= 1), so d'_c
+    // errs only by the float32 box entry; the tie term is not needed where the
+    // tile's difference range, widened by tie_m = 4 eta L, keeps one image
+    for (int c = 0; c < 3; ++c) {
+      au[c] = dB[4 * c] + conv[c];
+      F.tie_m[c] = tie > 0.0 ? (float)(2.0 * tie_c[c]) : 0.0f;
+    }
   } else if (F.variant == V_TRIC) {
     // sequential wrap along c, then b, then a (Eq. 5 below half the plane spacing);
     // D are the largest magnitudes of the intermediates, K the largest |k|
@@ -404,17 +417,17 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     // float32 entries (|Bf - B| per entry), then rounded once (half an ulp of the
     // largest |x + B k|); d = xj - x'i itself rounds relative to |d| (alpha)
     const double Sx = ax + fabs(bx) + fabs(cx), Sy = by + fabs(cy), Sz = cz;
-    a[0] = fmax(a[0], half_ulp_below(Xm[0] + Sx) + 2.0 * half_ulp_below(Sx) + dB[0] + dB[1] + dB[2] + conv[0]);
-    a[1] = fmax(a[1], half_ulp_below(Xm[1] + Sy) + half_ulp_below(Sy) + dB[4] + dB[5] + conv[1]);
-    a[2] = fmax(a[2], half_ulp_below(Xm[2] + Sz) + dB[8] + conv[2]);
+    au[0] = half_ulp_below(Xm[0] + Sx) + 2.0 * half_ulp_below(Sx) + dB[0] + dB[1] + dB[2] + conv[0];
+    au[1] = half_ulp_below(Xm[1] + Sy) + half_ulp_below(Sy) + dB[4] + dB[5] + conv[1];
+    au[2] = half_ulp_below(Xm[2] + Sz) + dB[8] + conv[2];
     I[0] = D2x + Kx * ax;
     I[1] = D1y + Ky * by;
     I[2] = R[2] + Kz * cz;
     // the three nearest-integer decisions must be exact for every pair closer
     // than r_max: their float32 errors must stay below a quarter of the margin
     double ez = (2.0 * u * R[2] + conv[2] + R[2] * fabs((double)F.invf[2] * cz - 1.0)) / cz;
-    double ey = (2.0 * (a[1] + u * D1y) + D1y * fabs((double)F.invf[1] * by - 1.0)) / by;
-    double ex = (2.0 * (a[0] + u * D2x) + D2x * fabs((double)F.invf[0] * ax - 1.0)) / ax;
+    double ey = (2.0 * (fmax(a[1], au[1]) + u * D1y) + D1y * fabs((double)F.invf[1] * by - 1.0)) / by;
+    double ex = (2.0 * (fmax(a[0], au[0]) + u * D2x) + D2x * fabs((double)F.invf[0] * ax - 1.0)) / ax;
     double emax = fmax(ex, fmax(ey, ez));
     if (!(emax < 0.25 * (double)F.margin) || D2x / ax > 1048576.0 || D1y / by > 1048576.0 ||
         R[2] / cz > 1048576.0)
@@ -443,26 +456,14 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   }
   if (F.variant == V_NONE)
     for (int c = 0; c < 3; ++c) a[c] = conv[c];  // d = xj - xi itself rounds relative to |d| (alpha)
+  const double abs_u = sqrt(au[0] * au[0] + au[1] * au[1] + au[2] * au[2]);
   double beta = S * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * (1.0 + 64.0 * u) + tie + 1.0 / 268435456.0;
+  double beta_u = (F.variant == V_ORTHO || F.variant == V_TRIC) ? S * abs_u * (1.0 + 64.0 * u) + 1.0 / 268435456.0
+                                                                 : beta;
   alpha = alpha * (1.0 + 1.0 / 1024.0) + 1e-12;
   double delta = alpha * ((double)F.nbins + 1.0) + beta;
-  if (!(delta < 0.25)) all_defer = 1;
-  const double slack = 1.0 + 1.0 / 1024.0;
-  // One-FMA forms of the q-space bound 2 alpha q + (alpha + 2 beta) t' + beta:
-  //  no box (float32 input only, so beta is tiny): t' <= (q + 1)/2 gives
-  //  (2.5 alpha + beta) q + (alpha/2 + 2 beta);
-  //  otherwise: for t' <= nbins + 2 (pairs beyond are never counted whatever the
-  //  decision, thanks to the clamp of the root), 2 alpha q <= 2 alpha (nbins + 2) t'
-  //  and t' <= s (1 + 2^-18).
-  if (all_defer) {
-    F.qb1 = F.qb0 = 1e30f;
-  } else if (F.variant == V_NONE) {
-    F.qb1 = (float)((2.5 * alpha + beta) * slack);
-    F.qb0 = (float)((0.5 * alpha + 2.0 * beta) * slack);
-  } else {
-    F.qb1 = (float)((2.0 * alpha * ((double)F.nbins + 2.0) + alpha + 2.0 * beta) * (1.0 + 1.0 / 262144.0) * slack);
-    F.qb0 = (float)(beta * slack);
-  }
+  if (!(delta < 0.25) || !(alpha * ((double)F.nbins + 1.0) + beta_u < 0.25)) all_defer = 1;
+  // the q-space test itself is formed per sweep (load_fast_params)
   double Imax = fmax(I[0], fmax(I[1], I[2]));
   double amid = 1.7320508075688772 * (R[0] + R[1] + R[2] + 4.0 * Imax) / 1099511627776.0;  // 2^-40
   if (F.X64)  // binary64 input: the split coordinates (2^-48 of the magnitude each) and d rounded in binary64
@@ -474,6 +475,7 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   F.delta = (float)fmin(delta, 1.0);
   F.alpha_t = (float)alpha;
   F.beta_t = (float)beta;
+  F.beta_u = (float)beta_u;
   F.eps_s = eps_s;
   F.all_defer = all_defer;
 }
@@ -488,7 +490,7 @@ constexpr int kJUMax = 16;
 
 struct FastParams {
   float S2;
-  float qb1, qb0;       // near-edge bound |n^2 - q| <= qb1*(q or s) + qb0 (q for V_NONE, s otherwise)
+  float qb1, qb0;       // near-edge bound |n^2 - q| <= qb1 q + qb0 (set_bound)
   int32_t kb1;          // bits(kMagicRound) + lo + 1
   uint32_t width;       // hi - lo
   int32_t lo, hi;       // bins [lo, hi) of this sweep
@@ -496,6 +498,26 @@ struct FastParams {
   float inv[3];
   float amb_thr;        // search variant: 0.5 - eps_s
 };
+
+// The q-space test of the sweep [P.lo, P.hi) as one FMA in q.  The bound
+// 2 alpha q + gamma t' + beta (gamma = alpha + 2 beta; beta_u for a tile with a
+// uniform image) with t' <= (q/tau + tau)/2, true for any tau > 0, becomes
+// (2 alpha + gamma/(2 tau)) q + (gamma tau/2 + beta), exact at t' = tau;
+// tau = (hi + 2)/sqrt(2) (at least lo + 1) minimises the mean window over the
+// sweep for pair counts growing like t^2.  The float32 evaluation (a few
+// roundings, and alpha_t, beta_t rounded) is covered by the factor 1 + 2^-10.
+__device__ __forceinline__ void set_bound(const FrameDev& F, FastParams& P, bool uniform) {
+  if (F.all_defer) {
+    P.qb1 = P.qb0 = 1e30f;
+    return;
+  }
+  const float tau = fmaxf((float)(P.hi + 2) * 0.70710678f, (float)(P.lo + 1));
+  const float slack = 1.0f + 1.0f / 1024.0f;
+  const float beta = uniform ? F.beta_u : F.beta_t;
+  const float g = F.alpha_t + 2.0f * beta;
+  P.qb1 = (2.0f * F.alpha_t + g / (2.0f * tau)) * slack;
+  P.qb0 = (0.5f * g * tau + beta) * slack;
+}
 
 // Triclinic tile image: the vector B k (|k| <= 1 per component, so each product
 // is exact) in a fixed operation order, negated: the i's of the tile move by it.
@@ -666,7 +688,7 @@ __device__ __forceinline__ void decide_arith2(float2 dx, float2 dy, float2 dz, c
   sm = add2(sc, bc2(kMagicRound));
   float2 n = add2(sm, bc2(-kMagicRound));
   e = fma2(n, n, nq);  // n^2 - q
-  bound = (V == V_NONE) ? fma2(nq, bc2(-P.qb1), bc2(P.qb0)) : fma2(sq, bc2(P.qb1), bc2(P.qb0));
+  bound = fma2(nq, bc2(-P.qb1), bc2(P.qb0));
   if (V == V_TRIC_SEARCH) {
     if (amb_a) bound.x = INFINITY;
     if (amb_b) bound.y = INFINITY;
@@ -1059,6 +1081,7 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
       const int jb = c * kSubJ, je = min(it.nj, jb + kSubJ);
       const float4 im = img[c];
       const float3 kt = make_float3(im.x, im.y, im.z);
+      set_bound(*F, P, im.w != 0.0f);
       if (im.w != 0.0f) {
         if (it.masked) run_tile<V, true, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
         else run_tile<V, false, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
@@ -1095,10 +1118,12 @@ __device__ float4 tile_image(const FrameDev& F, const float* imin, const float* 
     // and each image must be exactly subtractable from the coordinates it moves:
     // k = +1 from the j's, k = -1 from the i's, which Sterbenz's lemma grants when
     // they lie in [L/2, 2L]
+    // (widened by tie_m, so that no pair lies where float32 and binary64 may
+    // round d/L to different images: such tiles keep the per-pair path)
     float k[3];
     for (int c = 0; c < 3; ++c) {
-      k[c] = nint_scaled(lo[c], F.invf[c]);
-      if (!(nint_scaled(hi[c], F.invf[c]) == k[c])) return make_float4(0.f, 0.f, 0.f, 0.f);
+      k[c] = nint_scaled(__fsub_rn(lo[c], F.tie_m[c]), F.invf[c]);
+      if (!(nint_scaled(__fadd_rn(hi[c], F.tie_m[c]), F.invf[c]) == k[c])) return make_float4(0.f, 0.f, 0.f, 0.f);
       const float L = b[4 * c];
       bool ok = (k[c] == 0.0f) ||
                 (k[c] == 1.0f && jmin[c] >= 0.5f * L && jmax[c] <= 2.0f * L) ||
@@ -1189,8 +1214,6 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
   int lo_bin = pass * F.sweep_width;
   int hi_bin = min(F.nbins, lo_bin + F.sweep_width);
   P.S2 = F.S2;
-  P.qb1 = F.qb1;
-  P.qb0 = F.qb0;
   P.kb1 = __float_as_int(kMagicRound) + lo_bin + 1;
   P.width = (uint32_t)(hi_bin - lo_bin);
   P.lo = lo_bin;
@@ -1200,6 +1223,7 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) P.inv[c] = F.invf[c];
   P.amb_thr = 0.5f - F.eps_s;
+  set_bound(F, P, false);
 }
 
 // One instance per minimum-image variant V (every segment of the launch has a
