@@ -860,6 +860,15 @@ __device__ double exact_r2(const FrameDev& F, double3 pi, double3 pj) {
     dx = __dsub_rn(__dsub_rn(__dsub_rn(dx, __dmul_rn(ax, kx)), __dmul_rn(bx, ky)), __dmul_rn(cx, kz));
     dy = __dsub_rn(__dsub_rn(dy, __dmul_rn(by, ky)), __dmul_rn(cy, kz));
     dz = __dsub_rn(dz, __dmul_rn(cz, kz));
+    // Below half the plane spacing (V_TRIC: r_max <= (1 - 2^-8) h_min / 2) the
+    // shift m = 0 is the minimum of the 27 for every pair inside r_max: the
+    // sequential rounding is Babai's nearest plane in the upper-triangular
+    // basis, exact for vectors shorter than half its smallest Gram-Schmidt
+    // length (cz, by, ax >= h_min), and every other shift is longer than
+    // h_min - r_max > r_max.  Its value is the m = 0 term of the loop, bit for
+    // bit (adding the zero products changes nothing); a pair beyond r_max stays
+    // beyond it under any shift.  So the binary64 bin is the definition's.
+    if (V == V_TRIC) return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
     double best = INFINITY;
 #pragma unroll 1
     for (int mx = -1; mx <= 1; ++mx)
@@ -879,14 +888,17 @@ __device__ double exact_r2(const FrameDev& F, double3 pi, double3 pj) {
   return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
 }
 
-// Bin of a binary64 r^2 from the threshold table: the largest k with T[k] <= r2.
-__device__ __forceinline__ int bin_from_thresholds(const double* __restrict__ T, int nbins, double r2) {
-  int lo = 0, hi = nbins;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (__ldg(T + mid) <= r2) lo = mid; else hi = mid - 1;
-  }
-  return lo;
+// Bin of a binary64 r^2 from the threshold table: the largest k with T[k] <= r2
+// (T[0] = 0, T nondecreasing; 0 for NaN).  The float32 estimate S sqrt(r2) is
+// within a bin or two of it; the two walks make the result exact whatever the
+// estimate, with one or two dependent loads instead of a binary search's
+// log2(nbins).
+__device__ __forceinline__ int bin_from_thresholds(const double* __restrict__ T, float S, int nbins, double r2) {
+  if (!(r2 >= 0.0)) return 0;
+  int k = (int)fminf(__fmul_rn(sqrtf(__double2float_rn(r2)), S), (float)nbins);
+  while (k > 0 && __ldg(T + k) > r2) --k;
+  while (k < nbins && __ldg(T + k + 1) <= r2) ++k;
+  return k;
 }
 
 // The caller's coordinates of particle i of a frame, in binary64.
@@ -906,7 +918,7 @@ __device__ __forceinline__ int deferred_bin(const FrameDev& F, int i, int j, flo
                                             unsigned& nexact) {
   int k = mid_bin<V>(F, i, j, pi, pj);
   if (k < 0) {
-    k = bin_from_thresholds(F.T, F.nbins, exact_r2<V>(F, coords64(F, i), coords64(F, j)));
+    k = bin_from_thresholds(F.T, F.S, F.nbins, exact_r2<V>(F, coords64(F, i), coords64(F, j)));
     ++nexact;
   }
   return k;
@@ -1424,7 +1436,7 @@ __device__ void check_window_pair(const FrameDev& F, const FastParams& P, int i,
   bool amb0 = false, amb1 = false;
   float q = __fmul_rn(wrap_r2_2<V>(dx, dy, dz, P, amb0, amb1).x, P.S2);
   double r2 = exact_r2<V>(F, coords64(F, i), coords64(F, j));
-  int k64 = bin_from_thresholds(F.T, F.nbins, r2);
+  int k64 = bin_from_thresholds(F.T, F.S, F.nbins, r2);
   double t64 = __dmul_rn(__dsqrt_rn(r2), (double)F.nbins / F.r_max);
   if (t64 < (double)F.nbins + 1.0 && isfinite(q)) {
     double tq = __dsqrt_rn((double)q);
