@@ -911,6 +911,13 @@ __device__ __forceinline__ double3 coords64(const FrameDev& F, int i) {
   return make_double3((double)p.x, (double)p.y, (double)p.z);
 }
 
+// The binary64 replay of one pair (about one deferred pair in 10^4): out of
+// line, so that its code and registers stay out of the pair loop.
+template <int V>
+__device__ __noinline__ int exact_bin(const FrameDev& F, int i, int j) {
+  return bin_from_thresholds(F.T, F.S, F.nbins, exact_r2<V>(F, coords64(F, i), coords64(F, j)));
+}
+
 // Exact bin of one deferred pair (frame-local indices i, j; float32 copies pi,
 // pj): the double-float tier, then the binary64 replay.
 template <int V>
@@ -918,10 +925,16 @@ __device__ __forceinline__ int deferred_bin(const FrameDev& F, int i, int j, flo
                                             unsigned& nexact) {
   int k = mid_bin<V>(F, i, j, pi, pj);
   if (k < 0) {
-    k = bin_from_thresholds(F.T, F.S, F.nbins, exact_r2<V>(F, coords64(F, i), coords64(F, j)));
+    k = exact_bin<V>(F, i, j);
     ++nexact;
   }
   return k;
+}
+// The no-box variant's drain is faster with the double-float tier out of line too.
+template <int V>
+__device__ __noinline__ int deferred_bin_call(const FrameDev& F, int i, int j, float4 pi, float4 pj,
+                                              unsigned& nexact) {
+  return deferred_bin<V>(F, i, j, pi, pj, nexact);
 }
 
 __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P);
@@ -944,7 +957,8 @@ __device__ __forceinline__ int drain_queue_body(const FrameDev* F, int pass, int
     FastParams P;
     load_fast_params(*F, pass, P);
     int relp = provisional_rel<V, MULTI, UNI>(P, pi, pj, il & 31, ti, sj);
-    int relx = deferred_bin<V>(*F, i0 + il, j0 + jl, pi, pj, nexact) - P.lo;
+    int relx = (V == V_NONE ? deferred_bin_call<V>(*F, i0 + il, j0 + jl, pi, pj, nexact)
+                            : deferred_bin<V>(*F, i0 + il, j0 + jl, pi, pj, nexact)) - P.lo;
     if (relx != relp) {
       atomicAdd(sh + relp, 0xFFFFFFFFu);  // relp lies in the histogram or its guard words
       if ((uint32_t)relx < P.width) atomicAdd(sh + relx, 1u);
