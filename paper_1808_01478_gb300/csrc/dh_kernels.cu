@@ -412,14 +412,19 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
            conv[0];
     a[1] = half_ulp_below(R[1]) + half_ulp_below(D1y) + Kz * dB[5] + Ky * dB[4] + conv[1];
     a[2] = half_ulp_below(R[2]) + Kz * dB[8] + conv[2];
-    // tile images (|k| <= 1): the i's move by B k, summed in float32 (two
-    // roundings below half an ulp of the row sum) from exact products of the
-    // float32 entries (|Bf - B| per entry), then rounded once (half an ulp of the
+    // tile images (|k| <= 1): the i's move by B k, rounded to float32 from
+    // binary64 (half an ulp of the row sum), then added (half an ulp of the
     // largest |x + B k|); d = xj - x'i itself rounds relative to |d| (alpha)
     const double Sx = ax + fabs(bx) + fabs(cx), Sy = by + fabs(cy), Sz = cz;
-    au[0] = half_ulp_below(Xm[0] + Sx) + 2.0 * half_ulp_below(Sx) + dB[0] + dB[1] + dB[2] + conv[0];
-    au[1] = half_ulp_below(Xm[1] + Sy) + half_ulp_below(Sy) + dB[4] + dB[5] + conv[1];
-    au[2] = half_ulp_below(Xm[2] + Sz) + dB[8] + conv[2];
+    au[0] = half_ulp_below(Xm[0] + Sx) + half_ulp_below(Sx) + conv[0];
+    au[1] = half_ulp_below(Xm[1] + Sy) + half_ulp_below(Sy) + conv[1];
+    au[2] = half_ulp_below(Xm[2] + Sz) + half_ulp_below(Sz) + conv[2];
+    for (int m = 0; m < 27; ++m) {
+      const double kx = m / 9 - 1, ky = (m / 3) % 3 - 1, kz = m % 3 - 1;
+      F.tshift[m][0] = (float)-((kx * ax + ky * bx) + kz * cx);
+      F.tshift[m][1] = (float)-(ky * by + kz * cy);
+      F.tshift[m][2] = (float)-(kz * cz);
+    }
     I[0] = D2x + Kx * ax;
     I[1] = D1y + Ky * by;
     I[2] = R[2] + Kz * cz;
@@ -517,15 +522,6 @@ __device__ __forceinline__ void set_bound(const FrameDev& F, FastParams& P, bool
   const float g = F.alpha_t + 2.0f * beta;
   P.qb1 = (2.0f * F.alpha_t + g / (2.0f * tau)) * slack;
   P.qb0 = (0.5f * g * tau + beta) * slack;
-}
-
-// Triclinic tile image: the vector B k (|k| <= 1 per component, so each product
-// is exact) in a fixed operation order, negated: the i's of the tile move by it.
-__device__ __forceinline__ float3 tric_image_shift(const FastParams& P, float3 k) {
-  const float sx = __fadd_rn(__fadd_rn(__fmul_rn(k.x, P.b[0]), __fmul_rn(k.y, P.b[1])), __fmul_rn(k.z, P.b[2]));
-  const float sy = __fadd_rn(__fmul_rn(k.y, P.b[4]), __fmul_rn(k.z, P.b[5]));
-  const float sz = __fmul_rn(k.z, P.b[8]);
-  return make_float3(-sx, -sy, -sz);
 }
 
 // Guard words on each side of a shared-memory histogram copy: the increments
@@ -1010,7 +1006,8 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
     ti = make_float3(kt.x < 0.f ? P.b[0] : 0.f, kt.y < 0.f ? P.b[4] : 0.f, kt.z < 0.f ? P.b[8] : 0.f);
     sj = make_float3(kt.x > 0.f ? P.b[0] : 0.f, kt.y > 0.f ? P.b[4] : 0.f, kt.z > 0.f ? P.b[8] : 0.f);
   } else if (V == V_TRIC && UNI) {
-    ti = tric_image_shift(P, kt);
+    const float* v = F->tshift[9 * (int)(kt.x + 1.0f) + 3 * (int)(kt.y + 1.0f) + (int)(kt.z + 1.0f)];
+    ti = make_float3(v[0], v[1], v[2]);
   }
   float2 xi[RI], yi[RI], zi[RI];  // i coordinates broadcast to both halves
 #pragma unroll
