@@ -55,6 +55,7 @@ struct FrameDev {
   int32_t bad;       // a non-finite coordinate was seen
   int32_t all_defer; // float32 decisions are not safe for this frame: every pair is deferred
   float beta_u;      // beta of tiles that take a uniform image (orthorhombic, triclinic)
+  float beta_w[3];   // beta of tiles with a uniform image on all axes but a, wrapped per pair
   float tie_m[3];    // orthorhombic: margin of the uniform-image test (0: not needed)
   float mid2, mid1;  // double-float tier: |r2 - T[n]| <= mid2*r2 + mid1*s decides nothing
   float tie_eps;     // orthorhombic: | |d'_c| - L_c/2 | <= tie_eps is re-decided in binary64

@@ -362,6 +362,8 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   double I[3] = {R[0], R[1], R[2]};  // magnitudes of the wrap intermediates (for the double-float tier)
   double tie = 0.0, tie_eps = 0.0;
   double au[3] = {0, 0, 0};  // absolute error of d'_c in tiles with a uniform image
+  double aw[3][3] = {};      // the same, axis a wrapped per pair (M_AXIS + a); tie term tie_w[a]
+  double tie_w[3] = {0, 0, 0};
   for (int c = 0; c < 3; ++c) F.tie_m[c] = 0.0f;
   int all_defer = 0;
   float eps_s = 0.0f;
@@ -399,6 +401,11 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
       au[c] = dB[4 * c] + conv[c];
       F.tie_m[c] = tie > 0.0 ? (float)(2.0 * tie_c[c]) : 0.0f;
     }
+    // one axis wrapped per pair: its own error and, alone, its tie term
+    for (int w = 0; w < 3; ++w) {
+      for (int c = 0; c < 3; ++c) aw[w][c] = c == w ? a[c] : au[c];
+      tie_w[w] = tie > 0.0 ? S * tie_c[w] * 1.01 : 0.0;
+    }
   } else if (F.variant == V_TRIC) {
     // sequential wrap along c, then b, then a (Eq. 5 below half the plane spacing);
     // D are the largest magnitudes of the intermediates, K the largest |k|
@@ -419,6 +426,12 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     au[0] = half_ulp_below(Xm[0] + Sx) + half_ulp_below(Sx) + conv[0];
     au[1] = half_ulp_below(Xm[1] + Sy) + half_ulp_below(Sy) + conv[1];
     au[2] = half_ulp_below(Xm[2] + Sz) + half_ulp_below(Sz) + conv[2];
+    // x wrapped per pair after the uniform c and b images (M_AXIS): d_x before
+    // its wrap rounds at up to R_x + |bx| + |cx|, and the wrap adds |kx| |ax32 - ax|
+    const double Dxw = R[0] + fabs(bx) + fabs(cx);
+    aw[0][0] = au[0] + half_ulp_below(Dxw) + Kx * dB[0];
+    aw[0][1] = au[1];
+    aw[0][2] = au[2];
     for (int m = 0; m < 27; ++m) {
       const double kx = m / 9 - 1, ky = (m / 3) % 3 - 1, kz = m % 3 - 1;
       F.tshift[m][0] = (float)-((kx * ax + ky * bx) + kz * cx);
@@ -433,7 +446,8 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     double ez = (2.0 * u * R[2] + conv[2] + R[2] * fabs((double)F.invf[2] * cz - 1.0)) / cz;
     double ey = (2.0 * (fmax(a[1], au[1]) + u * D1y) + D1y * fabs((double)F.invf[1] * by - 1.0)) / by;
     double ex = (2.0 * (fmax(a[0], au[0]) + u * D2x) + D2x * fabs((double)F.invf[0] * ax - 1.0)) / ax;
-    double emax = fmax(ex, fmax(ey, ez));
+    double exw = (2.0 * (aw[0][0] + u * Dxw) + Dxw * fabs((double)F.invf[0] * ax - 1.0)) / ax;
+    double emax = fmax(fmax(ex, exw), fmax(ey, ez));
     if (!(emax < 0.25 * (double)F.margin) || D2x / ax > 1048576.0 || D1y / by > 1048576.0 ||
         R[2] / cz > 1048576.0)
       all_defer = 1;
@@ -465,9 +479,15 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   double beta = S * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * (1.0 + 64.0 * u) + tie + 1.0 / 268435456.0;
   double beta_u = (F.variant == V_ORTHO || F.variant == V_TRIC) ? S * abs_u * (1.0 + 64.0 * u) + 1.0 / 268435456.0
                                                                  : beta;
+  double beta_w[3] = {beta, beta, beta};
+  for (int w = 0; w < 3; ++w)
+    if (F.variant == V_ORTHO || (F.variant == V_TRIC && w == 0))
+      beta_w[w] = S * sqrt(aw[w][0] * aw[w][0] + aw[w][1] * aw[w][1] + aw[w][2] * aw[w][2]) * (1.0 + 64.0 * u) +
+                  tie_w[w] + 1.0 / 268435456.0;
   alpha = alpha * (1.0 + 1.0 / 1024.0) + 1e-12;
   double delta = alpha * ((double)F.nbins + 1.0) + beta;
-  if (!(delta < 0.25) || !(alpha * ((double)F.nbins + 1.0) + beta_u < 0.25)) all_defer = 1;
+  const double beta_max = fmax(fmax(beta, beta_u), fmax(beta_w[0], fmax(beta_w[1], beta_w[2])));
+  if (!(delta < 0.25) || !(alpha * ((double)F.nbins + 1.0) + beta_max < 0.25)) all_defer = 1;
   // the q-space test itself is formed per sweep (load_fast_params)
   double Imax = fmax(I[0], fmax(I[1], I[2]));
   double amid = 1.7320508075688772 * (R[0] + R[1] + R[2] + 4.0 * Imax) / 1099511627776.0;  // 2^-40
@@ -481,6 +501,7 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   F.alpha_t = (float)alpha;
   F.beta_t = (float)beta;
   F.beta_u = (float)beta_u;
+  for (int w = 0; w < 3; ++w) F.beta_w[w] = (float)beta_w[w];
   F.eps_s = eps_s;
   F.all_defer = all_defer;
 }
@@ -492,6 +513,12 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
 template <int RI>
 constexpr int ju_of() { return 16 / RI; }
 constexpr int kJUMax = 16;
+
+// Tile modes of the periodic variants (tile_image): per-pair images, one
+// uniform image, or a uniform image on all axes but one (M_AXIS + a:
+// orthorhombic axis a; triclinic only a = 0, x), which is wrapped per pair.
+constexpr int M_PAIR = 0, M_UNI = 1, M_AXIS = 2;
+constexpr bool shifted_mode(int mode) { return mode >= M_UNI; }
 
 struct FastParams {
   float S2;
@@ -505,20 +532,20 @@ struct FastParams {
 };
 
 // The q-space test of the sweep [P.lo, P.hi) as one FMA in q.  The bound
-// 2 alpha q + gamma t' + beta (gamma = alpha + 2 beta; beta_u for a tile with a
-// uniform image) with t' <= (q/tau + tau)/2, true for any tau > 0, becomes
-// (2 alpha + gamma/(2 tau)) q + (gamma tau/2 + beta), exact at t' = tau;
+// 2 alpha q + gamma t' + beta (gamma = alpha + 2 beta; beta of the tile mode:
+// beta_t, beta_u, beta_w[a]) with t' <= (q/tau + tau)/2, true for any tau > 0,
+// becomes (2 alpha + gamma/(2 tau)) q + (gamma tau/2 + beta), exact at t' = tau;
 // tau = (hi + 2)/sqrt(2) (at least lo + 1) minimises the mean window over the
 // sweep for pair counts growing like t^2.  The float32 evaluation (a few
 // roundings, and alpha_t, beta_t rounded) is covered by the factor 1 + 2^-10.
-__device__ __forceinline__ void set_bound(const FrameDev& F, FastParams& P, bool uniform) {
+__device__ __forceinline__ void set_bound(const FrameDev& F, FastParams& P, int mode) {
   if (F.all_defer) {
     P.qb1 = P.qb0 = 1e30f;
     return;
   }
   const float tau = fmaxf((float)(P.hi + 2) * 0.70710678f, (float)(P.lo + 1));
   const float slack = 1.0f + 1.0f / 1024.0f;
-  const float beta = uniform ? F.beta_u : F.beta_t;
+  const float beta = mode == M_PAIR ? F.beta_t : (mode == M_UNI ? F.beta_u : F.beta_w[mode - M_AXIS]);
   const float g = F.alpha_t + 2.0f * beta;
   P.qb1 = (2.0f * F.alpha_t + g / (2.0f * tau)) * slack;
   P.qb0 = (0.5f * g * tau + beta) * slack;
@@ -597,16 +624,25 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // float32 |d'|^2 of two pairs after the minimum image of the variant; each
-// component is rounded exactly as the scalar sequence of wrap_r2.  UNI: the
-// tile pair's nearest-image integers are known for every pair (see tile_image)
-// and the caller has already subtracted the image from the coordinates, so d
-// is the image vector itself.
-template <int V, bool UNI = false>
+// component is rounded exactly as the scalar sequence of wrap_r2.  In the
+// shifted modes the caller has already subtracted the tile's images from the
+// coordinates, so d is the image vector itself, but for the one axis of an
+// M_AXIS mode, wrapped here as wrap_r2 does.
+template <int V, int MODE = M_PAIR>
 __device__ __forceinline__ float2 wrap_r2_2(float2 dx, float2 dy, float2 dz, const FastParams& P, bool& amb_a,
-                                            bool& amb_b, float3 kt = make_float3(0.f, 0.f, 0.f)) {
+                                            bool& amb_b) {
   const float2 M = bc2(kMagicRound), NM = bc2(-kMagicRound);
-  if (UNI && (V == V_ORTHO || V == V_TRIC)) {
-    // the coordinates were shifted by the images already
+  if (shifted_mode(MODE) && (V == V_ORTHO || V == V_TRIC)) {
+    if (MODE == M_AXIS + 0) {
+      float2 kx = add2(fma2(dx, bc2(P.inv[0]), M), NM);
+      dx = fma2(kx, bc2(-P.b[0]), dx);
+    } else if (V == V_ORTHO && MODE == M_AXIS + 1) {
+      float2 ky = add2(fma2(dy, bc2(P.inv[1]), M), NM);
+      dy = fma2(ky, bc2(-P.b[4]), dy);
+    } else if (V == V_ORTHO && MODE == M_AXIS + 2) {
+      float2 kz = add2(fma2(dz, bc2(P.inv[2]), M), NM);
+      dz = fma2(kz, bc2(-P.b[8]), dz);
+    }
   } else if (V == V_ORTHO) {
     float2 kx = add2(fma2(dx, bc2(P.inv[0]), M), NM);
     float2 ky = add2(fma2(dy, bc2(P.inv[1]), M), NM);
@@ -671,12 +707,11 @@ __device__ __forceinline__ void count_or_defer(float sm, float e, float bound, u
 // decide_arith2 returns sm = s_c + 1.5*2^23, e and the bound as float pairs
 // (search variant: ambiguous images force the bound to +inf so the pair is
 // deferred); count_or_defer acts on them.
-template <int V, bool MULTI, bool UNI = false>
+template <int V, bool MULTI, int MODE = M_PAIR>
 __device__ __forceinline__ void decide_arith2(float2 dx, float2 dy, float2 dz, const FastParams& P, float chi,
-                                              float clo, float2& sm, float2& e, float2& bound,
-                                              float3 kt = make_float3(0.f, 0.f, 0.f)) {
+                                              float clo, float2& sm, float2& e, float2& bound) {
   bool amb_a = false, amb_b = false;
-  float2 r2 = wrap_r2_2<V, UNI>(dx, dy, dz, P, amb_a, amb_b, kt);
+  float2 r2 = wrap_r2_2<V, MODE>(dx, dy, dz, P, amb_a, amb_b);
   float2 nq = mul2(r2, bc2(-P.S2));  // -q
   float2 sq = make_float2(sqrt_approx(-nq.x), sqrt_approx(-nq.y));
   float2 sc = make_float2(fminf(sq.x, chi), fminf(sq.y, chi));  // NaN -> chi
@@ -707,16 +742,19 @@ __device__ __forceinline__ void fast_decide2(float2 dx, float2 dy, float2 dz, co
 // The relative bin at which the float32 path counted a pair (provisionally,
 // if it deferred it): the scalar replay of decide_arith2 and count_or_defer,
 // operation for operation, for the lane `src_lane` that evaluated the pair.
-template <int V, bool MULTI, bool UNI = false>
+template <int V, bool MULTI, int MODE = M_PAIR>
 __device__ __forceinline__ int provisional_rel(const FastParams& P, float4 pi, float4 pj, int src_lane,
                                                float3 ti = make_float3(0.f, 0.f, 0.f),
                                                float3 sj = make_float3(0.f, 0.f, 0.f)) {
   bool amb = false;
   float r2;
-  if ((V == V_ORTHO || V == V_TRIC) && UNI) {  // the coordinates shifted by the tile's images, no wrap
-    const float dx = __fsub_rn(__fsub_rn(pj.x, sj.x), __fsub_rn(pi.x, ti.x));
-    const float dy = __fsub_rn(__fsub_rn(pj.y, sj.y), __fsub_rn(pi.y, ti.y));
-    const float dz = __fsub_rn(__fsub_rn(pj.z, sj.z), __fsub_rn(pi.z, ti.z));
+  if ((V == V_ORTHO || V == V_TRIC) && shifted_mode(MODE)) {  // the coordinates shifted by the tile's images
+    float dx = __fsub_rn(__fsub_rn(pj.x, sj.x), __fsub_rn(pi.x, ti.x));
+    float dy = __fsub_rn(__fsub_rn(pj.y, sj.y), __fsub_rn(pi.y, ti.y));
+    float dz = __fsub_rn(__fsub_rn(pj.z, sj.z), __fsub_rn(pi.z, ti.z));
+    if (MODE == M_AXIS + 0) dx = __fmaf_rn(-nint_scaled(dx, P.inv[0]), P.b[0], dx);
+    if (V == V_ORTHO && MODE == M_AXIS + 1) dy = __fmaf_rn(-nint_scaled(dy, P.inv[1]), P.b[4], dy);
+    if (V == V_ORTHO && MODE == M_AXIS + 2) dz = __fmaf_rn(-nint_scaled(dz, P.inv[2]), P.b[8], dz);
     r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
   } else {
     r2 = wrap_r2<V>(__fadd_rn(pj.x, -pi.x), __fadd_rn(pj.y, -pi.y), __fadd_rn(pj.z, -pi.z), P, amb);
@@ -939,7 +977,7 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P);
 // provisional count of each to its exact bin where they differ, and shift the
 // rest of the queue down.  A queue entry is (i - i0) | (j - j0) << 16 for the
 // tile's first i and j; lane (i - i0) mod 32 evaluated the pair.
-template <int V, bool MULTI, bool UNI = false>
+template <int V, bool MULTI, int MODE = M_PAIR>
 __device__ __forceinline__ int drain_queue_body(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
                                                 uint32_t* sh, int lane, float3 ti = make_float3(0.f, 0.f, 0.f),
                                                 float3 sj = make_float3(0.f, 0.f, 0.f)) {
@@ -952,7 +990,7 @@ __device__ __forceinline__ int drain_queue_body(const FrameDev* F, int pass, int
     float4 pj = __ldg(F->X + j0 + jl);
     FastParams P;
     load_fast_params(*F, pass, P);
-    int relp = provisional_rel<V, MULTI, UNI>(P, pi, pj, il & 31, ti, sj);
+    int relp = provisional_rel<V, MULTI, MODE>(P, pi, pj, il & 31, ti, sj);
     int relx = (V == V_NONE ? deferred_bin_call<V>(*F, i0 + il, j0 + jl, pi, pj, nexact)
                             : deferred_bin<V>(*F, i0 + il, j0 + jl, pi, pj, nexact)) - P.lo;
     if (relx != relp) {
@@ -978,11 +1016,11 @@ __device__ __noinline__ int drain_queue_call(const FrameDev* F, int pass, int i0
 // The register allocation of the hot loop decides which form is faster
 // (measured): the periodic variants keep fewer live values across an inlined
 // drain than across a call, the no-box variant the other way round.
-template <int V, bool MULTI, bool UNI>
+template <int V, bool MULTI, int MODE>
 __device__ __forceinline__ int drain_queue(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
                                            uint32_t* sh, int lane, float3 ti, float3 sj) {
   if constexpr (V == V_ORTHO || V == V_TRIC)
-    return drain_queue_body<V, MULTI, UNI>(F, pass, i0, j0, q, qcount, sh, lane, ti, sj);
+    return drain_queue_body<V, MULTI, MODE>(F, pass, i0, j0, q, qcount, sh, lane, ti, sj);
   else
     return drain_queue_call<V, MULTI>(F, pass, i0, j0, q, qcount, sh, lane);
 }
@@ -990,7 +1028,7 @@ __device__ __forceinline__ int drain_queue(const FrameDev* F, int pass, int i0, 
 // j tile in shared memory as pairs of particles: A[p] = {x_2p, x_2p+1, y_2p, y_2p+1},
 // Z[p] = {z_2p, z_2p+1}, so one LDS.128 + one LDS.64 feed two j particles.
 // j particles [jb, je) of the staged tile (jb a multiple of kSubJ).
-template <int V, bool MASKED, bool MULTI, int RI, bool UNI>
+template <int V, bool MASKED, bool MULTI, int RI, int MODE>
 __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
                                          const float4* __restrict__ sjA, const float2* __restrict__ sjZ,
                                          uint32_t* sh, uint32_t* q, int tid, int lane, unsigned& ndeferred,
@@ -1001,11 +1039,12 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
   // sj from the j's.  Orthorhombic (exact, see tile_image): k = -1 takes L from
   // the i's, k = +1 from the j's.  Triclinic: the i's move by the image vector
   // B k, rounded once (|k| <= 1, so the products are exact).
+  constexpr bool SH = (V == V_ORTHO || V == V_TRIC) && shifted_mode(MODE);
   float3 ti = make_float3(0.f, 0.f, 0.f), sj = make_float3(0.f, 0.f, 0.f);
-  if (V == V_ORTHO && UNI) {
+  if (V == V_ORTHO && SH) {
     ti = make_float3(kt.x < 0.f ? P.b[0] : 0.f, kt.y < 0.f ? P.b[4] : 0.f, kt.z < 0.f ? P.b[8] : 0.f);
     sj = make_float3(kt.x > 0.f ? P.b[0] : 0.f, kt.y > 0.f ? P.b[4] : 0.f, kt.z > 0.f ? P.b[8] : 0.f);
-  } else if (V == V_TRIC && UNI) {
+  } else if (V == V_TRIC && SH) {
     const float* v = F->tshift[9 * (int)(kt.x + 1.0f) + 3 * (int)(kt.y + 1.0f) + (int)(kt.z + 1.0f)];
     ti = make_float3(v[0], v[1], v[2]);
   }
@@ -1017,7 +1056,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
     if (li < it.ni) {
       float4 p = __ldg(F->X + it.i0 + li);
       x = p.x; y = p.y; z = p.z;
-      if ((V == V_ORTHO || V == V_TRIC) && UNI) {
+      if (SH) {
         x = __fsub_rn(x, ti.x);
         y = __fsub_rn(y, ti.y);
         z = __fsub_rn(z, ti.z);
@@ -1042,10 +1081,10 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
       const float4 A = sjA[(jj0 + u) >> 1];
       float2 Z = sjZ[(jj0 + u) >> 1];
       float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
-      if (V == V_ORTHO && UNI) {
-        xj = add2(xj, bc2(-sj.x));
-        yj = add2(yj, bc2(-sj.y));
-        Z = add2(Z, bc2(-sj.z));
+      if (V == V_ORTHO && SH) {  // (the wrapped axis of an M_AXIS mode has no shift)
+        if (MODE != M_AXIS + 0) xj = add2(xj, bc2(-sj.x));
+        if (MODE != M_AXIS + 1) yj = add2(yj, bc2(-sj.y));
+        if (MODE != M_AXIS + 2) Z = add2(Z, bc2(-sj.z));
       }
 #pragma unroll
       for (int r = 0; r < RI; ++r) {
@@ -1059,7 +1098,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
           if (!(jg + 1 > ig)) { dx.y = qnan; dy.y = qnan; dz.y = qnan; }
         }
         float2 sm, e, bound;
-        decide_arith2<V, MULTI, UNI>(dx, dy, dz, P, chi, clo, sm, e, bound, kt);
+        decide_arith2<V, MULTI, MODE>(dx, dy, dz, P, chi, clo, sm, e, bound);
         count_or_defer(sm.x, e.x, bound.x, hbase, 1u << (u * RI + r), dmask);
         count_or_defer(sm.y, e.y, bound.y, hbase, 1u << ((u + 1) * RI + r), dmask);
       }
@@ -1078,13 +1117,13 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
       ndeferred += added;
       if (qcount >= 32) {
         __syncwarp();
-        qcount = drain_queue<V, MULTI, UNI>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane, ti, sj);
+        qcount = drain_queue<V, MULTI, MODE>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane, ti, sj);
       }
       bal = __ballot_sync(kFull, dmask != 0u);
     }
   }
   __syncwarp();
-  if (qcount > 0) drain_queue<V, MULTI, UNI>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane, ti, sj);
+  if (qcount > 0) drain_queue<V, MULTI, MODE>(F, it.pass, it.i0, it.j0, q, qcount, sh, lane, ti, sj);
   __syncwarp();
 }
 
@@ -1093,7 +1132,9 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
 // MULTI: some sweep of the launch starts above bin 0, so the root is also
 // clamped from below (valid for every sweep, a separate kernel for registers).
 // For the periodic variants the j tile is taken in sub-chunks of kSubJ
-// particles; img[c] is this warp's tile image for sub-chunk c (w = 0: none).
+// particles; img[c] is this warp's tile image and mode (w) for sub-chunk c.
+// Items that mask j <= i take the per-pair path in the M_AXIS modes (fewer
+// instances; such items are the diagonal of a species block).
 template <int V, bool MULTI, int RI>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
                          uint32_t* q, int tid, int lane, unsigned& ndeferred, const float4* img) {
@@ -1104,20 +1145,29 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
       const int jb = c * kSubJ, je = min(it.nj, jb + kSubJ);
       const float4 im = img[c];
       const float3 kt = make_float3(im.x, im.y, im.z);
-      set_bound(*F, P, im.w != 0.0f);
-      if (im.w != 0.0f) {
-        if (it.masked) run_tile<V, true, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
-        else run_tile<V, false, MULTI, RI, true>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
+      int mode = (int)im.w;
+      if (it.masked && mode >= M_AXIS) mode = M_PAIR;
+      set_bound(*F, P, mode);
+#define DH_TILE(M_, K_) run_tile<V, M_, MULTI, RI, K_>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je)
+      if (it.masked) {
+        if (mode == M_UNI) DH_TILE(true, M_UNI);
+        else DH_TILE(true, M_PAIR);
       } else {
-        if (it.masked) run_tile<V, true, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
-        else run_tile<V, false, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je);
+        switch (mode) {
+          case M_UNI: DH_TILE(false, M_UNI); break;
+          case M_AXIS + 0: DH_TILE(false, M_AXIS + 0); break;
+          case M_AXIS + 1: if (V == V_ORTHO) DH_TILE(false, M_AXIS + 1); break;
+          case M_AXIS + 2: if (V == V_ORTHO) DH_TILE(false, M_AXIS + 2); break;
+          default: DH_TILE(false, M_PAIR); break;
+        }
       }
+#undef DH_TILE
     }
     return;
   }
   const float3 k0 = make_float3(0.f, 0.f, 0.f);
-  if (it.masked) run_tile<V, true, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
-  else run_tile<V, false, MULTI, RI, false>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+  if (it.masked) run_tile<V, true, MULTI, RI, M_PAIR>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+  else run_tile<V, false, MULTI, RI, M_PAIR>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
 }
 
 // The nearest-image integers of a tile pair, when the float32 per-pair path
@@ -1127,7 +1177,9 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
 // subtracted); every step is a correctly rounded monotone function of d, so
 // the tile's extreme differences fl(jmin - imax) and fl(jmax - imin) bound the
 // value of every pair at every step, and equal integers at both ends are the
-// integers of every pair.  Returns (kx, ky, kz, 1) in that case, w = 0 else.
+// integers of every pair.  Returns (kx, ky, kz, mode): M_UNI in that case;
+// M_AXIS + a when that holds for every axis but a (orthorhombic; triclinic:
+// for c and b, a = 0), whose k is then 0 and wrapped per pair; M_PAIR else.
 template <int V>
 __device__ float4 tile_image(const FrameDev& F, const float* imin, const float* imax, const float* jmin,
                              const float* jmax) {
@@ -1142,18 +1194,23 @@ __device__ float4 tile_image(const FrameDev& F, const float* imin, const float* 
     // k = +1 from the j's, k = -1 from the i's, which Sterbenz's lemma grants when
     // they lie in [L/2, 2L]
     // (widened by tie_m, so that no pair lies where float32 and binary64 may
-    // round d/L to different images: such tiles keep the per-pair path)
+    // round d/L to different images); an axis that fails is wrapped per pair
     float k[3];
+    int nw = 0, wa = 0;
     for (int c = 0; c < 3; ++c) {
       k[c] = nint_scaled(__fsub_rn(lo[c], F.tie_m[c]), F.invf[c]);
-      if (!(nint_scaled(__fadd_rn(hi[c], F.tie_m[c]), F.invf[c]) == k[c])) return make_float4(0.f, 0.f, 0.f, 0.f);
       const float L = b[4 * c];
-      bool ok = (k[c] == 0.0f) ||
-                (k[c] == 1.0f && jmin[c] >= 0.5f * L && jmax[c] <= 2.0f * L) ||
-                (k[c] == -1.0f && imin[c] >= 0.5f * L && imax[c] <= 2.0f * L);
-      if (!ok) return make_float4(0.f, 0.f, 0.f, 0.f);
+      bool ok = nint_scaled(__fadd_rn(hi[c], F.tie_m[c]), F.invf[c]) == k[c] &&
+                ((k[c] == 0.0f) || (k[c] == 1.0f && jmin[c] >= 0.5f * L && jmax[c] <= 2.0f * L) ||
+                 (k[c] == -1.0f && imin[c] >= 0.5f * L && imax[c] <= 2.0f * L));
+      if (!ok) {
+        ++nw;
+        wa = c;
+        k[c] = 0.0f;
+      }
     }
-    return make_float4(k[0], k[1], k[2], 1.0f);
+    if (nw > 1) return make_float4(0.f, 0.f, 0.f, (float)M_PAIR);
+    return make_float4(k[0], k[1], k[2], nw == 0 ? (float)M_UNI : (float)(M_AXIS + wa));
   } else {
     // z, then y and x after the c image, then x after the b image
     const float kz = nint_scaled(lo[2], F.invf[2]);
@@ -1164,10 +1221,10 @@ __device__ float4 tile_image(const FrameDev& F, const float* imin, const float* 
     if (!(nint_scaled(yhi, F.invf[1]) == ky)) return make_float4(0.f, 0.f, 0.f, 0.f);
     xlo = __fmaf_rn(ky, -b[1], xlo);
     xhi = __fmaf_rn(ky, -b[1], xhi);
+    if (fabsf(ky) > 1.0f || fabsf(kz) > 1.0f) return make_float4(0.f, 0.f, 0.f, (float)M_PAIR);
     const float kx = nint_scaled(xlo, F.invf[0]);
-    if (!(nint_scaled(xhi, F.invf[0]) == kx)) return make_float4(0.f, 0.f, 0.f, 0.f);
-    if (fabsf(kx) > 1.0f || fabsf(ky) > 1.0f || fabsf(kz) > 1.0f) return make_float4(0.f, 0.f, 0.f, 0.f);
-    return make_float4(kx, ky, kz, 1.0f);
+    if (!(nint_scaled(xhi, F.invf[0]) == kx) || fabsf(kx) > 1.0f) return make_float4(0.f, ky, kz, (float)M_AXIS);
+    return make_float4(kx, ky, kz, (float)M_UNI);
   }
 }
 
@@ -1246,7 +1303,7 @@ __device__ void load_fast_params(const FrameDev& F, int pass, FastParams& P) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) P.inv[c] = F.invf[c];
   P.amb_thr = 0.5f - F.eps_s;
-  set_bound(F, P, false);
+  set_bound(F, P, M_PAIR);
 }
 
 // One instance per minimum-image variant V (every segment of the launch has a
@@ -1385,7 +1442,7 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
           if (ni_w > 0) img = tile_image<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3);
           if (lane == 0) {
             s_img[warp][c] = img;
-            if (img.w != 0.0f)
+            if (img.w == (float)M_UNI)
               atomicAdd(&it.fd->uniform_pairs,
                         (unsigned long long)ni_w * (unsigned long long)(min(it.nj, (c + 1) * kSubJ) - c * kSubJ));
           }
