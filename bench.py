@@ -595,6 +595,7 @@ def run_gpu(args, world, rank, local):
             "ms": round(statistics.mean(ts), 3),
             "deferred_frac": round(st["deferred"] / max(1, st["pairs"]), 6),
             "tile_image_frac": round(st["uniform_pairs"] / max(1, st["pairs"]), 4),
+            "axis_image_frac": round(st["axis_pairs"] / max(1, st["pairs"]), 4),
         }
 
     # ---- binary64 input coordinates (the same frames, coordinates perturbed below

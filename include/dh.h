@@ -130,6 +130,7 @@ typedef struct {
   int32_t blocks_per_sm;   /*   blocks per SM */
   int32_t block_threads;   /*   and threads per block */
   uint64_t uniform_pairs;  /* pairs evaluated with one nearest image for their whole tile (no per-pair rounding) */
+  uint64_t axis_pairs;     /* pairs whose tile image is uniform on all axes but one (that axis wrapped per pair) */
 } dh_stats;
 
 /* Create a context on config->device (NULL: device 0, defaults).  Owns a CUDA

@@ -16,7 +16,7 @@ enum Variant : int32_t {
 };
 
 constexpr int kTile = 1024;          // i particles per work item (and the longest j tile)
-constexpr int kSubJ = 128;           // j sub-chunk with its own tile image per warp
+constexpr int kSubJ = 256;           // j sub-chunk with its own tile image per warp
 // Pair-kernel blocks: 256 threads with 4 i particles each, 512 with 2, or 1024 with 1.
 constexpr int kBlockSmall = 256;
 constexpr int kBlockLarge = 512;
@@ -65,6 +65,7 @@ struct FrameDev {
   unsigned long long deferred;  // statistics: pairs queued for the double-float tier
   unsigned long long exact;     // pairs that also needed the binary64 replay
   unsigned long long uniform_pairs;  // pairs of (warp i run, j tile) blocks with one nearest image for all
+  unsigned long long axis_pairs;     // pairs of such blocks whose image is uniform on all axes but one
 };
 
 // One species pair (a,b) of one frame and one bin sweep, cut into kTile x kTile

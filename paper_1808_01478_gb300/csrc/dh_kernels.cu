@@ -1442,9 +1442,10 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
           if (ni_w > 0) img = tile_image<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3);
           if (lane == 0) {
             s_img[warp][c] = img;
-            if (img.w == (float)M_UNI)
-              atomicAdd(&it.fd->uniform_pairs,
-                        (unsigned long long)ni_w * (unsigned long long)(min(it.nj, (c + 1) * kSubJ) - c * kSubJ));
+            const unsigned long long np =
+                (unsigned long long)ni_w * (unsigned long long)(min(it.nj, (c + 1) * kSubJ) - c * kSubJ);
+            if (img.w == (float)M_UNI) atomicAdd(&it.fd->uniform_pairs, np);
+            else if (img.w >= (float)M_AXIS) atomicAdd(&it.fd->axis_pairs, np);
           }
         }
         __syncwarp();

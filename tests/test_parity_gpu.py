@@ -227,6 +227,7 @@ def test_tile_images_at_larger_n_match_the_unsorted_path(ctx, torch_mod, box_typ
     got = ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins).cpu().numpy().view(np.uint64)
     st = ctx.stats()
     assert 0 < st["uniform_pairs"] <= st["pairs"], st
+    assert 0 < st["axis_pairs"] <= st["pairs"] - st["uniform_pairs"], st  # one-axis tiles exercised too
     out = torch_mod.zeros((1, f.nbins), dtype=torch_mod.int64, device="cuda")
     fa = dh.FrameArgs(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
     dh.dh_histogram_noalloc(fa.frame)
