@@ -185,7 +185,8 @@ def test_repeat_calls_identical_and_threshold_cache(ctx, torch_mod, oracle_mod):
 
 # Species of periodic frames are put in spatial order before the pair kernel,
 # and tile pairs whose float32 nearest images are provably the same for every
-# pair skip the per-pair rounding; both must leave every bin unchanged.
+# pair (on all axes, or on all but one) skip the per-pair rounding of those
+# axes; both must leave every bin unchanged.
 SPATIAL = {
     "ortho_sorted_species": w.frame_from(
         w.uniform_frame(61, 30000, w.BOX_ORTHO, w.ortho_box(60.0, 50.0, 70.0), 25.0, 6000).coords,
@@ -206,8 +207,8 @@ def test_spatial_order_and_tile_images(ctx, torch_mod, oracle_mod, name):
     assert_same(got, oracle_mod.histogram_frame(f), name)
     st = ctx.stats()
     if name == "ortho_sorted_species":
-        assert st["uniform_pairs"] > 0, st
-    assert st["uniform_pairs"] <= st["pairs"]
+        assert st["uniform_pairs"] > 0 and st["axis_pairs"] > 0, st
+    assert st["uniform_pairs"] + st["axis_pairs"] <= st["pairs"]
 
 
 @pytest.mark.parametrize("box_type", [w.BOX_ORTHO, w.BOX_TRICLINIC])
