@@ -504,6 +504,14 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   for (int w = 0; w < 3; ++w) F.beta_w[w] = (float)beta_w[w];
   F.eps_s = eps_s;
   F.all_defer = all_defer;
+  // No box, one sweep: the largest possible distance, sqrt(sum R_c^2), maps below
+  // nbins + 1 even after the float32 roundings of q and of its square root
+  // (relative 2^-18 covers them), so no pair's root reaches the clamp.
+  {
+    const double D = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+    F.in_range = F.variant == V_NONE && F.sweep_width >= F.nbins && !all_defer &&
+                 S * D * (1.0 + 1.0 / 262144.0) < (double)F.nbins + 1.0;
+  }
 }
 
 // ------------------------------------------------------------------ A2-A8: pair kernel
@@ -517,6 +525,8 @@ constexpr int kJUMax = 16;
 // Tile modes of the periodic variants (tile_image): per-pair images, one
 // uniform image, or a uniform image on all axes but one (M_AXIS + a:
 // orthorhombic axis a; triclinic only a = 0, x), which is wrapped per pair.
+// No box: M_UNI marks a tile of an in-range frame without padding, whose
+// roots need no clamp.
 constexpr int M_PAIR = 0, M_UNI = 1, M_AXIS = 2;
 constexpr bool shifted_mode(int mode) { return mode >= M_UNI; }
 
@@ -714,7 +724,9 @@ __device__ __forceinline__ void decide_arith2(float2 dx, float2 dy, float2 dz, c
   float2 r2 = wrap_r2_2<V, MODE>(dx, dy, dz, P, amb_a, amb_b);
   float2 nq = mul2(r2, bc2(-P.S2));  // -q
   float2 sq = make_float2(sqrt_approx(-nq.x), sqrt_approx(-nq.y));
-  float2 sc = make_float2(fminf(sq.x, chi), fminf(sq.y, chi));  // NaN -> chi
+  // NaN -> chi; a no-box tile of an in-range frame (M_UNI) has neither NaN nor
+  // roots near the clamp
+  float2 sc = (V == V_NONE && MODE == M_UNI) ? sq : make_float2(fminf(sq.x, chi), fminf(sq.y, chi));
   if (MULTI) sc = make_float2(fmaxf(sc.x, clo), fmaxf(sc.y, clo));
   sm = add2(sc, bc2(kMagicRound));
   float2 n = add2(sm, bc2(-kMagicRound));
@@ -1166,8 +1178,14 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
     return;
   }
   const float3 k0 = make_float3(0.f, 0.f, 0.f);
-  if (it.masked) run_tile<V, true, MULTI, RI, M_PAIR>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
-  else run_tile<V, false, MULTI, RI, M_PAIR>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+  if (it.masked) {
+    run_tile<V, true, MULTI, RI, M_PAIR>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+  } else if (V == V_NONE && F->in_range && it.ni == kTile && (it.nj % kJUMax) == 0) {
+    // every pair real (no NaN padding) and in range: the root needs no clamp
+    run_tile<V, false, MULTI, RI, M_UNI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+  } else {
+    run_tile<V, false, MULTI, RI, M_PAIR>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+  }
 }
 
 // The nearest-image integers of a tile pair, when the float32 per-pair path
