@@ -270,7 +270,7 @@ dh_status dh_selfcheck(dh_ctx* ctx, int32_t what, const dh_frame* frame, uint64_
  * on it and must be serialised by the caller. */
 #define DH_NOALLOC_MAX_N 131072
 #define DH_NOALLOC_MAX_BINS 65536
-#define DH_NOALLOC_SCRATCH_BYTES 3163904
+#define DH_NOALLOC_SCRATCH_BYTES 3164928
 dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream);
 
 /* Library version string. */

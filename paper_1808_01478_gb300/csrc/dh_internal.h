@@ -47,6 +47,9 @@ struct FrameDev {
   float margin;      // triclinic: 1 - 2 r_max / h_min (no-search precondition margin)
   float tshift[27][3];  // triclinic tile images: -B k rounded once from binary64, k in {-1,0,1}^3
                         // (index 9 (kx+1) + 3 (ky+1) + (kz+1))
+  float tserr[27][3];   // |tshift - (-B k)|, rounded up
+  float convf[3];       // binary64 input: per-axis conversion error (conv), rounded up
+  float kxdb;           // triclinic: largest |kx| times |ax32 - ax|, rounded up
   double eps_S;      // |S - nbins/r_max| / (nbins/r_max)
   double eps_S2;     // |S2 - (nbins/r_max)^2| / (nbins/r_max)^2
   // ---- written on the device

@@ -364,7 +364,11 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   double au[3] = {0, 0, 0};  // absolute error of d'_c in tiles with a uniform image
   double aw[3][3] = {};      // the same, axis a wrapped per pair (M_AXIS + a); tie term tie_w[a]
   double tie_w[3] = {0, 0, 0};
-  for (int c = 0; c < 3; ++c) F.tie_m[c] = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    F.tie_m[c] = 0.0f;
+    F.convf[c] = __double2float_ru(conv[c]);
+  }
+  F.kxdb = 0.0f;
   int all_defer = 0;
   float eps_s = 0.0f;
   const double* B = F.B;
@@ -434,10 +438,14 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     aw[0][2] = au[2];
     for (int m = 0; m < 27; ++m) {
       const double kx = m / 9 - 1, ky = (m / 3) % 3 - 1, kz = m % 3 - 1;
-      F.tshift[m][0] = (float)-((kx * ax + ky * bx) + kz * cx);
-      F.tshift[m][1] = (float)-(ky * by + kz * cy);
-      F.tshift[m][2] = (float)-(kz * cz);
+      const double v[3] = {-((kx * ax + ky * bx) + kz * cx), -(ky * by + kz * cy), -(kz * cz)};
+      for (int c = 0; c < 3; ++c) {
+        F.tshift[m][c] = (float)v[c];
+        // the binary64 sum itself errs by at most 2^-52 of the row sum
+        F.tserr[m][c] = __double2float_ru(fabs((double)F.tshift[m][c] - v[c]) + fmax(Sx, fmax(Sy, Sz)) * 0x1p-51);
+      }
     }
+    F.kxdb = __double2float_ru(Kx * dB[0]);
     I[0] = D2x + Kx * ax;
     I[1] = D1y + Ky * by;
     I[2] = R[2] + Kz * cz;
@@ -548,17 +556,49 @@ struct FastParams {
 // tau = (hi + 2)/sqrt(2) (at least lo + 1) minimises the mean window over the
 // sweep for pair counts growing like t^2.  The float32 evaluation (a few
 // roundings, and alpha_t, beta_t rounded) is covered by the factor 1 + 2^-10.
-__device__ __forceinline__ void set_bound(const FrameDev& F, FastParams& P, int mode) {
+__device__ __forceinline__ void set_bound_beta(const FrameDev& F, FastParams& P, float beta) {
   if (F.all_defer) {
     P.qb1 = P.qb0 = 1e30f;
     return;
   }
   const float tau = fmaxf((float)(P.hi + 2) * 0.70710678f, (float)(P.lo + 1));
   const float slack = 1.0f + 1.0f / 1024.0f;
-  const float beta = mode == M_PAIR ? F.beta_t : (mode == M_UNI ? F.beta_u : F.beta_w[mode - M_AXIS]);
   const float g = F.alpha_t + 2.0f * beta;
   P.qb1 = (2.0f * F.alpha_t + g / (2.0f * tau)) * slack;
   P.qb0 = (0.5f * g * tau + beta) * slack;
+}
+__device__ __forceinline__ void set_bound(const FrameDev& F, FastParams& P, int mode) {
+  set_bound_beta(F, P, mode == M_PAIR ? F.beta_t : (mode == M_UNI ? F.beta_u : F.beta_w[mode - M_AXIS]));
+}
+
+// Half an ulp of the largest float32 of magnitude at most X (X >= 0, finite):
+// the rounding error of any result whose magnitude X bounds.
+__device__ __forceinline__ float half_ulp_f(float X) {
+  return __uint_as_float(__float_as_uint(X) & 0x7f800000u) * 0x1p-24f;
+}
+
+// beta of one triclinic tile in a shifted mode (img = (kx, ky, kz, mode), kx = 0
+// for M_AXIS), from the tile's own magnitudes instead of the frame's largest:
+// x'_i = fl(x_i - tshift) rounds at half an ulp of the largest |x'_i| of the
+// warp's run (fl is monotone, so the run's bounds give it), tshift errs by
+// tserr, and binary64 input adds its conversion error; in M_AXIS the x
+// difference before its wrap rounds at half an ulp of its largest magnitude and
+// the wrap adds |kx| |ax32 - ax|.  These replace the frame-wide terms of beta_u
+// and beta_w[0] (which bound them), with the same outer factors.
+__device__ float tric_tile_beta(const FrameDev& F, const float* imin, const float* imax, const float* jmin,
+                                const float* jmax, float4 img) {
+  const int m = 9 * (int)(img.x + 1.0f) + 3 * (int)(img.y + 1.0f) + (int)(img.z + 1.0f);
+  float a2 = 0.0f;
+  for (int c = 0; c < 3; ++c) {
+    const float lo = __fsub_rn(imin[c], F.tshift[m][c]), hi = __fsub_rn(imax[c], F.tshift[m][c]);
+    float e = half_ulp_f(fmaxf(fabsf(lo), fabsf(hi))) + F.tserr[m][c] + F.convf[c];
+    if (c == 0 && img.w >= (float)M_AXIS) {
+      const float D = fmaxf(fabsf(__fsub_rn(jmax[0], lo)), fabsf(__fsub_rn(jmin[0], hi)));
+      e += half_ulp_f(D) + F.kxdb;
+    }
+    a2 = __fmaf_ru(e, e, a2);
+  }
+  return __fmul_ru(__fmul_ru(F.S, __fsqrt_ru(a2)), 1.0f + 0x1p-12f) + 0x1p-28f;
 }
 
 // Guard words on each side of a shared-memory histogram copy: the increments
@@ -1149,7 +1189,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
 // instances; such items are the diagonal of a species block).
 template <int V, bool MULTI, int RI>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
-                         uint32_t* q, int tid, int lane, unsigned& ndeferred, const float4* img) {
+                         uint32_t* q, int tid, int lane, unsigned& ndeferred, const float4* img, const float* tbeta) {
   FastParams P;
   load_fast_params(*F, it.pass, P);
   if (V == V_ORTHO || V == V_TRIC) {
@@ -1159,7 +1199,8 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
       const float3 kt = make_float3(im.x, im.y, im.z);
       int mode = (int)im.w;
       if (it.masked && mode >= M_AXIS) mode = M_PAIR;
-      set_bound(*F, P, mode);
+      if (V == V_TRIC && mode >= M_UNI) set_bound_beta(*F, P, tbeta[c]);  // the tile's own beta
+      else set_bound(*F, P, mode);
 #define DH_TILE(M_, K_) run_tile<V, M_, MULTI, RI, K_>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je)
       if (it.masked) {
         if (mode == M_UNI) DH_TILE(true, M_UNI);
@@ -1352,6 +1393,7 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
   // per j sub-chunk: j min xyz, j max xyz; per warp and sub-chunk: the tile image
   __shared__ float s_bnd[kTileImage ? kTile / kSubJ : 1][6];
   __shared__ float4 s_img[kTileImage ? BLOCK / 32 : 1][kTileImage ? kTile / kSubJ : 1];
+  __shared__ float s_beta[V == V_TRIC ? BLOCK / 32 : 1][V == V_TRIC ? kTile / kSubJ : 1];  // triclinic tile beta
   static_assert(!kTileImage || BLOCK / 32 >= kTile / kSubJ, "one warp per j sub-chunk");
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1458,8 +1500,11 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
         for (int c = 0; c * kSubJ < it.nj; ++c) {
           float4 img = make_float4(0.f, 0.f, 0.f, 0.f);
           if (ni_w > 0) img = tile_image<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3);
+          float tb = 0.0f;
+          if (V == V_TRIC && img.w >= (float)M_UNI) tb = tric_tile_beta(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3, img);
           if (lane == 0) {
             s_img[warp][c] = img;
+            if (V == V_TRIC) s_beta[warp][c] = tb;
             const unsigned long long np =
                 (unsigned long long)ni_w * (unsigned long long)(min(it.nj, (c + 1) * kSubJ) - c * kSubJ);
             if (img.w == (float)M_UNI) atomicAdd(&it.fd->uniform_pairs, np);
@@ -1469,7 +1514,8 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
         __syncwarp();
       }
       unsigned ndef = 0;
-      run_item<V, MULTI, RI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, s_img[kTileImage ? warp : 0]);
+      run_item<V, MULTI, RI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, s_img[kTileImage ? warp : 0],
+                             s_beta[V == V_TRIC ? warp : 0]);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();

@@ -27,7 +27,7 @@ namespace {
 
 // Scratch layout (bytes, each part 256-byte aligned).
 constexpr size_t kNaCtl = 256;                                  // Control
-constexpr size_t kNaFrame = 1024;                               // FrameDev
+constexpr size_t kNaFrame = 2048;                               // FrameDev
 constexpr size_t kNaJob = 256;                                  // StageJob
 constexpr size_t kNaSegs = 16 * 1024;                           // Segment[] (256 of them)
 constexpr size_t kNaT = ((size_t)DH_NOALLOC_MAX_BINS + 1) * 16; // thresholds + float-pair copy
