@@ -50,6 +50,10 @@ struct FrameDev {
   float tserr[27][3];   // |tshift - (-B k)|, rounded up
   float convf[3];       // binary64 input: per-axis conversion error (conv), rounded up
   float kxdb;           // triclinic: largest |kx| times |ax32 - ax|, rounded up
+  float dBf[9];         // |B32 - B| per entry, rounded up
+  float tie_t[3];       // orthorhombic: t-space tie term of one wrapped axis (0: none), rounded up
+  float tie_all;        // orthorhombic: the frame's tie term (all axes wrapped), rounded up
+  float rr2;            // orthorhombic: (r_max (1 + 2/nbins))^2, rounded up
   double eps_S;      // |S - nbins/r_max| / (nbins/r_max)
   double eps_S2;     // |S2 - (nbins/r_max)^2| / (nbins/r_max)^2
   // ---- written on the device

@@ -366,14 +366,20 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
   double tie_w[3] = {0, 0, 0};
   for (int c = 0; c < 3; ++c) {
     F.tie_m[c] = 0.0f;
+    F.tie_t[c] = 0.0f;
     F.convf[c] = __double2float_ru(conv[c]);
   }
   F.kxdb = 0.0f;
+  F.tie_all = 0.0f;
+  F.rr2 = 0.0f;
   int all_defer = 0;
   float eps_s = 0.0f;
   const double* B = F.B;
   double dB[9];
-  for (int q = 0; q < 9; ++q) dB[q] = fabs((double)F.Bf[q] - B[q]);
+  for (int q = 0; q < 9; ++q) {
+    dB[q] = fabs((double)F.Bf[q] - B[q]);
+    F.dBf[q] = __double2float_ru(dB[q]);
+  }
   if (F.variant == V_ORTHO) {
     double Lmin = INFINITY, tie_c[3];
     for (int c = 0; c < 3; ++c) {
@@ -409,7 +415,10 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     for (int w = 0; w < 3; ++w) {
       for (int c = 0; c < 3; ++c) aw[w][c] = c == w ? a[c] : au[c];
       tie_w[w] = tie > 0.0 ? S * tie_c[w] * 1.01 : 0.0;
+      F.tie_t[w] = __double2float_ru(tie_w[w]);
     }
+    F.tie_all = __double2float_ru(tie);
+    F.rr2 = __double2float_ru(rr * rr);
   } else if (F.variant == V_TRIC) {
     // sequential wrap along c, then b, then a (Eq. 5 below half the plane spacing);
     // D are the largest magnitudes of the intermediates, K the largest |k|
@@ -577,28 +586,86 @@ __device__ __forceinline__ float half_ulp_f(float X) {
   return __uint_as_float(__float_as_uint(X) & 0x7f800000u) * 0x1p-24f;
 }
 
-// beta of one triclinic tile in a shifted mode (img = (kx, ky, kz, mode), kx = 0
-// for M_AXIS), from the tile's own magnitudes instead of the frame's largest:
-// x'_i = fl(x_i - tshift) rounds at half an ulp of the largest |x'_i| of the
-// warp's run (fl is monotone, so the run's bounds give it), tshift errs by
-// tserr, and binary64 input adds its conversion error; in M_AXIS the x
-// difference before its wrap rounds at half an ulp of its largest magnitude and
-// the wrap adds |kx| |ax32 - ax|.  These replace the frame-wide terms of beta_u
-// and beta_w[0] (which bound them), with the same outer factors.
-__device__ float tric_tile_beta(const FrameDev& F, const float* imin, const float* imax, const float* jmin,
-                                const float* jmax, float4 img) {
-  const int m = 9 * (int)(img.x + 1.0f) + 3 * (int)(img.y + 1.0f) + (int)(img.z + 1.0f);
-  float a2 = 0.0f;
-  for (int c = 0; c < 3; ++c) {
-    const float lo = __fsub_rn(imin[c], F.tshift[m][c]), hi = __fsub_rn(imax[c], F.tshift[m][c]);
-    float e = half_ulp_f(fmaxf(fabsf(lo), fabsf(hi))) + F.tserr[m][c] + F.convf[c];
-    if (c == 0 && img.w >= (float)M_AXIS) {
-      const float D = fmaxf(fabsf(__fsub_rn(jmax[0], lo)), fabsf(__fsub_rn(jmin[0], hi)));
-      e += half_ulp_f(D) + F.kxdb;
+// Largest |k| = |nint(d/L)| over |d| <= D, with room for the float32 roundings.
+__device__ __forceinline__ float k_bound(float D, float inv) {
+  return floorf(__fmaf_ru(D, inv * (1.0f + 0x1p-16f), 0.5f + 0x1p-16f));
+}
+
+// beta of one tile (img = (kx, ky, kz, mode) from tile_image) from the tile's
+// own magnitudes instead of the frame's largest: the terms of frame_setup_kernel
+// with each coordinate range, intermediate and image bound taken over the warp
+// run and the j sub-chunk (imin..jmax).  Every float32 value of the tile lies
+// between the rounded extreme differences (rounding is monotone), so half an ulp
+// of the larger bound covers each rounding.  Orthorhombic: uniform axes err by
+// |k| |L32 - L|, wrapped axes by the rounding of d = xj - xi and |k| |L32 - L|;
+// the tie term of a wrapped axis a is kept only when some pair of the tile
+// could lie within r_max (1 + 2/nbins) with |d'_a| near L_a/2, judged from the
+// smallest displacements on the uniform axes.  Triclinic, shifted modes:
+// x'_i = fl(x_i - tshift) rounds at half an ulp of the run's largest |x'|,
+// tshift errs by tserr; in M_AXIS the x difference before its wrap rounds at
+// half an ulp of its largest magnitude and the wrap adds |kx| |ax32 - ax|.
+// Triclinic, per-pair images: the sequential wrap's intermediates.  Each is
+// bounded by the frame's counterpart, so the result never exceeds the frame's
+// beta of the mode; the outer factors are the same.
+template <int V>
+__device__ float tile_beta(const FrameDev& F, const float* imin, const float* imax, const float* jmin,
+                           const float* jmax, float4 img) {
+  const int mode = (int)img.w;
+  const float kk[3] = {img.x, img.y, img.z};
+  float a[3], tie = 0.0f;
+  if (V == V_ORTHO) {
+    if (mode == M_UNI) return F.beta_u;
+    float mn2 = 0.0f;  // smallest squared displacement over the uniform axes (rounded down)
+    for (int c = 0; c < 3; ++c) {
+      if (mode == M_PAIR || mode == M_AXIS + c) {
+        const float D = fmaxf(fabsf(__fsub_rn(jmin[c], imax[c])), fabsf(__fsub_rn(jmax[c], imin[c])));
+        a[c] = half_ulp_f(D) + k_bound(D, F.invf[c]) * F.dBf[4 * c] + F.convf[c];
+      } else {
+        a[c] = fabsf(kk[c]) * F.dBf[4 * c] + F.convf[c];
+        // exact displacements lie in [jmin - imax, jmax - imin] - k L, L within dBf of L32
+        const float kL = kk[c] * F.Bf[4 * c];
+        const float lo = __fsub_rd(__fsub_rd(jmin[c], imax[c]), kL) - F.dBf[4 * c];
+        const float hi = __fsub_ru(__fsub_ru(jmax[c], imin[c]), kL) + F.dBf[4 * c];
+        const float m = (lo > 0.0f) ? lo : (hi < 0.0f ? -hi : 0.0f);
+        mn2 = __fmaf_rd(m, m, mn2);
+      }
     }
-    a2 = __fmaf_ru(e, e, a2);
+    if (mode == M_PAIR) {
+      tie = F.tie_all;
+    } else {
+      const int w = mode - M_AXIS;
+      const float h = __fmul_rd(0.5f * F.Bf[4 * w], 1.0f - 0x1p-10f);
+      if (__fmaf_rd(h, h, mn2) <= F.rr2) tie = F.tie_t[w];
+    }
+  } else {
+    if (mode >= M_UNI) {
+      const int m = 9 * (int)(kk[0] + 1.0f) + 3 * (int)(kk[1] + 1.0f) + (int)(kk[2] + 1.0f);
+      for (int c = 0; c < 3; ++c) {
+        const float lo = __fsub_rn(imin[c], F.tshift[m][c]), hi = __fsub_rn(imax[c], F.tshift[m][c]);
+        a[c] = half_ulp_f(fmaxf(fabsf(lo), fabsf(hi))) + F.tserr[m][c] + F.convf[c];
+        if (c == 0 && mode >= M_AXIS) {
+          const float D = fmaxf(fabsf(__fsub_rn(jmax[0], lo)), fabsf(__fsub_rn(jmin[0], hi)));
+          a[0] += half_ulp_f(D) + F.kxdb;
+        }
+      }
+    } else {
+      float D[3];
+      for (int c = 0; c < 3; ++c)
+        D[c] = fmaxf(fabsf(__fsub_rn(jmin[c], imax[c])), fabsf(__fsub_rn(jmax[c], imin[c])));
+      const float* b = F.Bf;
+      const float Kz = k_bound(D[2], F.invf[2]);
+      const float D1x = __fmaf_ru(Kz, fabsf(b[2]), D[0]), D1y = __fmaf_ru(Kz, fabsf(b[5]), D[1]);
+      const float Ky = k_bound(D1y, F.invf[1]);
+      const float D2x = __fmaf_ru(Ky, fabsf(b[1]), D1x);
+      const float Kx = k_bound(D2x, F.invf[0]);
+      a[0] = half_ulp_f(D[0]) + half_ulp_f(D1x) + half_ulp_f(D2x) + Kz * F.dBf[2] + Ky * F.dBf[1] +
+             Kx * F.dBf[0] + F.convf[0];
+      a[1] = half_ulp_f(D[1]) + half_ulp_f(D1y) + Kz * F.dBf[5] + Ky * F.dBf[4] + F.convf[1];
+      a[2] = half_ulp_f(D[2]) + Kz * F.dBf[8] + F.convf[2];
+    }
   }
-  return __fmul_ru(__fmul_ru(F.S, __fsqrt_ru(a2)), 1.0f + 0x1p-12f) + 0x1p-28f;
+  const float a2 = __fmaf_ru(a[2], a[2], __fmaf_ru(a[1], a[1], __fmul_ru(a[0], a[0])));
+  return __fadd_ru(__fmul_ru(__fmul_ru(F.S, __fsqrt_ru(a2)), 1.0f + 0x1p-12f), tie) + 0x1p-28f;
 }
 
 // Guard words on each side of a shared-memory histogram copy: the increments
@@ -1199,7 +1266,8 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
       const float3 kt = make_float3(im.x, im.y, im.z);
       int mode = (int)im.w;
       if (it.masked && mode >= M_AXIS) mode = M_PAIR;
-      if (V == V_TRIC && mode >= M_UNI) set_bound_beta(*F, P, tbeta[c]);  // the tile's own beta
+      // the tile's own beta; masked tiles demoted to per-pair images take the frame's
+      if (mode == (int)im.w) set_bound_beta(*F, P, tbeta[c]);
       else set_bound(*F, P, mode);
 #define DH_TILE(M_, K_) run_tile<V, M_, MULTI, RI, K_>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je)
       if (it.masked) {
@@ -1393,7 +1461,7 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
   // per j sub-chunk: j min xyz, j max xyz; per warp and sub-chunk: the tile image
   __shared__ float s_bnd[kTileImage ? kTile / kSubJ : 1][6];
   __shared__ float4 s_img[kTileImage ? BLOCK / 32 : 1][kTileImage ? kTile / kSubJ : 1];
-  __shared__ float s_beta[V == V_TRIC ? BLOCK / 32 : 1][V == V_TRIC ? kTile / kSubJ : 1];  // triclinic tile beta
+  __shared__ float s_beta[kTileImage ? BLOCK / 32 : 1][kTileImage ? kTile / kSubJ : 1];  // per-tile beta
   static_assert(!kTileImage || BLOCK / 32 >= kTile / kSubJ, "one warp per j sub-chunk");
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1500,11 +1568,10 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
         for (int c = 0; c * kSubJ < it.nj; ++c) {
           float4 img = make_float4(0.f, 0.f, 0.f, 0.f);
           if (ni_w > 0) img = tile_image<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3);
-          float tb = 0.0f;
-          if (V == V_TRIC && img.w >= (float)M_UNI) tb = tric_tile_beta(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3, img);
+          const float tb = tile_beta<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3, img);
           if (lane == 0) {
             s_img[warp][c] = img;
-            if (V == V_TRIC) s_beta[warp][c] = tb;
+            s_beta[warp][c] = tb;
             const unsigned long long np =
                 (unsigned long long)ni_w * (unsigned long long)(min(it.nj, (c + 1) * kSubJ) - c * kSubJ);
             if (img.w == (float)M_UNI) atomicAdd(&it.fd->uniform_pairs, np);
@@ -1515,7 +1582,7 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
       }
       unsigned ndef = 0;
       run_item<V, MULTI, RI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, s_img[kTileImage ? warp : 0],
-                             s_beta[V == V_TRIC ? warp : 0]);
+                             s_beta[kTileImage ? warp : 0]);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();
