@@ -240,9 +240,19 @@ dh_status dh_tune_cache_count(const char* path, int32_t sm_count, int32_t* n_ent
  *    binary64 (definition) and delta is the frame's decision window (must be
  *    < 1); out[1] = sampled pairs the float32 path would decide whose bin differs
  *    from the binary64 bin (must be 0); out[2] = pairs compared; out[3] = delta.
+ *  what = DH_CHECK_TILES (orthorhombic or triclinic frames without search):
+ *    stages `frame` and draws n_samples tiles with splitmix64 from `seed`, each
+ *    a run of 128 consecutive particles against a run of 256 (the pair kernel's
+ *    warp tiles, in the staged order); every pair of a tile is evaluated in the
+ *    tile's image mode with the tile's own window, as the pair kernel does:
+ *    out[0] = largest |t32 - t64| / (alpha t64 + beta_tile) (must be < 1),
+ *    out[1] = pairs decided in float32 with a bin other than the binary64 one
+ *    (must be 0), out[2] = pairs compared, out[3] = tiles drawn that took a
+ *    shifted (uniform or one-axis) mode.  DH_ERR_INVALID for other boxes.
  * out must hold 4 doubles.  Synchronous. */
 #define DH_CHECK_SQRT 0
 #define DH_CHECK_WINDOW 1
+#define DH_CHECK_TILES 2
 dh_status dh_selfcheck(dh_ctx* ctx, int32_t what, const dh_frame* frame, uint64_t n_samples, uint64_t seed,
                        double* out);
 

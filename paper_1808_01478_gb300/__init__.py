@@ -111,6 +111,7 @@ DH_NOALLOC_MAX_BINS = 65536
 
 DH_CHECK_SQRT = 0
 DH_CHECK_WINDOW = 1
+DH_CHECK_TILES = 2
 
 
 def load_library(path: str | None = None) -> ctypes.CDLL:
@@ -383,6 +384,12 @@ class Context:
         out = dh_selfcheck(self.handle, DH_CHECK_WINDOW, fa.frame, n_samples, seed)
         return {"max_ratio": float(out[0]), "violations": int(out[1]), "checked": int(out[2]),
                 "delta": float(out[3])}
+
+    def check_tiles(self, coords, offsets, box_type, box, r_max, nbins, n_tiles=4096, seed=1) -> dict:
+        fa = FrameArgs(coords, offsets, box_type, box, r_max, nbins)
+        out = dh_selfcheck(self.handle, DH_CHECK_TILES, fa.frame, n_tiles, seed)
+        return {"max_ratio": float(out[0]), "violations": int(out[1]), "checked": int(out[2]),
+                "shifted_tiles": int(out[3])}
 
     # served path: the buffers of a submitted request are held here until its
     # final status has been reported (the library reads and writes them until then)

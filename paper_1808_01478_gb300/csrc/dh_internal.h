@@ -149,6 +149,8 @@ cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* s
 // One pair-kernel launch over segments whose frames all have minimum-image variant `variant`.
 cudaError_t launch_pairs(const PairLaunch& p, int variant, int grid, size_t smem, cudaStream_t stream);
 cudaError_t launch_check_sqrt(unsigned long long* out, cudaStream_t stream);
+cudaError_t launch_check_tiles(const FrameDev* F, int variant, uint64_t n_tiles, uint64_t seed,
+                               unsigned long long* out, cudaStream_t stream);
 cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t seed, unsigned long long* out,
                                 cudaStream_t stream);
 cudaError_t launch_rdf(const uint64_t* counts, int32_t n_hist, int32_t nbins, double r_max,

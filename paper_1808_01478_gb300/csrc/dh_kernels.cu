@@ -1700,6 +1700,134 @@ cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t 
   return cudaGetLastError();
 }
 
+// The tile modes against their own bounds: one pair of a tile evaluated with the
+// arithmetic of run_tile in mode MODE (coordinates shifted by the tile's images,
+// then decide_arith2 with the tile's bound), against the binary64 bin.
+template <int V, int MODE>
+__device__ void check_tile_pair(const FrameDev& F, const FastParams& P, float beta, float3 kt, int i, int j,
+                                double* worst, unsigned long long* viol, unsigned long long* checked) {
+  const float4 pi = F.X[i], pj = F.X[j];
+  float3 ti = make_float3(0.f, 0.f, 0.f), sj = make_float3(0.f, 0.f, 0.f);
+  if (V == V_ORTHO && MODE >= M_UNI) {
+    ti = make_float3(kt.x < 0.f ? P.b[0] : 0.f, kt.y < 0.f ? P.b[4] : 0.f, kt.z < 0.f ? P.b[8] : 0.f);
+    sj = make_float3(kt.x > 0.f ? P.b[0] : 0.f, kt.y > 0.f ? P.b[4] : 0.f, kt.z > 0.f ? P.b[8] : 0.f);
+  } else if (V == V_TRIC && MODE >= M_UNI) {
+    const float* v = F.tshift[9 * (int)(kt.x + 1.0f) + 3 * (int)(kt.y + 1.0f) + (int)(kt.z + 1.0f)];
+    ti = make_float3(v[0], v[1], v[2]);
+  }
+  const float2 dx = bc2(__fsub_rn(__fsub_rn(pj.x, sj.x), __fsub_rn(pi.x, ti.x)));
+  const float2 dy = bc2(__fsub_rn(__fsub_rn(pj.y, sj.y), __fsub_rn(pi.y, ti.y)));
+  const float2 dz = bc2(__fsub_rn(__fsub_rn(pj.z, sj.z), __fsub_rn(pi.z, ti.z)));
+  float2 sm, e, bound;
+  decide_arith2<V, false, MODE>(dx, dy, dz, P, (float)(P.hi + 1), 0.0f, sm, e, bound);
+  bool amb0 = false, amb1 = false;
+  const float q = __fmul_rn(wrap_r2_2<V, MODE>(dx, dy, dz, P, amb0, amb1).x, P.S2);
+  const double r2 = exact_r2<V>(F, coords64(F, i), coords64(F, j));
+  const int k64 = bin_from_thresholds(F.T, F.S, F.nbins, r2);
+  const double t64 = __dmul_rn(__dsqrt_rn(r2), (double)F.nbins / F.r_max);
+  if (t64 < (double)F.nbins + 1.0 && isfinite(q)) {
+    *worst = fmax(*worst, fabs(__dsqrt_rn((double)q) - t64) / ((double)F.alpha_t * t64 + (double)beta));
+    ++*checked;
+  }
+  if (!(fabsf(e.x) <= bound.x)) {
+    const uint32_t rel = __float_as_uint(sm.x) + (__float_as_uint(e.x) >> 31) - (uint32_t)P.kb1;
+    const int k32 = rel > (uint32_t)F.nbins ? F.nbins : (int)rel;
+    if (k32 != k64) ++*viol;
+  }
+}
+
+// One block per sampled tile: a run of 128 consecutive particles (the i's of one
+// warp of a 256-thread block) and a j sub-chunk of kSubJ, at random aligned
+// starts.  out[0] = largest |t32 - t64| / (alpha t64 + beta_tile) (must be < 1),
+// out[1] = pairs decided in float32 with a bin other than the binary64 one (must
+// be 0), out[2] = pairs compared, out[3] = sampled tiles in a shifted mode.
+template <int V>
+__global__ void check_tiles_kernel(const FrameDev* Fp, uint64_t n_tiles, uint64_t seed, unsigned long long* out) {
+  const FrameDev& F = *Fp;
+  FastParams P;
+  load_fast_params(F, 0, P);
+  P.width = (uint32_t)F.nbins;
+  P.hi = F.nbins;
+  __shared__ float s_b[8][6];
+  __shared__ float s_bnd[12];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double worst = 0.0;
+  unsigned long long viol = 0, checked = 0, shifted = 0;
+  const int ni = min(128, F.n), nj = min(kSubJ, F.n);
+  for (uint64_t s = blockIdx.x; s < n_tiles; s += gridDim.x) {
+    const uint64_t h = mix64(seed ^ mix64(s));
+    const int i0 = (int)((h % (uint64_t)((F.n - ni) / 128 + 1)) * 128);
+    const int j0 = (int)(((h >> 32) % (uint64_t)((F.n - nj) / kSubJ + 1)) * kSubJ);
+    for (int part = 0; part < 2; ++part) {  // bounds of the i run, then of the j chunk
+      const int b0 = part ? j0 : i0, nb = part ? nj : ni;
+      float m[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+      for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        const float4 v = F.X[b0 + k];
+        m[0] = fminf(m[0], v.x); m[1] = fminf(m[1], v.y); m[2] = fminf(m[2], v.z);
+        m[3] = fmaxf(m[3], v.x); m[4] = fmaxf(m[4], v.y); m[5] = fmaxf(m[5], v.z);
+      }
+      for (int o = 16; o > 0; o >>= 1)
+        for (int a = 0; a < 6; ++a) {
+          const float other = __shfl_xor_sync(kFull, m[a], o);
+          m[a] = a < 3 ? fminf(m[a], other) : fmaxf(m[a], other);
+        }
+      if (lane == 0)
+        for (int a = 0; a < 6; ++a) s_b[warp][a] = m[a];
+      __syncthreads();
+      if (threadIdx.x < 6) {
+        float v = s_b[0][threadIdx.x];
+        for (int w = 1; w < 8; ++w)
+          v = threadIdx.x < 3 ? fminf(v, s_b[w][threadIdx.x]) : fmaxf(v, s_b[w][threadIdx.x]);
+        s_bnd[6 * part + threadIdx.x] = v;
+      }
+      __syncthreads();
+    }
+    const float4 img = tile_image<V>(F, s_bnd, s_bnd + 3, s_bnd + 6, s_bnd + 9);
+    const float beta = tile_beta<V>(F, s_bnd, s_bnd + 3, s_bnd + 6, s_bnd + 9, img);
+    FastParams Q = P;
+    set_bound_beta(F, Q, beta);
+    const float3 kt = make_float3(img.x, img.y, img.z);
+    if (threadIdx.x == 0 && img.w >= (float)M_UNI) ++shifted;
+    for (int k = threadIdx.x; k < ni * nj; k += blockDim.x) {
+      const int i = i0 + k % ni, j = j0 + k / ni;
+      if (i == j) continue;
+      switch ((int)img.w) {
+        case M_UNI: check_tile_pair<V, M_UNI>(F, Q, beta, kt, i, j, &worst, &viol, &checked); break;
+        case M_AXIS + 0: check_tile_pair<V, M_AXIS + 0>(F, Q, beta, kt, i, j, &worst, &viol, &checked); break;
+        case M_AXIS + 1:
+          if (V == V_ORTHO) check_tile_pair<V, M_AXIS + 1>(F, Q, beta, kt, i, j, &worst, &viol, &checked);
+          break;
+        case M_AXIS + 2:
+          if (V == V_ORTHO) check_tile_pair<V, M_AXIS + 2>(F, Q, beta, kt, i, j, &worst, &viol, &checked);
+          break;
+        default: check_tile_pair<V, M_PAIR>(F, Q, beta, kt, i, j, &worst, &viol, &checked); break;
+      }
+    }
+    __syncthreads();  // s_b, s_bnd are rewritten by the next tile
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    worst = fmax(worst, __shfl_xor_sync(kFull, worst, o));
+    viol += __shfl_xor_sync(kFull, viol, o);
+    checked += __shfl_xor_sync(kFull, checked, o);
+    shifted += __shfl_xor_sync(kFull, shifted, o);
+  }
+  if (lane == 0) {
+    atomicMax(out, (unsigned long long)__double_as_longlong(worst));
+    atomicAdd(out + 1, viol);
+    atomicAdd(out + 2, checked);
+    atomicAdd(out + 3, shifted);
+  }
+}
+
+cudaError_t launch_check_tiles(const FrameDev* F, int variant, uint64_t n_tiles, uint64_t seed,
+                               unsigned long long* out, cudaStream_t stream) {
+  if (variant == V_ORTHO) check_tiles_kernel<V_ORTHO><<<456, 256, 0, stream>>>(F, n_tiles, seed, out);
+  else if (variant == V_TRIC) check_tiles_kernel<V_TRIC><<<456, 256, 0, stream>>>(F, n_tiles, seed, out);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+
 // ------------------------------------------------------------------ g(r), Eq. 1
 
 // g = (counts / n_frames) / (pair density x shell volume) per bin, binary64.

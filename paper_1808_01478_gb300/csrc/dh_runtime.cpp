@@ -984,10 +984,14 @@ dh_status selfcheck(dh_ctx* c, int32_t what, const dh_frame* frame, uint64_t n_s
     std::memcpy(&out[0], &h[0], 8);
     return DH_OK;
   }
-  if (what != DH_CHECK_WINDOW || !frame) return fail(DH_ERR_INVALID, "unknown self check %d", what);
+  if ((what != DH_CHECK_WINDOW && what != DH_CHECK_TILES) || !frame)
+    return fail(DH_ERR_INVALID, "unknown self check %d", what);
   std::vector<PlannedFrame> pfs(1);
   dh_status s = check_frame(frame, pfs[0], c->max_width);
   if (s != DH_OK) return s;
+  if (what == DH_CHECK_TILES && ((pfs[0].variant != V_ORTHO && pfs[0].variant != V_TRIC) || pfs[0].big_box ||
+                                 frame->n < 2))
+    return fail(DH_ERR_INVALID, "the tile check needs an orthorhombic or triclinic frame without search");
   bool dev = (frame->flags & DH_DEVICE_PTRS) != 0;
   std::vector<uint64_t*> dev_out(1);
   DH_CUDA_TRY(c->hist.ensure(sizeof(uint64_t) * (size_t)pfs[0].n_hist * frame->nbins));
@@ -995,7 +999,11 @@ dh_status selfcheck(dh_ctx* c, int32_t what, const dh_frame* frame, uint64_t n_s
   DH_CUDA_TRY(cudaMemsetAsync(c->tstat.p, 0, sizeof(int32_t), st));
   s = enqueue_frames(c, pfs, dev_out, !dev, false);
   if (s == DH_OK) {
-    cudaError_t e = launch_check_window((const FrameDev*)c->meta.p, n_samples, seed, (unsigned long long*)res.p, st);
+    cudaError_t e =
+        what == DH_CHECK_TILES
+            ? launch_check_tiles((const FrameDev*)c->meta.p, pfs[0].variant, n_samples, seed,
+                                 (unsigned long long*)res.p, st)
+            : launch_check_window((const FrameDev*)c->meta.p, n_samples, seed, (unsigned long long*)res.p, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, res.p, sizeof h, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) s = fail(DH_ERR_CUDA, "self check: %s", cudaGetErrorString(e));
   }
@@ -1012,7 +1020,7 @@ dh_status selfcheck(dh_ctx* c, int32_t what, const dh_frame* frame, uint64_t n_s
   out[0] = worst;
   out[1] = (double)h[1];
   out[2] = (double)h[2];
-  out[3] = (double)((FrameDev*)c->hmeta.p)->delta;
+  out[3] = what == DH_CHECK_TILES ? (double)h[3] : (double)((FrameDev*)c->hmeta.p)->delta;
   return DH_OK;
 }
 

@@ -52,6 +52,34 @@ def test_window_bound_holds(ctx, name):
     assert res["max_ratio"] < 1.0, res
 
 
+TILE_FRAMES = {
+    "ortho_c2": lambda: w.config_ortho_two_species(seed=1),
+    "tric_c3": lambda: w.config_triclinic_clusters(seed=1),
+    "headline_ortho": lambda: w.headline_frame(w.BOX_ORTHO, seed=12),
+    "headline_tric": lambda: w.headline_frame(w.BOX_TRICLINIC, seed=13),
+    "ortho_small_box": lambda: w.uniform_frame(17, 60000, w.BOX_ORTHO, w.ortho_box(30.0, 26.0, 34.0), 12.9, 4000),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TILE_FRAMES))
+def test_tile_mode_windows_hold(ctx, name):
+    # every pair of sampled warp tiles, in the tile's image mode with its own
+    # window (uniform, one axis wrapped, or per pair), against binary64
+    f = TILE_FRAMES[name]()
+    res = ctx.check_tiles(f.coords, f.offsets, f.box_type, f.box, f.r_max, f.nbins, n_tiles=4096, seed=9)
+    assert res["checked"] > 1 << 24
+    assert res["shifted_tiles"] > 0, res
+    assert res["violations"] == 0, res
+    assert res["max_ratio"] < 1.0, res
+
+
+def test_tile_check_rejects_other_boxes(ctx):
+    f = w.config_small_nobox(seed=1)
+    with pytest.raises(dh.DHError) as e:
+        ctx.check_tiles(f.coords, f.offsets, f.box_type, f.box, f.r_max, f.nbins)
+    assert e.value.status == dh.DH_ERR_INVALID
+
+
 def _f64(f):
     # the same frame with binary64 coordinates that are not float32 values
     x = f.coords.astype(np.float64) + w.rng_for(5).random(f.coords.shape) * 1e-5
