@@ -72,6 +72,10 @@ class OracleLib:
         lib.dh_oracle_pairs_r2_f64.restype = None
         lib.dh_oracle_rdf.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P, ctypes.c_uint64, P]
         lib.dh_oracle_rdf.restype = None
+        lib.dh_oracle_histogram_one.argtypes = [P, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_int32, P, ctypes.c_double, ctypes.c_int32, P,
+                                                 ctypes.c_int32]
+        lib.dh_oracle_histogram_one.restype = ctypes.c_int
         lib.dh_oracle_max_threads.argtypes = []
         lib.dh_oracle_max_threads.restype = ctypes.c_int
         self.lib = lib
@@ -93,6 +97,20 @@ class OracleLib:
         nt = self.max_threads() if nthreads is None else int(nthreads)
         fn = self.lib.dh_oracle_histogram_f64 if f64 else self.lib.dh_oracle_histogram
         rc = fn(_ptr(x), x.shape[0], _ptr(off), s, int(box_type), _ptr(bx), float(r_max), int(nbins), _ptr(out), nt)
+        if rc != 0:
+            raise ValueError(f"oracle rejected the frame (code {rc})")
+        return out
+
+    def histogram_one(self, coords, offsets, box_type, box, r_max, nbins, a: int, c: int,
+                      nthreads: int | None = None) -> np.ndarray:
+        """The histogram of species pair (a, c), a <= c, alone (float32 coordinates), shape (nbins,)."""
+        x = np.ascontiguousarray(coords, dtype=np.float32).reshape(-1, 3)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        bx = _box9(box)
+        out = np.zeros(int(nbins), dtype=np.uint64)
+        nt = self.max_threads() if nthreads is None else int(nthreads)
+        rc = self.lib.dh_oracle_histogram_one(_ptr(x), x.shape[0], _ptr(off), off.shape[0] - 1, int(a), int(c),
+                                              int(box_type), _ptr(bx), float(r_max), int(nbins), _ptr(out), nt)
         if rc != 0:
             raise ValueError(f"oracle rejected the frame (code {rc})")
         return out
@@ -160,6 +178,10 @@ def max_threads() -> int:
 
 def histogram(coords, offsets, box_type, box, r_max, nbins, nthreads: int | None = None):
     return default().histogram(coords, offsets, box_type, box, r_max, nbins, nthreads)
+
+
+def histogram_one(coords, offsets, box_type, box, r_max, nbins, a: int, c: int, nthreads: int | None = None):
+    return default().histogram_one(coords, offsets, box_type, box, r_max, nbins, a, c, nthreads)
 
 
 def histogram_frame(frame, nthreads: int | None = None):

@@ -185,9 +185,35 @@ int histogram_all(const T* coords, int64_t n, const int64_t* offsets, int32_t n_
   return 0;
 }
 
+// One species-pair histogram (a <= c) of a frame, the same loops as histogram_all.
+template <typename T>
+int histogram_one(const T* coords, int64_t n, const int64_t* offsets, int32_t n_species, int32_t a, int32_t c,
+                  int32_t box_type, const double* box, double r_max, int32_t nbins, uint64_t* out,
+                  int32_t nthreads) {
+  if (n < 0 || n_species < 1 || nbins < 1 || !(r_max > 0.0)) return -1;
+  if (box_type < BOX_NONE || box_type > BOX_TRICLINIC) return -1;
+  if (a < 0 || c < a || c >= n_species) return -1;
+  if (offsets[0] != 0 || offsets[n_species] != n) return -1;
+  for (int32_t s = 0; s < n_species; ++s)
+    if (offsets[s + 1] < offsets[s]) return -1;
+  double zero[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  Box b = make_box(box_type, box ? box : zero);
+  std::memset(out, 0, sizeof(uint64_t) * (size_t)nbins);
+  histogram_pair(coords, offsets[a], offsets[a + 1], offsets[c], offsets[c + 1], a == c, b, r_max, nbins, out,
+                 nthreads);
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
+
+// the histogram of species pair (a, c), a <= c, alone (float32 coordinates, n x 3)
+int dh_oracle_histogram_one(const float* coords, int64_t n, const int64_t* offsets, int32_t n_species, int32_t a,
+                            int32_t c, int32_t box_type, const double* box, double r_max, int32_t nbins,
+                            uint64_t* out, int32_t nthreads) {
+  return histogram_one(coords, n, offsets, n_species, a, c, box_type, box, r_max, nbins, out, nthreads);
+}
 
 // float32 coordinates (n x 3)
 int dh_oracle_histogram(const float* coords, int64_t n, const int64_t* offsets, int32_t n_species,

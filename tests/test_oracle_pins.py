@@ -102,6 +102,40 @@ def test_hand_three_species_histogram_order(oracle_mod):
     assert nz == expect
 
 
+def test_hand_single_species_pair_histogram(oracle_mod):
+    # histogram_one(a, c) is the (a, c) histogram alone: the hand-worked
+    # three-species frame above, and the two-species frame's AB pair
+    A = [[0, 0, 0], [1, 0, 0]]
+    B = [[0, 10, 0], [2, 10, 0]]
+    C = [[0, 0, 30], [3, 0, 30]]
+    x = np.array(A + B + C, dtype=np.float32)
+    d = lambda p, q: int(math.floor(math.dist(p, q)))
+    want = {(0, 1): [d(p, q) for p in A for q in B], (1, 2): [d(p, q) for p in B for q in C],
+            (2, 2): [d(C[0], C[1])]}
+    for (a, c), ds in want.items():
+        h = oracle_mod.histogram_one(x, [0, 2, 4, 6], NONE, None, 64.0, 64, a, c)
+        assert sorted(np.repeat(np.arange(64), h.astype(np.int64)).tolist()) == sorted(ds)
+    h = oracle_mod.histogram_one(np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0]], np.float32), [0, 1, 3], NONE, None,
+                                 4.0, 4, 0, 1)
+    assert h.tolist() == [0, 1, 1, 0]
+    with pytest.raises(ValueError):
+        oracle_mod.histogram_one(x, [0, 2, 4, 6], NONE, None, 64.0, 64, 1, 0)
+
+
+@pytest.mark.parametrize("box_type", [NONE, ORTHO, TRIC])
+def test_single_species_pair_matches_all_pairs(oracle_mod, box_type):
+    # each species-pair histogram alone equals its row of the full set
+    box = {NONE: None, ORTHO: w.ortho_box(9.0, 8.0, 10.0), TRIC: w.triclinic_box(9, 9, 9, *w.C3_ANGLES)}[box_type]
+    f = w.uniform_frame(71, 900, box_type, box if box is not None else w.ortho_box(9.0), 4.0, 200, n_species=3)
+    full = oracle_mod.histogram_frame(f)
+    k = 0
+    for a in range(3):
+        for c in range(a, 3):
+            one = oracle_mod.histogram_one(f.coords, f.offsets, f.box_type, f.box, f.r_max, f.nbins, a, c)
+            assert np.array_equal(one, full[k]), (a, c)
+            k += 1
+
+
 def test_empty_species_and_tiny_frames(oracle_mod):
     h = hist(oracle_mod, [[0, 0, 0], [1, 0, 0]], [0, 0, 2, 2], NONE, None, 4.0, 4)
     assert h.shape == (6, 4)
