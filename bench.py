@@ -669,10 +669,14 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         nthreads = os.cpu_count() or 1
         cb = oracle_sample(frames, args.cpu_seconds, nthreads)
+        c1 = oracle_sample(frames, args.cpu_seconds / 5.0, 1)  # the same oracle on one core
         line["cpu_baseline"] = {"value": round(cb["gpairs_s"], 6), "unit": UNIT, "cores": nthreads,
                                 "kind": "oracle",
                                 "sample": f"leading subsets N={cb['sizes']} of the three frames, "
-                                          f"{cb['pairs']} pairs in {cb['seconds']:.1f} s"}
+                                          f"{cb['pairs']} pairs in {cb['seconds']:.1f} s",
+                                "one_core": {"value": round(c1["gpairs_s"], 6), "cores": 1,
+                                             "sample": f"leading subsets N={c1['sizes']}, {c1['pairs']} pairs "
+                                                       f"in {c1['seconds']:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
