@@ -703,7 +703,7 @@ def main(argv=None) -> int:
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of measured ones")
     ap.add_argument("--c4-frames", type=int, default=256)
     ap.add_argument("--served-requests", type=int, default=200)
-    ap.add_argument("--served-loads", type=float, nargs="*", default=[0.5, 0.8])
+    ap.add_argument("--served-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95])
     ap.add_argument("--scan", action="store_true",
                     help="instead of the bench line: throughput against nbins and histogram copies")
     ap.add_argument("--scan-particles", type=int, nargs="*", default=[200_000])

@@ -512,15 +512,21 @@ bool Server::launch_wave(int v) {
   }
   if (run.empty()) return false;
   WaveSlot& W = ln.slots[slot];
-  const double budget = ln.rate * wave_seconds_;
-  const double share = budget / (double)run.size();
   const double pairs_per_item = (double)kTile * (double)kTile;
+  // Water-filling of the wave's pair budget: requests with the least work left
+  // first, each taking what it needs up to an equal share of what remains, so
+  // small requests finish in the wave they join and the rest of the budget goes
+  // to the larger ones in equal parts.
+  std::stable_sort(run.begin(), run.end(),
+                   [](const Request* a, const Request* b) { return a->n_items - a->next < b->n_items - b->next; });
+  double budget_left = ln.rate * wave_seconds_;
   std::vector<Segment> wsegs;
   int64_t witems = 0;
   int width = 1, multi = 0;
   double wpairs = 0;
   std::vector<Request*> finishing;
-  for (Request* r : run) {
+  for (size_t q = 0; q < run.size(); ++q) {
+    Request* r = run[q];
     if (!r->prepped) {
       dh_status s = prep(*r);
       if (s != DH_OK) {
@@ -529,8 +535,10 @@ bool Server::launch_wave(int v) {
         continue;
       }
     }
+    const double share = std::max(0.0, budget_left) / (double)(run.size() - q);
     int64_t take = std::max<int64_t>(1, (int64_t)(share / pairs_per_item));
     take = std::min(take, r->n_items - r->next);
+    budget_left -= (double)take * pairs_per_item;
     int64_t lo = r->next, hi = r->next + take;
     for (const Segment& sg : r->segs) {
       int64_t count = sg.intra ? (int64_t)sg.n_ti * (sg.n_ti + 1) / 2 : (int64_t)sg.n_ti * sg.n_tj;
