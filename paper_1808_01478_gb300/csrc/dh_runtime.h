@@ -88,8 +88,8 @@ struct PlannedFrame {
   uint64_t pairs;
   // binary64 input without a box runs as an orthorhombic box of side 2^60: every
   // nearest image is 0 and each wrap step an exact identity, so the histogram is
-  // the no-box one, with the orthorhombic error window (linear in the root) that
-  // suits the absolute error of the rounded input
+  // the no-box one; every tile takes the uniform image mode, whose per-tile
+  // window holds only the conversion error of the rounded input
   bool big_box = false;
 };
 
