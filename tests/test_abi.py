@@ -97,3 +97,18 @@ def test_tune_cache_file_parsing(lib, tmp_path):
     with pytest.raises(dh.DHError) as e:
         dh.dh_tune_cache_count(str(tmp_path / "missing.txt"), 152)
     assert e.value.status == dh.DH_ERR_NOTFOUND
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no CPU fallback: without libdh.so the binding raises on first use
+    import subprocess
+    import sys
+
+    code = ("import paper_1808_01478_gb300 as dh\n"
+            "try:\n    dh.Context(0)\nexcept RuntimeError as e:\n    print('raised', e)\n")
+    env = dict(os.environ, DH_LIB_PATH=str(tmp_path / "absent" / "libdh.so"))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                         timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("raised") and "libdh.so not found" in out.stdout, out.stdout
