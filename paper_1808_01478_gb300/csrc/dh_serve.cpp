@@ -38,7 +38,11 @@ using Clock = std::chrono::steady_clock;
 
 constexpr size_t kAlign = 256;
 constexpr int kWaveSlots = 4;          // waves that may be in flight at once
-constexpr int kWavesAhead = 2;         // waves kept enqueued ahead of the GPU
+// Waves in flight per lane.  One: the next wave is built when the running one
+// completes (the scheduler polls every 50 us), so a request that arrives waits
+// for the running wave only, not also for one queued behind it; the idle gap
+// per wave is a few tens of microseconds, and the other lanes fill it.
+constexpr int kWavesAhead = 1;
 constexpr double kWaveSecondsDefault = 0.006;  // target device time of one wave
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
