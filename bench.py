@@ -2,20 +2,20 @@
 
 One step = the three headline frames (N = 1,000,000 particles, 1 species,
 uniform at density 0.1, 10,000 bins; no box, orthorhombic and triclinic cell)
-through one dh_histogram_batch call (one persistent pair-kernel launch for all
-three frames), inputs resident in HBM.  Printed on one JSON line:
+through one dh_histogram_batch call (one persistent pair-kernel launch per
+minimum-image variant, replayed as a CUDA graph), inputs resident in HBM.  Printed on one JSON line:
 
   value          Gpairs/s of the batched step (device time, CUDA events)
   e2e            the same metric through the C ABI with pinned HOST buffers:
                  host->device copy of the coordinates and device->host copy of
                  the histograms inside the timed region
   plain          per-frame dh_histogram Gpairs/s for each box type
-  roofline       ALU-bound roofline of the pair kernel
+  roofline       the pair kernel's float32 operations per second against the lane peak
   cpu_baseline   the FP64 oracle on the host cores, on a bounded sample
   clocks         nvidia-smi SM clocks and throttle reasons during the timed region
 
-``--impl reference`` times the FP64 oracle (the reference arm of this build) on
-bounded samples of the same workload instead.  Under torchrun each rank runs its
+``--impl reference`` times the FP64 oracle (the reference arm) on bounded
+samples of the same workload instead.  Under torchrun each rank runs its
 own replica (frames are independent; no data-path collective) and rank 0
 reports the aggregate.
 """
