@@ -4,8 +4,8 @@
 // The paper's engine (Sec. 3.3) feeds whole frames from a reader queue to
 // worker processes.  Here one scheduler thread per context keeps the GPU busy
 // with "waves": each wave is one launch of the persistent pair kernel over a
-// slice of the work items of every admitted request (a fair share of a pair
-// budget sized for a few milliseconds).  A request that arrives while others
+// slice of the work items of every admitted request (a pair budget sized for a
+// few milliseconds, water-filled: the requests with the least work left first).  A request that arrives while others
 // run is admitted as soon as pool memory and a slot are free, and its items
 // join the next wave next to the remaining items of the running requests, so
 // small frames are not stuck behind large ones.  Each minimum-image variant
@@ -488,8 +488,8 @@ dh_status Server::finalize_enqueue(Request& r) {
   return DH_OK;
 }
 
-// One wave of lane v: a fair share of the lane's pair budget from every
-// running request of that variant, as one pair-kernel launch.
+// One wave of lane v: the lane's pair budget water-filled over the running
+// requests of that variant, as one pair-kernel launch.
 bool Server::launch_wave(int v) {
   Lane& ln = lanes_[v];
   int slot = -1;
