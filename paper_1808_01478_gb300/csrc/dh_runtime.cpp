@@ -182,8 +182,6 @@ dh_status check_frame(const dh_frame* f, PlannedFrame& pf, int max_width) {
   switch (f->box_type) {
     case DH_BOX_NONE:
       pf.variant = V_NONE;
-      pf.big_box = (f->flags & DH_COORDS_F64) != 0;
-      if (pf.big_box) pf.variant = V_ORTHO;
       break;
     case DH_BOX_ORTHO:
       for (int q = 0; q < 9; ++q) {
@@ -241,7 +239,6 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   F.r_max = f->r_max;
   for (int q = 0; q < 9; ++q) {
     F.B[q] = (f->box_type == DH_BOX_NONE) ? 0.0 : f->box[q];
-    if (pf.big_box) F.B[q] = (q == 0 || q == 4 || q == 8) ? 0x1p60 : 0.0;
     F.Bf[q] = (float)F.B[q];
     F.Bl[q] = (float)(F.B[q] - (double)F.Bf[q]);
   }
@@ -279,7 +276,7 @@ std::vector<SortSeg> plan_spatial_order(const PlannedFrame& pf, const FrameDev* 
   std::vector<SortSeg> out;
   *keys = 0;
   *chunks = 0;
-  if ((pf.variant != V_ORTHO && pf.variant != V_TRIC) || pf.big_box) return out;
+  if (pf.variant != V_ORTHO && pf.variant != V_TRIC) return out;
   const int64_t* o = pf.src->species_offsets;
   for (int a = 0; a < pf.src->n_species; ++a) {
     const int64_t na = o[a + 1] - o[a];
@@ -989,8 +986,7 @@ dh_status selfcheck(dh_ctx* c, int32_t what, const dh_frame* frame, uint64_t n_s
   std::vector<PlannedFrame> pfs(1);
   dh_status s = check_frame(frame, pfs[0], c->max_width);
   if (s != DH_OK) return s;
-  if (what == DH_CHECK_TILES && ((pfs[0].variant != V_ORTHO && pfs[0].variant != V_TRIC) || pfs[0].big_box ||
-                                 frame->n < 2))
+  if (what == DH_CHECK_TILES && ((pfs[0].variant != V_ORTHO && pfs[0].variant != V_TRIC) || frame->n < 2))
     return fail(DH_ERR_INVALID, "the tile check needs an orthorhombic or triclinic frame without search");
   bool dev = (frame->flags & DH_DEVICE_PTRS) != 0;
   std::vector<uint64_t*> dev_out(1);

@@ -86,11 +86,6 @@ struct PlannedFrame {
   int32_t sweep_width;
   double margin;
   uint64_t pairs;
-  // binary64 input without a box runs as an orthorhombic box of side 2^60: every
-  // nearest image is 0 and each wrap step an exact identity, so the histogram is
-  // the no-box one; every tile takes the uniform image mode, whose per-tile
-  // window holds only the conversion error of the rounded input
-  bool big_box = false;
 };
 
 dh_status check_frame(const dh_frame* f, PlannedFrame& pf, int max_width);
