@@ -112,3 +112,28 @@ def test_missing_library_fails_loudly(tmp_path):
                          timeout=120)
     assert out.returncode == 0, out.stderr
     assert out.stdout.startswith("raised") and "libdh.so not found" in out.stdout, out.stdout
+
+
+@pytest.mark.parametrize("cname", ["dh_config", "dh_frame", "dh_stats"])
+def test_struct_layouts_match_the_header(tmp_path, cname):
+    # the ctypes mirrors of the ABI structs against a C compiler's layout of dh.h
+    import ctypes
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    py = getattr(dh, cname)
+    fields = [name for name, _ in py._fields_]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof({cname}, {f}));\n' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "dh.h"\n'
+                   f'int main(void) {{\n  printf("%zu\\n", sizeof({cname}));\n{body}  return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(py), (cname, out[0], ctypes.sizeof(py))
+    for f, off in zip(fields, out[1:]):
+        assert getattr(py, f).offset == off, (cname, f, off, getattr(py, f).offset)
