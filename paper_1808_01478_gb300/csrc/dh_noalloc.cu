@@ -3,10 +3,11 @@
 // The regular entry points keep their workspace (packed coordinates, the
 // binary64 threshold table, frame and work descriptors, the work counter) in
 // device memory that the context allocates with cudaMalloc on first use.  Some
-// callers cannot allow that: code that runs while a CUDA graph is being
-// captured, code inside a framework whose memory is owned by its own
-// allocator, or a process with a fixed device-memory budget must not trigger
-// new device allocations.  This variant takes device input and output from the
+// callers cannot allow that: code inside a framework whose device memory is
+// owned by its own allocator (a cudaMalloc behind its back fragments or
+// overcommits the pool it manages), or a process that runs under a fixed
+// device-memory budget, must not trigger new device allocations.  This variant
+// takes device input and output from the
 // caller and keeps all of its scratch in one file-scope __device__ array of a
 // fixed size, so it never calls cudaMalloc, cudaFree or any other allocating
 // routine.  The paper has no counterpart of it.
@@ -107,6 +108,18 @@ extern "C" dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream_pt
   double* T = (double*)(base + kNaOffT);
   float4* X = (float4*)(base + kNaOffX);
 
+  // Every host-side check comes before the first enqueued operation, so that a
+  // call that fails leaves the caller's output and the shared scratch untouched.
+  Segment hS[kNaMaxSegs];
+  int n_segs = 0;
+  const int64_t n_items = fill_segments(pf, fd, 0, 1, hS, kNaMaxSegs, &n_segs);
+  if (n_segs > kNaMaxSegs)
+    return fail(DH_ERR_INVALID, "%d species x %d sweeps need %d work segments, beyond the allocation-free limit of %d",
+                frame->n_species, pf.sweeps, n_segs, kNaMaxSegs);
+  const int block = default_block(pf.variant, pf.sweep_width);
+  const int bps = n_items > 0 ? pair_kernel_blocks_per_sm(pf.variant, pf.sweep_width, 1, block) : 1;
+  if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", pf.sweep_width);
+
   // Host-side descriptors live on the stack; the copies below read them before returning.
   FrameDev hF;
   fill_frame_dev(pf, hF, X, frame->out, T);
@@ -118,41 +131,6 @@ extern "C" dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream_pt
   hJ.n = frame->n;
   hJ.stride = (frame->flags & DH_COORDS_F4) ? 4 : 3;
   hJ.chunk0 = 0;
-  Segment hS[kNaMaxSegs];
-  int n_segs = 0;
-  int64_t n_items = 0;
-  {
-    // the same work segments as add_segments builds, in a fixed stack array instead of a vector
-    int S = frame->n_species;
-    int64_t need = (int64_t)pf.sweeps * S * (S + 1) / 2;
-    if (need > kNaMaxSegs)
-      return fail(DH_ERR_INVALID, "%d species x %d sweeps exceed the allocation-free limit", S, pf.sweeps);
-    const int64_t* o = frame->species_offsets;
-    for (int pass = 0; pass < pf.sweeps; ++pass) {
-      int h = 0;
-      for (int a = 0; a < S; ++a)
-        for (int b = a; b < S; ++b, ++h) {
-          int32_t na = (int32_t)(o[a + 1] - o[a]), nb = (int32_t)(o[b + 1] - o[b]);
-          bool intra = (a == b);
-          if (na == 0 || nb == 0 || (intra && na < 2)) continue;
-          Segment& g = hS[n_segs++];
-          std::memset(&g, 0, sizeof g);
-          g.fd = fd;
-          g.intra = intra ? 1 : 0;
-          g.h = h;
-          g.pass = pass;
-          g.a0 = (int32_t)o[a];
-          g.na = na;
-          g.b0 = (int32_t)o[b];
-          g.nb = nb;
-          g.n_ti = (na + kTile - 1) / kTile;
-          g.n_tj = (nb + kTile - 1) / kTile;
-          g.item0 = n_items;
-          g.item_base = 0;
-          n_items += intra ? (int64_t)g.n_ti * (g.n_ti + 1) / 2 : (int64_t)g.n_ti * g.n_tj;
-        }
-    }
-  }
   size_t out_bytes = sizeof(uint64_t) * (size_t)pf.n_hist * (size_t)frame->nbins;
 
   // Clear what must start at zero, upload descriptors, build the table, stage, run.
@@ -166,9 +144,6 @@ extern "C" dh_status dh_histogram_noalloc(const dh_frame* frame, void* stream_pt
   if (chunks > 0) DH_CUDA_TRY(launch_stage(job, 1, chunks, st));
   DH_CUDA_TRY(launch_frame_setup(fd, 1, 0, st));
   if (n_items > 0) {
-    const int block = default_block(pf.variant, pf.sweep_width);
-    int bps = pair_kernel_blocks_per_sm(pf.variant, pf.sweep_width, 1, block);
-    if (bps < 1) return fail(DH_ERR_INVALID, "histogram of %d bins does not fit in shared memory", pf.sweep_width);
     PairLaunch L;
     std::memset(&L, 0, sizeof L);
     L.block = block;

@@ -307,15 +307,19 @@ int default_block(int variant, int width) {
   return kBlockSmall;
 }
 
-// Tiles of one frame's species pairs for every bin sweep, appended to segs
-// (fd: the frame's device descriptor); returns the item count.
-int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::vector<Segment>& segs, int jm) {
+// Tiles of one frame's species pairs for every bin sweep (fd: the frame's
+// device descriptor; items numbered from item0): the first min(cap, total)
+// segments are written to out, *n_out receives the total, and the item count
+// is returned.
+int64_t fill_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, int jm, Segment* out, int cap,
+                      int* n_out) {
   const dh_frame* f = pf.src;
   jm = (jm == 2 || jm == 4) ? jm : 1;
   const int tile_j = kTile / jm;
   const int64_t* o = f->species_offsets;
   int S = f->n_species;
   int64_t items = 0;
+  int n = 0;
   for (int pass = 0; pass < pf.sweeps; ++pass) {
     int h = 0;
     for (int a = 0; a < S; ++a)
@@ -341,10 +345,20 @@ int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::v
         // intra: row ti keeps the j tiles tj >= jm ti (at least one, since na > (n_ti - 1) kTile)
         items += intra ? (int64_t)s.n_ti * s.n_tj - (int64_t)jm * s.n_ti * (s.n_ti - 1) / 2
                        : (int64_t)s.n_ti * s.n_tj;
-        segs.push_back(s);
+        if (n < cap) out[n] = s;
+        ++n;
       }
   }
+  *n_out = n;
   return items;
+}
+
+int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::vector<Segment>& segs, int jm) {
+  int n = 0;
+  fill_segments(pf, fd, item0, jm, nullptr, 0, &n);
+  const size_t at = segs.size();
+  segs.resize(at + (size_t)n);
+  return fill_segments(pf, fd, item0, jm, segs.data() + at, n, &n);
 }
 
 namespace {
@@ -918,7 +932,7 @@ dh_status tune_variant(dh_ctx* c, int v, const VariantSummary& vs) {
   const double g_def = g;
   for (int block : {kBlockSmall, kBlockLarge, kBlockHuge})
     for (int jm = 1; jm <= 4 && s == DH_OK; jm *= 2)
-      for (int depth = 1; depth <= 4 && s == DH_OK; depth *= 2) {
+      for (int depth = 1; depth <= 8 && s == DH_OK; depth *= 2) {
         int bmax = pair_kernel_blocks_per_sm(v, vs.width, depth, block);
         for (int bps = bmax; bps >= 1 && bps >= bmax - 1 && s == DH_OK; --bps) {
           LaunchParams p;

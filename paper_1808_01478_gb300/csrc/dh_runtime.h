@@ -90,7 +90,10 @@ struct PlannedFrame {
 
 dh_status check_frame(const dh_frame* f, PlannedFrame& pf, int max_width);
 void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64_t* out, const double* T);
-// jm: j tiles of kTile/jm particles per i tile of kTile
+// jm: j tiles of kTile/jm particles per i tile of kTile.  fill_segments writes
+// at most cap segments to out and the total to *n_out; add_segments appends all.
+int64_t fill_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, int jm, Segment* out, int cap,
+                      int* n_out);
 int64_t add_segments(const PlannedFrame& pf, FrameDev* fd, int64_t item0, std::vector<Segment>& segs, int jm = 1);
 
 // Launch shape of one pair-kernel launch.

@@ -133,6 +133,7 @@ struct Request {
   uint32_t* sort_C = nullptr;
   int64_t n_items = 0, next = 0;
   bool prepped = false, finalize_enqueued = false, cancel = false;
+  bool timed_out = false;        // cancelled because it passed its deadline (dh_config.timeout_ns)
   uint64_t last_wave = 0;        // sequence number of the last wave carrying its work
   cudaEvent_t done_ev = nullptr;
   int state = Q_QUEUED;
@@ -177,6 +178,7 @@ class Server {
 
  private:
   void loop();
+  void expire();
   void admit();
   bool launch_wave(int v);
   void reap();
@@ -192,6 +194,7 @@ class Server {
   Arena dev_arena_, pin_arena_;
   int max_inflight_ = 64;
   double wave_seconds_ = kWaveSecondsDefault;
+  uint64_t timeout_ns_ = 0;  // deadline of a request after its submission (0: none)
   Lane lanes_[kNumVariants];
 
   std::mutex mu_;
@@ -220,6 +223,7 @@ dh_status Server::start() {
   pin_arena_.init(pin);
   max_inflight_ = ctx_->cfg.max_inflight > 0 ? ctx_->cfg.max_inflight : 64;
   if (ctx_->cfg.wave_us) wave_seconds_ = 1e-6 * (double)ctx_->cfg.wave_us;
+  timeout_ns_ = ctx_->cfg.timeout_ns;
   for (Lane& ln : lanes_) {
     DH_CUDA_TRY(cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking));
     DH_CUDA_TRY(ln.tstat.ensure(64));
@@ -472,6 +476,10 @@ dh_status Server::prep(Request& r) {
                                     r.sort_K, r.sort_C, st));
   }
   DH_CUDA_TRY(launch_frame_setup(r.fd, 1, 0, st));
+  // marks the end of the preparation: a request cancelled before its first wave
+  // keeps its pool memory until this work has finished
+  if (!r.done_ev) DH_CUDA_TRY(cudaEventCreateWithFlags(&r.done_ev, cudaEventDisableTiming));
+  DH_CUDA_TRY(cudaEventRecord(r.done_ev, st));
   r.prepped = true;
   return DH_OK;
 }
@@ -620,7 +628,8 @@ void Server::reap() {
       if (q == cudaSuccess) {
         finished = true;
         if (r.cancel) {
-          complete(r, DH_ERR_CANCELLED, "cancelled");
+          complete(r, r.timed_out ? DH_ERR_TIMEOUT : DH_ERR_CANCELLED,
+                   r.timed_out ? "request passed its deadline (dh_config.timeout_ns)" : "cancelled");
         } else if (r.fd_pin->bad) {
           complete(r, DH_ERR_INVALID, "frame has non-finite coordinates");
         } else {
@@ -637,10 +646,14 @@ void Server::reap() {
         finished = true;
         complete(r, DH_ERR_CUDA, cudaGetErrorString(q));
       }
-    } else if (r.cancel && r.last_wave <= lanes_[r.pf.variant].done_seq) {
+    } else if (r.cancel && r.last_wave <= lanes_[r.pf.variant].done_seq &&
+               (!r.prepped || !r.done_ev || cudaEventQuery(r.done_ev) != cudaErrorNotReady)) {
       finished = true;  // no work of it left on the device
-      complete(r, r.error.empty() ? DH_ERR_CANCELLED : DH_ERR_CUDA,
-               r.error.empty() ? "cancelled" : r.error.c_str());
+      if (r.timed_out)
+        complete(r, DH_ERR_TIMEOUT, "request passed its deadline (dh_config.timeout_ns)");
+      else
+        complete(r, r.error.empty() ? DH_ERR_CANCELLED : DH_ERR_CUDA,
+                 r.error.empty() ? "cancelled" : r.error.c_str());
     }
     if (finished) {
       release_resources(r);
@@ -651,10 +664,31 @@ void Server::reap() {
   }
 }
 
+// Requests past their deadline: queued ones end now, running ones are
+// cancelled and end once none of their work is left on the device.
+void Server::expire() {
+  if (!timeout_ns_) return;
+  const auto now = Clock::now();
+  const auto limit = std::chrono::nanoseconds(timeout_ns_);
+  for (size_t k = 0; k < queue_.size();) {
+    Request& r = *queue_[k];
+    if (now - r.t_submit > limit) {
+      r.timed_out = r.cancel = true;
+      complete(r, DH_ERR_TIMEOUT, "request passed its deadline (dh_config.timeout_ns) while queued");
+      queue_.erase(queue_.begin() + (long)k);
+    } else {
+      ++k;
+    }
+  }
+  for (Request* r : active_)
+    if (!r->cancel && now - r->t_submit > limit) r->timed_out = r->cancel = true;
+}
+
 void Server::loop() {
   cudaSetDevice(device_);
   std::unique_lock<std::mutex> lk(mu_);
   while (!stop_) {
+    expire();
     reap();
     admit();
     for (int v = 0; v < kNumVariants; ++v)

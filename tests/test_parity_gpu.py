@@ -212,10 +212,12 @@ def test_spatial_order_and_tile_images(ctx, torch_mod, oracle_mod, name):
 
 
 @pytest.mark.parametrize("box_type", [w.BOX_ORTHO, w.BOX_TRICLINIC])
-def test_tile_images_at_larger_n_match_the_unsorted_path(ctx, torch_mod, box_type):
-    # N = 131,072 (too many pairs for the oracle here): the sorted path with tile
-    # images against dh_histogram_noalloc, which neither sorts nor uses tile
-    # images (and is itself compared with the oracle); both must agree bin for bin
+def test_tile_images_at_larger_n_match_the_unsorted_path(ctx, torch_mod, oracle_mod, box_type):
+    # N = 131,072: the sorted path with tile images against dh_histogram_noalloc,
+    # which does not sort (its warps see unsorted runs, which rarely share one
+    # nearest image), bin for bin; and, independently, the histograms of a
+    # species of 2,048 particles carved out of the same frame (its AA and AB
+    # pairs against every particle) against the oracle
     n = dh.DH_NOALLOC_MAX_N
     if box_type == w.BOX_ORTHO:
         box = w.ortho_box((n / 0.1) ** (1.0 / 3.0))
@@ -233,3 +235,10 @@ def test_tile_images_at_larger_n_match_the_unsorted_path(ctx, torch_mod, box_typ
     fa = dh.FrameArgs(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
     dh.dh_histogram_noalloc(fa.frame)
     assert_same(got, out.cpu().numpy().view(np.uint64), "noalloc")
+    g = w.frame_from(f.coords, [0, 2048, n], f.box_type, f.box, f.r_max, f.nbins, "carved")
+    h = ctx.histogram(x, g.offsets, g.box_type, g.box, g.r_max, g.nbins).cpu().numpy().view(np.uint64)
+    assert ctx.stats()["uniform_pairs"] > 0
+    for k, (a, c) in enumerate([(0, 0), (0, 1)]):
+        want = oracle_mod.histogram_one(g.coords, g.offsets, g.box_type, g.box, g.r_max, g.nbins, a, c)
+        assert np.array_equal(h[k], want), (a, c)
+    assert np.array_equal(h.sum(0), got[0])  # the split histograms add up to the frame's

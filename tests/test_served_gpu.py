@@ -125,3 +125,18 @@ def test_admission_by_footprint(torch_mod, oracle_mod):
         with pytest.raises(dh.DHError) as e:
             submit(c, huge)
         assert e.value.status == dh.DH_ERR_NOMEM
+
+
+def test_request_deadline(torch_mod, oracle_mod):
+    # dh_config.timeout_ns: a request not finished that long after dh_submit is
+    # cancelled and reports DH_ERR_TIMEOUT, queued or running; requests that
+    # finish in time are unaffected and the server keeps serving
+    big = w.uniform_frame(8, 600_000, w.BOX_TRICLINIC, w.scale_box(w.triclinic_box(1, 1, 1, *w.C3_ANGLES), 6e6),
+                          60.0, 16384)
+    with dh.Context(0, pool_bytes=1 << 30, max_inflight=4, timeout_ns=20_000_000) as c:
+        t_big, _ = submit(c, big)
+        assert c.wait(t_big, timeout_ns=30_000_000_000) == dh.DH_ERR_TIMEOUT
+        f = mixed_frames(9, k=1, n_lo=800, n_hi=1500)[0]
+        t, fa = submit(c, f)
+        assert c.wait(t) == dh.DH_OK
+        assert np.array_equal(fa.out, oracle_mod.histogram_frame(f))

@@ -1,10 +1,12 @@
 """dh_histogram_noalloc: the allocation-free entry point.
 
-Callers that may not allocate device memory (inside CUDA graph capture, under
-a framework's own allocator, with a fixed memory budget) use this variant: it
+Callers that may not allocate device memory (code under a framework's own
+caching allocator, which a cudaMalloc behind its back would fragment or
+overcommit; processes with a fixed device-memory budget) use this variant: it
 keeps its scratch in a fixed device array inside the library.  Its output must
 equal the regular dh_histogram bin for bin (the integer tolerance of every
-parity test here), call after call, since all calls share that array.
+parity test here), call after call, since all calls share that array, and the
+FP64 oracle as well.
 
 This file is named so pytest collects it last; it also passes on its own in a
 fresh process.
@@ -41,8 +43,16 @@ FRAMES = [
 ]
 
 
+@pytest.fixture(scope="module")
+def oracle_lib():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
 @pytest.mark.parametrize("k", range(len(FRAMES)))
-def test_noalloc_matches_dh_histogram_on_two_calls(torch_mod, k):
+def test_noalloc_matches_dh_histogram_on_two_calls(torch_mod, oracle_lib, k):
     f = FRAMES[k]
     x = torch_mod.from_numpy(f.coords).cuda()
     with dh.Context(0) as ctx:
@@ -51,6 +61,7 @@ def test_noalloc_matches_dh_histogram_on_two_calls(torch_mod, k):
     second = noalloc(torch_mod, f, x)
     assert np.array_equal(first, ref), f.name
     assert np.array_equal(second, ref), f.name
+    assert np.array_equal(first, oracle_lib.histogram_frame(f)), f.name
 
 
 def test_noalloc_on_a_stream_and_after_another_frame(torch_mod):
@@ -84,3 +95,13 @@ def test_noalloc_rejects_frames_beyond_its_limits(torch_mod):
     with pytest.raises(dh.DHError) as e:
         dh.dh_histogram_noalloc(fh.frame)
     assert e.value.status == dh.DH_ERR_INVALID
+    # more species pairs than work segments: rejected before any work, out untouched
+    n = 1000
+    many = w.uniform_frame(25, n, w.BOX_NONE, w.ortho_box(10.0), 5.0, 64, n_species=40)
+    xm = torch_mod.from_numpy(many.coords).cuda()
+    out = torch_mod.full((many.n_hist, 64), 7, dtype=torch_mod.int64, device=xm.device)
+    fa = dh.FrameArgs(xm, many.offsets, many.box_type, many.box, many.r_max, many.nbins, out)
+    with pytest.raises(dh.DHError) as e:
+        dh.dh_histogram_noalloc(fa.frame)
+    assert e.value.status == dh.DH_ERR_INVALID
+    assert bool((out == 7).all())
