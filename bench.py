@@ -10,7 +10,11 @@ minimum-image variant, replayed as a CUDA graph), inputs resident in HBM.  Print
                  host->device copy of the coordinates and device->host copy of
                  the histograms inside the timed region
   plain          per-frame dh_histogram Gpairs/s for each box type
-  roofline       the pair kernel's float32 operations per second against the lane peak
+  configs        the plain path on C1 (no box, N = 2,000), C2 (orthorhombic, N =
+                 100,000) and C3 (clustered triclinic, N = 500,000)
+  pipes          measured per-SM throughput of the pipes the pair kernel uses
+  roofline       the pair kernel's pairs per second against the minimum over
+                 those pipes of measured rate / operations per pair
   cpu_baseline   the FP64 oracle on the host cores, on a bounded sample
   clocks         nvidia-smi SM clocks and throttle reasons during the timed region
 
@@ -42,15 +46,84 @@ METRIC = "Gpairs/s binned at N=1M (plain vs batched/served) + p50/p99 frame late
 UNIT = "Gpairs/s"
 BOXES = (w.BOX_NONE, w.BOX_ORTHO, w.BOX_TRICLINIC)
 
-# Algorithmic operations per evaluated pair (float32-pipe-equivalent), from the
-# definition: none: 3 sub, 3 mul/fma for r^2, sqrt, scale, floor, bin compare = 10;
-# orthorhombic: + 3 x (mul by 1/L, nearest integer, fma) = 19; triclinic
-# (single wrap below half the plane spacing): + back substitution (6),
-# 3 nearest integers, d - B k (9) = 28; plus one shared-memory increment for each
-# pair inside r_max.
-OPS_PER_PAIR = {w.BOX_NONE: 10.0, w.BOX_ORTHO: 19.0, w.BOX_TRICLINIC: 28.0}
+# Per-pair arithmetic of the pair kernel on the float32 (FMA) pipe, by tile mode,
+# as lane operations of each packed kind (FADD2, FMUL2, FFMA2 count two lanes).
+# Every mode: d = xj - xi (3 add), r^2 (1 mul, 2 fma), q = S^2 r^2 (1 mul), the
+# nearest integer of the root and its residual (2 add, 1 fma), the near-edge
+# bound (1 fma).  Orthorhombic tiles with a uniform image shift the j's by the
+# image (3 packed adds per 2 j x 4 i: 0.75 lanes per pair; 0.5 with one axis
+# wrapped per pair).  A wrapped axis adds a nearest integer and an fma (1 add,
+# 2 fma); the per-pair triclinic wrap rounds along c, b, a (3 add, 9 fma).  The
+# square root is one MUFU operation per pair and the histogram update one
+# shared-memory atomic per pair (the clamp of out-of-range roots runs on the
+# integer ALU).
+BASE_OPS = {"fadd": 5.0, "fmul": 2.0, "ffma": 4.0}
+MODE_OPS = {
+    (w.BOX_NONE, "uni"): {}, (w.BOX_NONE, "pair"): {},
+    (w.BOX_ORTHO, "uni"): {"fadd": 0.75}, (w.BOX_ORTHO, "axis"): {"fadd": 1.5, "ffma": 2.0},
+    (w.BOX_ORTHO, "pair"): {"fadd": 3.0, "ffma": 6.0},
+    (w.BOX_TRICLINIC, "uni"): {}, (w.BOX_TRICLINIC, "axis"): {"fadd": 1.0, "ffma": 2.0},
+    (w.BOX_TRICLINIC, "pair"): {"fadd": 3.0, "ffma": 9.0},
+}
 SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+PIPE_SET = ("ffma2", "fadd2", "fmul2", "ffma", "sqrt", "frnd", "f2i", "lop3", "iadd", "imad", "dfma", "match",
+            "smem_atomic_clustered", "smem_atomic_same", "smem_atomic_sequential")
+
+
+def measure_pipes(device: int, widths) -> dict:
+    """Measured per-SM throughput (operations per clock per SM) of the pipes the
+    pair kernel runs on (dh_pipe_rate), with the shared-memory atomic rate on
+    uniform random bins for every histogram width in `widths`."""
+    import paper_1808_01478_gb300 as dh
+
+    out = {}
+    for name in PIPE_SET:
+        width = 10000 if name.startswith("smem") else 0
+        r = dh.dh_pipe_rate(device, name, width)
+        out[name] = {"per_clk_sm": round(r["per_clk_sm"], 3), "mhz": round(r["sm_mhz"], 1)}
+    for wd in sorted(set(int(x) for x in widths)):
+        r = dh.dh_pipe_rate(device, "smem_atomic_random", min(wd, 57344))
+        out[f"smem_atomic_random@{wd}"] = {"per_clk_sm": round(r["per_clk_sm"], 3), "mhz": round(r["sm_mhz"], 1)}
+    r = dh.dh_pipe_rate(device, "global_atomic64", 10000)
+    out["global_atomic64@10000"] = {"per_clk_sm": round(r["per_clk_sm"], 4), "mhz": round(r["sm_mhz"], 1)}
+    return out
+
+
+def fp32_lane_ops(box_type: int, f_uni: float, f_axis: float) -> dict:
+    """Float32 lane operations per pair of each kind, averaged over the tile modes
+    with the fractions of pairs the kernel evaluated in each."""
+    f_pair = max(0.0, 1.0 - f_uni - f_axis)
+    ops = dict(BASE_OPS)
+    for mode, frac in (("uni", f_uni), ("axis", f_axis), ("pair", f_pair)):
+        for k, v in MODE_OPS.get((box_type, mode), {}).items():
+            ops[k] += frac * v
+    return ops
+
+
+def pair_bound(box_type: int, width: int, f_uni: float, f_axis: float, pipes: dict) -> dict:
+    """Roofline of the pair kernel for one frame in pairs per clock per SM: the
+    minimum over pipes of measured rate / operations per pair (float32 FMA
+    pipe, MUFU square root, shared-memory atomic at the frame's width)."""
+    ops = fp32_lane_ops(box_type, f_uni, f_axis)
+    fp32_clk = (ops["fadd"] / pipes["fadd2"]["per_clk_sm"] + ops["fmul"] / pipes["fmul2"]["per_clk_sm"]
+                + ops["ffma"] / pipes["ffma2"]["per_clk_sm"])
+    key = f"smem_atomic_random@{width}"
+    bounds = {"fp32": 1.0 / fp32_clk, "mufu": pipes["sqrt"]["per_clk_sm"],
+              "smem_atomic": pipes[key]["per_clk_sm"] if key in pipes else float("nan")}
+    binding = min((v, k) for k, v in bounds.items() if v == v)[1]
+    return {"pairs_per_clk_sm": bounds[binding], "binding": binding,
+            "fp32_lane_ops_per_pair": round(sum(ops.values()), 3),
+            "bounds_pairs_per_clk_sm": {k: round(v, 3) for k, v in bounds.items()}}
+
+
+def roofline_entry(pairs: float, seconds: float, mhz: float, bound: dict) -> dict:
+    """Achieved pairs per clock per SM (at the SM clock sampled under load)
+    against the frame's bound."""
+    achieved = pairs / seconds / (SM_COUNT * mhz * 1e6)
+    return {"achieved_pairs_per_clk_sm": round(achieved, 3), "bound_pairs_per_clk_sm": round(bound["pairs_per_clk_sm"], 3),
+            "frac": round(achieved / bound["pairs_per_clk_sm"], 4), "binding": bound["binding"],
+            "fp32_lane_ops_per_pair": bound["fp32_lane_ops_per_pair"],
+            "bounds_pairs_per_clk_sm": bound["bounds_pairs_per_clk_sm"]}
 
 
 def load_peaks() -> dict:
@@ -89,10 +162,6 @@ def committed_traffic() -> int | None:
         elif p[0] == "launch":
             total += int(p[3]) + int(p[4])
     return total or None
-
-
-def alu_peak_tops(sm_count: int, mhz: float) -> float:
-    return sm_count * FP32_LANES_PER_SM * mhz * 1e6 / 1e12
 
 
 # ---------------------------------------------------------------- clocks
@@ -292,6 +361,55 @@ def run_reference(args, world, rank):
 
 
 
+# ---------------------------------------------------------------- configurations C1-C3
+
+
+def config_frames() -> dict:
+    """C1: no box, N = 2,000 in a cube of side 10, r_max 17.33, 1,000 bins;
+    C2: orthorhombic 60^3, N = 100,000, 2 species, r_max 30, 10,000 bins;
+    C3: triclinic 80 A cell (70/80/100 deg), N = 500,000 as 200 Gaussian clusters
+    (sigma 2) plus 20 % background, 3 species, r_max 35, 20,000 bins."""
+    return {"c1": w.config_small_nobox(seed=1), "c2": w.config_ortho_two_species(seed=2),
+            "c3": w.config_triclinic_clusters(seed=3)}
+
+
+def run_configs(ctx, stream, dev, args, pipes, mhz, flush_l2):
+    """The plain path on C1-C3 with device-resident inputs: Gpairs/s of the whole
+    call (CUDA events), the pair kernel's share, deferrals and the roofline
+    fraction of the pair kernel."""
+    import torch
+
+    out = {}
+    for name, f in config_frames().items():
+        x = torch.from_numpy(f.coords).to(dev)
+        o = torch.zeros((f.n_hist, f.nbins), dtype=torch.int64, device=dev)
+        ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, o)
+        reps = max(3, args.plain_steps) if f.n_pairs() < 1e10 else max(1, args.plain_steps)
+        ts, pk = [], []
+        for _ in range(reps):
+            flush_l2()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, o)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            pk.append(ctx.stats()["pair_kernel_ms"])
+        st = ctx.stats()
+        fu = st["uniform_pairs"] / max(1, st["pairs"])
+        fa_ = st["axis_pairs"] / max(1, st["pairs"])
+        bound = pair_bound(f.box_type, f.nbins, fu, fa_, pipes)
+        pairs = f.n_pairs()
+        out[name] = {"workload": f.name, "pairs": pairs, "gpairs_s": round(pairs / (statistics.median(ts) / 1e3) / 1e9, 3),
+                     "ms": round(statistics.median(ts), 4), "pair_kernel_ms": round(statistics.median(pk), 4),
+                     "deferred_frac": round(st["deferred"] / max(1, st["pairs"]), 6),
+                     "binary64_frac": round(st["exact_fallback"] / max(1, st["pairs"]), 8),
+                     "tile_image_frac": round(fu, 4), "axis_image_frac": round(fa_, 4),
+                     "roofline": roofline_entry(pairs, statistics.median(pk) / 1e3, mhz, bound)}
+        del x, o
+    return out
+
+
 # ---------------------------------------------------------------- batched and served legs
 
 
@@ -440,8 +558,13 @@ def run_served_c5(dev_index, dev, args):
 
 
 def scan_frame(box_name: str, n: int, nbins: int):
-    """One frame of the scan: uniform at density 0.1, orthorhombic cube (r_max = L/2)
-    or the 70/80/100-degree cell (r_max = 0.95 h_min/2)."""
+    """One frame of the scan: uniform at density 0.1, no box (a cube, r_max its
+    diagonal), orthorhombic cube (r_max = L/2) or the 70/80/100-degree cell
+    (r_max = 0.95 h_min/2)."""
+    if box_name == "none":
+        side = (n / 0.1) ** (1.0 / 3.0)
+        f = w.uniform_frame(101, n, w.BOX_ORTHO, w.ortho_box(side), side * math.sqrt(3.0), nbins)
+        return w.frame_from(f.coords, f.offsets, w.BOX_NONE, np.zeros(9), side * math.sqrt(3.0), nbins, "none")
     if box_name == "triclinic":
         box = w.scale_box(w.triclinic_box(1.0, 1.0, 1.0, *w.C3_ANGLES), n / 0.1)
         return w.uniform_frame(101, n, w.BOX_TRICLINIC, box, 0.95 * float(w.box_heights(box).min()) / 2.0, nbins)
@@ -476,10 +599,10 @@ def run_scan(args, world, rank, local):
             c0.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
             sweeps = c0.stats()["sweeps"]
         width = -(-nbins // sweeps)
-        key = (1 if f.box_type == w.BOX_ORTHO else 2, max(0, math.ceil(math.log2(width))),
+        key = ({w.BOX_NONE: 0, w.BOX_ORTHO: 1}.get(f.box_type, 2), max(0, math.ceil(math.log2(width))),
                math.floor(math.log2(math.sqrt(2.0 * max(f.n_pairs(), 1))) + 0.5), 0)
         ref = None
-        for block, depth in ((256, 1), (256, 2), (256, 4), (512, 1), (512, 2), (1024, 1)):
+        for block, depth in args.scan_shapes:
             path = os.path.join(tmp, f"t_{box_name}_{n}_{nbins}_{block}_{depth}.txt")
             with open(path, "w") as fh:
                 fh.write(f"{sms} {key[0]} {key[1]} {key[2]} {key[3]} 1024 {block} {depth} 32 1.0\n")
@@ -528,6 +651,9 @@ def run_gpu(args, world, rank, local):
         with torch.cuda.stream(stream):
             flush.fill_(1)
 
+    # ---- measured per-pipe peaks (operations per clock per SM)
+    pipes = measure_pipes(local, [args.nbins, 1000, 10000, 20000])
+
     # ---- batched step (headline value); the first warm-up call runs the autotuner
     tune_runs = 0
     for _ in range(args.warmup):
@@ -557,29 +683,14 @@ def run_gpu(args, world, rank, local):
     value, t_total = aggregate_throughput(td, pairs_step * args.steps, sum(step_ms) / 1e3, dev)
     hist_sums = [int(o.sum().item()) for o in OUT]
 
-    # ---- roofline of the pair kernel (device time of its launches in the timed steps)
-    peaks = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    ops = sum(p * (OPS_PER_PAIR[f.box_type] + hs / p) for f, p, hs in zip(frames, pairs, hist_sums))
-    mean_pair_s = statistics.mean(pair_ms) / 1e3
-    achieved = ops / mean_pair_s / 1e12
-    peak = alu_peak_tops(SM_COUNT, sm_max)
-    headline_size = (args.n, args.nbins) == (1_000_000, 10_000)
-    traffic = committed_traffic() if headline_size else None
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "traffic_basis": ("DRAM bytes read + written by the step's three pair-kernel launches (ncu, "
-                                  f"{TRAFFIC_FILE}); algorithmic: 3 x (16 B x N + 8 B x nbins)"
-                                  if traffic else None),
-                "kernel": "dh::pair_kernel", "ops_per_step": ops,
-                "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max clock)"}
+    mhz = float(clocks["sm_mhz"]) if clocks else float(load_peaks().get("sm_max_mhz", 2070.0))
 
-    # ---- plain per-frame path
+    # ---- plain per-frame path (and the pair kernel's own device time per frame)
     plain = {}
+    bounds = {}
     for k, f in enumerate(frames):
-        for _ in range(1):
-            ctx.histogram(X[k], f.offsets, f.box_type, f.box, f.r_max, f.nbins, OUT[k])
-        ts = []
+        ctx.histogram(X[k], f.offsets, f.box_type, f.box, f.r_max, f.nbins, OUT[k])
+        ts, pk = [], []
         for _ in range(max(1, args.plain_steps)):
             flush_l2()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -589,14 +700,42 @@ def run_gpu(args, world, rank, local):
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
+            pk.append(ctx.stats()["pair_kernel_ms"])
         st = ctx.stats()
+        fu = st["uniform_pairs"] / max(1, st["pairs"])
+        fa_ = st["axis_pairs"] / max(1, st["pairs"])
+        bounds[k] = pair_bound(f.box_type, f.nbins, fu, fa_, pipes)
         plain[w.BOX_NAMES[f.box_type]] = {
             "gpairs_s": round(pairs[k] / (statistics.mean(ts) / 1e3) / 1e9, 3),
             "ms": round(statistics.mean(ts), 3),
+            "pair_kernel_ms": round(statistics.mean(pk), 3),
             "deferred_frac": round(st["deferred"] / max(1, st["pairs"]), 6),
-            "tile_image_frac": round(st["uniform_pairs"] / max(1, st["pairs"]), 4),
-            "axis_image_frac": round(st["axis_pairs"] / max(1, st["pairs"]), 4),
+            "tile_image_frac": round(fu, 4),
+            "axis_image_frac": round(fa_, 4),
+            "roofline": roofline_entry(pairs[k], statistics.mean(pk) / 1e3, mhz, bounds[k]),
         }
+
+    # ---- roofline of the pair kernel in the timed batched steps: pairs per
+    # second of its launches (CUDA events on their stream) against the bound of
+    # the step's frames, min over pipes of measured rate / operations per pair,
+    # scaled by the SMs and the median SM clock sampled during the timed steps
+    mean_pair_s = statistics.mean(pair_ms) / 1e3
+    clk_per_step = sum(p / bounds[k]["pairs_per_clk_sm"] for k, p in enumerate(pairs))  # SM-clocks
+    peak_gpairs = pairs_step / clk_per_step * SM_COUNT * mhz * 1e6 / 1e9
+    achieved_gpairs = pairs_step / mean_pair_s / 1e9
+    headline_size = (args.n, args.nbins) == (1_000_000, 10_000)
+    traffic = committed_traffic() if headline_size else None
+    roofline = {"bound": "alu", "achieved": round(achieved_gpairs, 3), "peak": round(peak_gpairs, 3),
+                "unit": "Gpairs/s", "frac": round(achieved_gpairs / peak_gpairs, 4), "traffic": traffic,
+                "traffic_basis": ("DRAM bytes read + written by the step's three pair-kernel launches (ncu, "
+                                  f"{TRAFFIC_FILE}); algorithmic: 3 x (16 B x N + 8 B x nbins)"
+                                  if traffic else None),
+                "kernel": "dh::pair_kernel",
+                "per_frame": {w.BOX_NAMES[f.box_type]: plain[w.BOX_NAMES[f.box_type]]["roofline"] for f in frames},
+                "peak_basis": (f"per frame min over pipes of measured rate (dh_pipe_rate, ops/clk/SM) / ops per "
+                               f"pair (float32 FMA pipe by tile mode, MUFU sqrt, shared atomic at the width), "
+                               f"combined over the step's frames, x {SM_COUNT} SMs x {mhz:.0f} MHz (median SM "
+                               f"clock sampled during the timed steps)")}
 
     # ---- binary64 input coordinates (the same frames, coordinates perturbed below
     # float32 resolution so that they are not float32 values)
@@ -642,6 +781,7 @@ def run_gpu(args, world, rank, local):
     h2d = sum(f.n * 12 for f in frames)
     d2h = sum(f.nbins * 8 for f in frames)
 
+    configs = run_configs(ctx, stream, dev, args, pipes, mhz, flush_l2) if args.configs else None
     c4 = run_batched_c4(ctx, stream, dev, args) if args.c4_frames > 0 else None
     served = run_served_c5(local, dev, args) if args.served_requests > 0 else None
 
@@ -662,6 +802,8 @@ def run_gpu(args, world, rank, local):
                                      "blocks_per_sm": stats_b["blocks_per_sm"], "autotune_runs": tune_runs},
                     "c4": c4},
         "served": served,
+        "configs": configs,
+        "pipes": {"unit": "operations per clock per SM (dh_pipe_rate)", **pipes},
         "roofline": roofline,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -702,7 +844,9 @@ def main(argv=None) -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of measured ones")
     ap.add_argument("--c4-frames", type=int, default=256)
-    ap.add_argument("--served-requests", type=int, default=200)
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the C1-C3 configurations")
     ap.add_argument("--served-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95])
     ap.add_argument("--scan", action="store_true",
                     help="instead of the bench line: throughput against nbins and histogram copies")
@@ -710,8 +854,11 @@ def main(argv=None) -> int:
     ap.add_argument("--scan-bins", type=int, nargs="*",
                     default=[1024, 4096, 16384, 32768, 50000, 60000, 100000, 160000, 250000])
     ap.add_argument("--scan-reps", type=int, default=3)
-    ap.add_argument("--scan-boxes", nargs="*", default=["ortho", "triclinic"], choices=["ortho", "triclinic"])
+    ap.add_argument("--scan-boxes", nargs="*", default=["ortho", "triclinic"], choices=["none", "ortho", "triclinic"])
+    ap.add_argument("--scan-shapes", nargs="*", default=["256x1", "256x2", "256x4", "512x1", "512x2", "1024x1"],
+                    help="threads x lane-interleaved histogram copies per block")
     args = ap.parse_args(argv)
+    args.scan_shapes = [tuple(int(v) for v in s.split("x")) for s in args.scan_shapes]
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_env()

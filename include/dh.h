@@ -57,7 +57,7 @@ typedef enum {
   DH_ERR_INVALID = -1,     /* bad argument: offsets, nbins, r_max, box, non-finite coordinates */
   DH_ERR_NOMEM = -2,       /* device or pinned host memory could not be obtained */
   DH_ERR_CUDA = -3,        /* a CUDA call failed (message in dh_last_error) */
-  DH_ERR_TIMEOUT = -4,     /* dh_wait ran out of time, or a device wait gave up */
+  DH_ERR_TIMEOUT = -4,     /* dh_wait ran out of time, or a served request passed its deadline */
   DH_ERR_CANCELLED = -5,   /* the request was cancelled before it finished */
   DH_ERR_NOTFOUND = -6     /* unknown ticket */
 } dh_status;
@@ -88,7 +88,8 @@ typedef struct {
   int32_t device;        /* CUDA device ordinal */
   uint64_t pool_bytes;   /* served path: device memory the admission control may use (0: 1/2 of free) */
   int32_t max_inflight;  /* served path: most requests resident on the device at once (0: 64) */
-  uint64_t timeout_ns;   /* served path: bound on device-side waits (0: 2 s) */
+  uint64_t timeout_ns;   /* served path: deadline of a request, counted from its dh_submit; a request
+                            not finished by then is cancelled and reports DH_ERR_TIMEOUT (0: none) */
   const char* tune_cache;/* autotuner cache file (read at dh_create, rewritten after each new
                             measurement), or NULL for in-memory only */
   uint32_t flags;        /* DH_CFG_* */
@@ -126,7 +127,7 @@ typedef struct {
   int32_t tune_runs;       /* autotuner measurement launches made before the call (DH_CFG_AUTOTUNE) */
   double pair_kernel_ms;   /* device time of the pair-kernel launches (needs DH_CFG_TIMING), else 0 */
   int32_t tile_j;          /* launch shape of the largest pair-kernel launch: j-tile length, */
-  int32_t hist_depth;      /*   private histogram copies per block, */
+  int32_t hist_depth;      /*   private histogram copies per block (warp w uses copy w mod depth), */
   int32_t blocks_per_sm;   /*   blocks per SM */
   int32_t block_threads;   /*   and threads per block */
   uint64_t uniform_pairs;  /* pairs evaluated with one nearest image for their whole tile (no per-pair rounding) */
@@ -222,7 +223,7 @@ dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds);
  * 27-image search; width_log2 = ceil(log2 of the shared-memory histogram
  * width); n_log2 = round(log2 of the mean particles per frame); frames_log4 =
  * min(3, floor(log4 of the frames per launch)); tile_j in {256, 512, 1024};
- * block, the threads per block, in {256, 512, 1024}; depth in {1, 2, 4}; bps, the
+ * block, the threads per block, in {256, 512, 1024}; depth in {1, 2, 4, 8}; bps, the
  * blocks per SM, >= 1 (at most what fits is used); gpairs_s > 0).  *n_entries receives the number
  * of distinct launch keys with a well-formed line for a GPU with sm_count SMs
  * (a later line replaces an earlier one of the same key); lines for other SM
@@ -256,14 +257,48 @@ dh_status dh_tune_cache_count(const char* path, int32_t sm_count, int32_t* n_ent
 dh_status dh_selfcheck(dh_ctx* ctx, int32_t what, const dh_frame* frame, uint64_t n_samples, uint64_t seed,
                        double* out);
 
+/* Diagnostics: throughput of one GPU pipe that the pair kernel runs on (the
+ * paper sizes its kernels from measured occupancy and throughput, Sec. 3.2.4
+ * and Sec. 4.2; these are the ceilings the pair kernel's rate is compared
+ * with).  Runs one microbenchmark on `device`: a single wave of blocks keeping
+ * every resident warp busy with independent instances of one instruction, after
+ * a warm-up launch.  out (4 doubles): out[0] = operations per clock per SM (from
+ * the SM cycle counter), out[1] = operations per second, out[2] = the SM clock
+ * in MHz over the measured launch, out[3] = its duration in ms.  An operation
+ * is one lane's result (a packed float32x2 instruction counts 2), one shared or
+ * global atomic, one match.  width: histogram bins of the atomic benchmarks
+ * (shared: 64..57,344 uint32 bins of one block-private histogram; global:
+ * 64..2^24 uint64 bins), ignored otherwise.  The call allocates and frees a few
+ * small device buffers and its own stream.  DH_ERR_INVALID for an unknown pipe
+ * or a width out of range. */
+#define DH_PIPE_FFMA2 0                 /* fma.rn.f32x2 */
+#define DH_PIPE_FADD2 1                 /* add.rn.f32x2 */
+#define DH_PIPE_FMUL2 2                 /* mul.rn.f32x2 */
+#define DH_PIPE_FFMA 3                  /* fma.rn.f32 */
+#define DH_PIPE_SQRT 4                  /* sqrt.approx.ftz.f32 (MUFU) */
+#define DH_PIPE_FRND 5                  /* cvt.rni.f32.f32 */
+#define DH_PIPE_F2I 6                   /* cvt.rni.s32.f32 */
+#define DH_PIPE_LOP3 7                  /* lop3.b32 */
+#define DH_PIPE_IADD 8                  /* add.u32 */
+#define DH_PIPE_IMAD 9                  /* mad.lo.u32 */
+#define DH_PIPE_DFMA 10                 /* fma.rn.f64 */
+#define DH_PIPE_MATCH 11                /* match.any.sync.b32 */
+#define DH_PIPE_SMEM_ATOMIC_RANDOM 12   /* red.shared.add.u32, uniform random bins */
+#define DH_PIPE_SMEM_ATOMIC_CLUSTERED 13 /* the same, the 32 lanes of a warp on 4 neighbouring bins */
+#define DH_PIPE_SMEM_ATOMIC_SAME 14     /* the same, all lanes of a warp on one bin */
+#define DH_PIPE_SMEM_ATOMIC_SEQUENTIAL 15 /* the same, lane l on bin base + l (no bank conflict) */
+#define DH_PIPE_GLOBAL_ATOMIC64 16      /* atom.global.add.u64, uniform random bins */
+dh_status dh_pipe_rate(int32_t device, int32_t pipe, int32_t width, double* out);
+
 /* Allocation-free histogram (the paper has no counterpart of this entry point).
  *
- * For callers that must not allocate device memory: code that runs while a
- * CUDA graph is being captured, frameworks whose device memory belongs to
- * their own allocator, processes with a fixed memory budget.  Every other
- * entry point keeps its workspace in memory the context obtains with
- * cudaMalloc; this one needs no context and calls no cudaMalloc, cudaFree or
- * other allocating routine.  It computes exactly what dh_histogram computes.
+ * For callers that must not allocate device memory: frameworks whose device
+ * memory belongs to their own caching allocator (a cudaMalloc behind its back
+ * fragments or overcommits the pool it manages), and processes that run under
+ * a fixed device-memory budget.  Every other entry point keeps its workspace in
+ * memory the context obtains with cudaMalloc; this one needs no context and
+ * calls no cudaMalloc, cudaFree or other allocating routine.  It computes
+ * exactly what dh_histogram computes.
  *
  * frame->flags must contain DH_DEVICE_PTRS: coords and out are device
  * pointers on the current device (species_offsets stays a host array); the
@@ -272,7 +307,8 @@ dh_status dh_selfcheck(dh_ctx* ctx, int32_t what, const dh_frame* frame, uint64_
  * array of DH_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
  * until the process exits; limits: n <= DH_NOALLOC_MAX_N, nbins <=
  * DH_NOALLOC_MAX_BINS, at most 256 species-pair work segments (n_species <= 15
- * when one bin sweep suffices).  Larger frames return DH_ERR_INVALID.
+ * when one bin sweep suffices).  Larger frames return DH_ERR_INVALID before
+ * any work is enqueued (out and the scratch are then left untouched).
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  All calls share the array: each call clears what must start at

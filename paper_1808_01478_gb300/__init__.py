@@ -104,10 +104,16 @@ _SIGNATURES = {
     "dh_rdf": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                 ctypes.c_uint64, ctypes.c_void_p], ctypes.c_int),
     "dh_tune_cache_count": ([ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "dh_pipe_rate": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p], ctypes.c_int),
 }
 
 DH_NOALLOC_MAX_N = 131072
 DH_NOALLOC_MAX_BINS = 65536
+
+PIPES = {"ffma2": 0, "fadd2": 1, "fmul2": 2, "ffma": 3, "sqrt": 4, "frnd": 5, "f2i": 6, "lop3": 7,
+         "iadd": 8, "imad": 9, "dfma": 10, "match": 11, "smem_atomic_random": 12,
+         "smem_atomic_clustered": 13, "smem_atomic_same": 14, "smem_atomic_sequential": 15,
+         "global_atomic64": 16}
 
 DH_CHECK_SQRT = 0
 DH_CHECK_WINDOW = 1
@@ -227,6 +233,15 @@ def dh_selfcheck(ctx, what: int, frame: dh_frame | None = None, n_samples: int =
 def dh_histogram_noalloc(frame: dh_frame, stream_ptr: int | None = None) -> None:
     """Allocation-free histogram of one frame with device pointers (no context needed)."""
     _check(load_library().dh_histogram_noalloc(ctypes.byref(frame), ctypes.c_void_p(stream_ptr or 0)))
+
+
+def dh_pipe_rate(device: int, pipe, width: int = 0) -> dict:
+    """Measured throughput of one pipe (see dh.h): ops per clock per SM, ops/s, MHz, ms."""
+    lib = load_library()
+    code = PIPES[pipe] if isinstance(pipe, str) else int(pipe)
+    out = (ctypes.c_double * 4)()
+    _check(lib.dh_pipe_rate(int(device), code, int(width), out))
+    return {"per_clk_sm": out[0], "per_s": out[1], "sm_mhz": out[2], "ms": out[3]}
 
 
 def dh_rdf(ctx, counts_ptr: int, n_hist: int, nbins: int, r_max: float, pair_density, n_frames: int,

@@ -31,6 +31,12 @@ namespace dh {
 
 // ------------------------------------------------------------------ helpers
 
+// Every launcher reports the error of its own launch: a non-sticky error that an
+// earlier, unrelated API call on this thread left behind (this library's or
+// another's) is cleared first.  Errors of kernels already running are sticky
+// and still surface at the next synchronisation.
+static inline void clear_stale_error() { (void)cudaGetLastError(); }
+
 // Order-preserving map float -> int32 (for atomicMin/atomicMax on floats).
 __device__ __forceinline__ int32_t ord_of(float f) {
   int32_t i = __float_as_int(f);
@@ -533,11 +539,13 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
 
 // ------------------------------------------------------------------ A2-A8: pair kernel
 
-// j particles per deferral-mask group: 16 pairs per lane and group whatever the
-// i particles per thread (mask bit = u * RI + r); the j tile is padded to kJUMax
-template <int RI>
-constexpr int ju_of() { return 16 / RI; }
-constexpr int kJUMax = 16;
+// j particles per deferral-mask group: 32 pairs per lane and group without a box
+// and 16 for the periodic variants (whose larger loop bodies, one per tile mode,
+// outgrow the instruction cache when doubled), whatever the i particles per
+// thread (mask bit = u * RI + r); the j tile is padded to kJUMax
+template <int V, int RI>
+constexpr int ju_of() { return (V == V_NONE ? 32 : 16) / RI; }
+constexpr int kJUMax = 32;
 
 // Tile modes of the periodic variants (tile_image): per-pair images, one
 // uniform image, or a uniform image on all axes but one (M_AXIS + a:
@@ -787,7 +795,9 @@ __device__ __forceinline__ float2 wrap_r2_2(float2 dx, float2 dy, float2 dz, con
 // bits(sm) - bits(1.5*2^23) = its nearest integer n) and the residual
 // e = n^2 - q (e > 0: t < n, so floor(t) = n - 1; e < 0: floor(t) = n), the
 // bin relative to the sweep is v - kb1 with v = bits(sm) + signbit(e), and the
-// shared-memory address is 4 v + hbase.  Every pair increments that word.  The
+// shared-memory address is 4 v + hbase (a shift and an add, which stay off the
+// FMA pipe that the packed float32 arithmetic keeps busy; a multiply-add by 4
+// measured 1-2 % slower).  Every pair increments that word.  The
 // clamp of s_c to [lo - lane, hi + 1 + lane] (integers below 2^22) keeps the
 // relative bin in [-1 - lane, width + 1 + lane]: pairs outside the sweep, and
 // NaN pairs (s_c = hi + 1 + lane, e NaN with a clear sign bit: bin width + lane),
@@ -804,7 +814,8 @@ __device__ __forceinline__ void count_or_defer(float sm, float e, float bound, u
       "mov.b32 eb, %2;\n\t"
       "shr.u32 sg, eb, 31;\n\t"
       "add.u32 v, %1, sg;\n\t"
-      "mad.lo.u32 addr, v, 4, %4;\n\t"
+      "shl.b32 addr, v, 2;\n\t"
+      "add.u32 addr, addr, %4;\n\t"
       "abs.f32 ae, %2;\n\t"
       "setp.gtu.f32 pn, ae, %3;\n\t"
       "@!pn or.b32 %0, %0, %5;\n\t"
@@ -1189,7 +1200,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
   const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(sh) - 4u * (uint32_t)P.kb1;
   const float chi = (float)(P.hi + 1 + lane);
   const float clo = (float)(P.lo - lane);
-  constexpr int kJU = ju_of<RI>();
+  constexpr int kJU = ju_of<V, RI>();
   const int nj4 = (je + kJU - 1) & ~(kJU - 1);  // the j tile is padded with NaN particles
   int qcount = 0;
   for (int jj0 = jb; jj0 < nj4; jj0 += kJU) {
@@ -1690,12 +1701,14 @@ __global__ void check_window_kernel(const FrameDev* Fp, uint64_t n_samples, uint
 }
 
 cudaError_t launch_check_sqrt(unsigned long long* out, cudaStream_t stream) {
+  clear_stale_error();
   check_sqrt_kernel<<<1024, 256, 0, stream>>>(out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_check_window(const FrameDev* F, uint64_t n_samples, uint64_t seed, unsigned long long* out,
                                 cudaStream_t stream) {
+  clear_stale_error();
   check_window_kernel<<<1024, 256, 0, stream>>>(F, n_samples, seed, out);
   return cudaGetLastError();
 }
@@ -1821,6 +1834,7 @@ __global__ void check_tiles_kernel(const FrameDev* Fp, uint64_t n_tiles, uint64_
 
 cudaError_t launch_check_tiles(const FrameDev* F, int variant, uint64_t n_tiles, uint64_t seed,
                                unsigned long long* out, cudaStream_t stream) {
+  clear_stale_error();
   if (variant == V_ORTHO) check_tiles_kernel<V_ORTHO><<<456, 256, 0, stream>>>(F, n_tiles, seed, out);
   else if (variant == V_TRIC) check_tiles_kernel<V_TRIC><<<456, 256, 0, stream>>>(F, n_tiles, seed, out);
   else return cudaErrorInvalidValue;
@@ -1851,6 +1865,7 @@ __global__ void rdf_kernel(const uint64_t* __restrict__ counts, int32_t n_hist, 
 
 cudaError_t launch_rdf(const uint64_t* counts, int32_t n_hist, int32_t nbins, double r_max,
                        const double* pair_density, uint64_t n_frames, double* g, cudaStream_t stream) {
+  clear_stale_error();
   int64_t total = (int64_t)n_hist * nbins;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
   rdf_kernel<<<blocks, 256, 0, stream>>>(counts, n_hist, nbins, r_max, pair_density, n_frames, g);
@@ -1858,6 +1873,7 @@ cudaError_t launch_rdf(const uint64_t* counts, int32_t n_hist, int32_t nbins, do
 }
 
 // ------------------------------------------------------------------ launchers
+
 
 size_t pair_kernel_smem(int hist_width, int depth, int block) {
   size_t stride = (size_t)((hist_width + 3) & ~3) + 2 * kGuard;
@@ -1875,13 +1891,22 @@ int pair_kernel_max_width() {
   return (int)(((size_t)optin - fixed) / 4) & ~3;
 }
 
+// Blocks of both instances that fit on one SM with `smem` bytes of dynamic
+// shared memory; 0 (and no error left behind) when the request cannot be met.
 template <int V, int RI>
 int blocks_per_sm_vr(size_t smem) {
   int nb0 = 0, nb1 = 0;
-  cudaFuncSetAttribute(pair_kernel<V, false, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, pair_kernel<V, false, RI>, kTile / RI, smem);
-  cudaFuncSetAttribute(pair_kernel<V, true, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, pair_kernel<V, true, RI>, kTile / RI, smem);
+  if (cudaFuncSetAttribute(pair_kernel<V, false, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, pair_kernel<V, false, RI>, kTile / RI, smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(pair_kernel<V, true, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, pair_kernel<V, true, RI>, kTile / RI, smem) !=
+          cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
   return nb0 < nb1 ? nb0 : nb1;
 }
 
@@ -1902,6 +1927,7 @@ int pair_kernel_blocks_per_sm(int variant, int hist_width, int depth, int block)
 }
 
 cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cudaStream_t stream) {
+  clear_stale_error();
   if (n_jobs <= 0 || n_chunks <= 0) return cudaSuccess;
   stage_kernel<<<(unsigned)n_chunks, 256, 0, stream>>>(jobs, n_jobs);
   return cudaGetLastError();
@@ -1910,6 +1936,7 @@ cudaError_t launch_stage(const StageJob* jobs, int n_jobs, int64_t n_chunks, cud
 cudaError_t launch_spatial_sort(const SortSeg* segs, int n_segs, int max_chunks, float4* X, float4* Xs,
                                 double4* X64, double4* Xs64, int32_t* keys, uint32_t* counts,
                                 cudaStream_t stream) {
+  clear_stale_error();
   if (n_segs <= 0 || max_chunks <= 0) return cudaSuccess;
   dim3 grid((unsigned)max_chunks, (unsigned)n_segs);
   sort_count_kernel<<<grid, 256, 0, stream>>>(segs, X, keys, counts);
@@ -1920,6 +1947,7 @@ cudaError_t launch_spatial_sort(const SortSeg* segs, int n_segs, int max_chunks,
 }
 
 cudaError_t launch_frame_setup(FrameDev* frames, int n_frames, int, cudaStream_t stream) {
+  clear_stale_error();
   if (n_frames <= 0) return cudaSuccess;
   frame_setup_kernel<<<(n_frames + 63) / 64, 64, 0, stream>>>(frames, n_frames);
   return cudaGetLastError();
@@ -1927,6 +1955,7 @@ cudaError_t launch_frame_setup(FrameDev* frames, int n_frames, int, cudaStream_t
 
 cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* status,
                               cudaStream_t stream) {
+  clear_stale_error();
   int threads = 128;
   int blocks = (nbins + 1 + threads - 1) / threads;
   thresholds_kernel<<<blocks, threads, 0, stream>>>(r_max, nbins, T, status);
@@ -1935,6 +1964,7 @@ cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* s
 
 template <int V, bool MULTI, int RI>
 cudaError_t launch_pairs_vmr(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
+  clear_stale_error();
   cudaError_t e =
       cudaFuncSetAttribute(pair_kernel<V, MULTI, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

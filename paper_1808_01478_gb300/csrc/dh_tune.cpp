@@ -23,7 +23,7 @@ int ceil_log2(int64_t v) {
 }
 
 bool valid_shape(const LaunchParams& p) {
-  return (p.jm == 1 || p.jm == 2 || p.jm == 4) && (p.depth == 1 || p.depth == 2 || p.depth == 4) &&
+  return (p.jm == 1 || p.jm == 2 || p.jm == 4) && (p.depth == 1 || p.depth == 2 || p.depth == 4 || p.depth == 8) &&
          p.bps >= 1 && p.bps <= 32 && (p.block == kBlockSmall || p.block == kBlockLarge || p.block == kBlockHuge);
 }
 

@@ -84,6 +84,7 @@ def test_tune_cache_file_parsing(lib, tmp_path):
         "148 2 15 19 0 1024 256 1 3 1000.0",   # another SM count
         "152 2 15 19 0 1000 256 1 3 1000.0",   # tile_j not a power-of-two tile
         "152 2 15 19 0 1024 256 3 3 1000.0",   # depth 3 not offered
+        "152 2 15 19 0 1024 256 16 3 1000.0",  # nor depth 16
         "152 2 15 19 0 1024 384 1 3 1000.0",   # block size not offered
         "152 2 15 19 0 1024 2048 1 3 1000.0",  # nor this one
         "152 9 15 19 0 1024 256 1 3 1000.0",   # unknown variant

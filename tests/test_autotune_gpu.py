@@ -1,7 +1,7 @@
 """Autotuned launch shapes (DH_CFG_AUTOTUNE, dh_config.tune_cache).
 
 Every launch shape the autotuner may pick (j-tile length 256/512/1024, blocks
-of 256, 512 or 1024 threads, one to four private histogram copies per block, blocks
+of 256, 512 or 1024 threads, one to eight histogram copies per block, blocks
 per SM) must give the FP64 oracle's histogram bin for bin; the shapes are forced through the tuner's own
 cache file.  The autotuner must measure each new launch key once, record it in
 the file, and a context that reads the file must use it without measuring.
@@ -76,7 +76,7 @@ FRAMES = {
 }
 SHAPES = [(256, 1, 3, 256), (512, 2, 2, 256), (256, 4, 1, 256), (1024, 2, 3, 256), (512, 4, 2, 256),
           (1024, 1, 1, 256), (1024, 1, 1, 512), (256, 2, 1, 512), (512, 4, 1, 512), (1024, 1, 1, 1024),
-          (256, 2, 1, 1024)]
+          (256, 2, 1, 1024), (1024, 8, 1, 256), (512, 8, 1, 1024), (1024, 4, 1, 1024)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"tj{s[0]}_d{s[1]}_b{s[2]}_t{s[3]}")
