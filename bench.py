@@ -100,16 +100,41 @@ def fp32_lane_ops(box_type: int, f_uni: float, f_axis: float) -> dict:
     return ops
 
 
-def pair_bound(box_type: int, width: int, f_uni: float, f_axis: float, pipes: dict) -> dict:
+def bank_load(f_in: float, trials: int = 4000) -> float:
+    """Expected largest number of distinct words one bank receives in a warp's
+    shared-memory increment when a fraction f_in of its 32 lanes hits uniform
+    random bins and the others their own guard words (one bank each: the
+    clamp sends lane l's out-of-range pairs to the word hi + 1 + l)."""
+    rng = np.random.default_rng(12345)
+    inr = rng.random((trials, 32)) < f_in
+    banks = np.where(inr, rng.integers(0, 32, (trials, 32)), np.arange(32)[None, :])
+    loads = np.zeros((trials, 32))
+    np.add.at(loads, (np.repeat(np.arange(trials), 32), banks.ravel()), 1.0)
+    return float(loads.max(axis=1).mean())
+
+
+def atomic_rate(width: int, f_in: float, pipes: dict) -> float:
+    """Shared-memory increments per clock per SM for a histogram of `width`
+    bins when a fraction f_in of the pairs is inside r_max: the measured rate
+    on uniform random bins (every lane in range), scaled by the expected bank
+    load relative to that case, but never above the conflict-free rate."""
+    key = f"smem_atomic_random@{width}"
+    if key not in pipes:
+        return float("nan")
+    r_rand, r_free = pipes[key]["per_clk_sm"], pipes["smem_atomic_sequential"]["per_clk_sm"]
+    return min(r_free, r_rand * bank_load(1.0) / bank_load(min(1.0, max(0.0, f_in))))
+
+
+def pair_bound(box_type: int, width: int, f_uni: float, f_axis: float, pipes: dict, f_in: float = 1.0) -> dict:
     """Roofline of the pair kernel for one frame in pairs per clock per SM: the
     minimum over pipes of measured rate / operations per pair (float32 FMA
-    pipe, MUFU square root, shared-memory atomic at the frame's width)."""
+    pipe, MUFU square root, shared-memory atomic at the frame's width and
+    fraction f_in of pairs inside r_max)."""
     ops = fp32_lane_ops(box_type, f_uni, f_axis)
     fp32_clk = (ops["fadd"] / pipes["fadd2"]["per_clk_sm"] + ops["fmul"] / pipes["fmul2"]["per_clk_sm"]
                 + ops["ffma"] / pipes["ffma2"]["per_clk_sm"])
-    key = f"smem_atomic_random@{width}"
     bounds = {"fp32": 1.0 / fp32_clk, "mufu": pipes["sqrt"]["per_clk_sm"],
-              "smem_atomic": pipes[key]["per_clk_sm"] if key in pipes else float("nan")}
+              "smem_atomic": atomic_rate(width, f_in, pipes)}
     binding = min((v, k) for k, v in bounds.items() if v == v)[1]
     return {"pairs_per_clk_sm": bounds[binding], "binding": binding,
             "fp32_lane_ops_per_pair": round(sum(ops.values()), 3),
@@ -398,8 +423,8 @@ def run_configs(ctx, stream, dev, args, pipes, mhz, flush_l2):
         st = ctx.stats()
         fu = st["uniform_pairs"] / max(1, st["pairs"])
         fa_ = st["axis_pairs"] / max(1, st["pairs"])
-        bound = pair_bound(f.box_type, f.nbins, fu, fa_, pipes)
         pairs = f.n_pairs()
+        bound = pair_bound(f.box_type, f.nbins, fu, fa_, pipes, int(o.sum().item()) / max(1, pairs))
         out[name] = {"workload": f.name, "pairs": pairs, "gpairs_s": round(pairs / (statistics.median(ts) / 1e3) / 1e9, 3),
                      "ms": round(statistics.median(ts), 4), "pair_kernel_ms": round(statistics.median(pk), 4),
                      "deferred_frac": round(st["deferred"] / max(1, st["pairs"]), 6),
@@ -561,6 +586,8 @@ def scan_frame(box_name: str, n: int, nbins: int):
     """One frame of the scan: uniform at density 0.1, no box (a cube, r_max its
     diagonal), orthorhombic cube (r_max = L/2) or the 70/80/100-degree cell
     (r_max = 0.95 h_min/2)."""
+    if box_name in ("c1", "c2", "c3"):
+        return config_frames()[box_name]
     if box_name == "none":
         side = (n / 0.1) ** (1.0 / 3.0)
         f = w.uniform_frame(101, n, w.BOX_ORTHO, w.ortho_box(side), side * math.sqrt(3.0), nbins)
@@ -591,10 +618,12 @@ def run_scan(args, world, rank, local):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     tmp = tempfile.mkdtemp(prefix="dh_scan_")
     points = [(b, n, k) for b in args.scan_boxes for n in args.scan_particles for k in args.scan_bins]
+    points = list(dict.fromkeys((b, 0, 0) if b.startswith("c") else (b, n, k) for b, n, k in points))
     for box_name, n, nbins in points:
         f = scan_frame(box_name, n, nbins)
+        n, nbins = f.n, f.nbins
         x = torch.from_numpy(f.coords).to(dev)
-        out = torch.zeros((1, nbins), dtype=torch.int64, device=dev)
+        out = torch.zeros((f.n_hist, nbins), dtype=torch.int64, device=dev)
         with dh.Context(local) as c0:  # default shape: learn the sweep width of this frame
             c0.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
             sweeps = c0.stats()["sweeps"]
@@ -602,14 +631,14 @@ def run_scan(args, world, rank, local):
         key = ({w.BOX_NONE: 0, w.BOX_ORTHO: 1}.get(f.box_type, 2), max(0, math.ceil(math.log2(width))),
                math.floor(math.log2(math.sqrt(2.0 * max(f.n_pairs(), 1))) + 0.5), 0)
         ref = None
-        for block, depth in args.scan_shapes:
-            path = os.path.join(tmp, f"t_{box_name}_{n}_{nbins}_{block}_{depth}.txt")
+        for block, depth, agg in args.scan_shapes:
+            path = os.path.join(tmp, f"t_{box_name}_{n}_{nbins}_{block}_{depth}_{agg}.txt")
             with open(path, "w") as fh:
-                fh.write(f"{sms} {key[0]} {key[1]} {key[2]} {key[3]} 1024 {block} {depth} 32 1.0\n")
+                fh.write(f"{sms} {key[0]} {key[1]} {key[2]} {key[3]} 1024 {block} {depth} 32 1.0 {agg}\n")
             with dh.Context(local, flags=dh.DH_CFG_TIMING, tune_cache=path) as ctx:
                 ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins, out)
                 st = ctx.stats()
-                if (st["hist_depth"], st["block_threads"]) != (depth, block):
+                if (st["hist_depth"], st["block_threads"], st["warp_agg"]) != (depth, block, agg):
                     continue  # the copies or the larger block do not fit in shared memory
                 ms = []
                 for _ in range(args.scan_reps):
@@ -619,7 +648,7 @@ def run_scan(args, world, rank, local):
                 ref = got if ref is None else ref
                 print(json.dumps({"scan": "bins x block x depth", "box": box_name, "n": n, "nbins": nbins,
                                   "sweeps": st["sweeps"], "block_threads": block,
-                                  "hist_depth": depth, "blocks_per_sm": st["blocks_per_sm"],
+                                  "hist_depth": depth, "warp_agg": agg, "blocks_per_sm": st["blocks_per_sm"],
                                   "pair_kernel_ms": round(min(ms), 3),
                                   "gpairs_s": round(f.n_pairs() / (min(ms) / 1e3) / 1e9, 2),
                                   "same_as_first_shape": bool(torch.equal(got, ref))}), flush=True)
@@ -704,7 +733,8 @@ def run_gpu(args, world, rank, local):
         st = ctx.stats()
         fu = st["uniform_pairs"] / max(1, st["pairs"])
         fa_ = st["axis_pairs"] / max(1, st["pairs"])
-        bounds[k] = pair_bound(f.box_type, f.nbins, fu, fa_, pipes)
+        f_in = int(OUT[k].sum().item()) / max(1, pairs[k])  # pairs inside r_max
+        bounds[k] = pair_bound(f.box_type, f.nbins, fu, fa_, pipes, f_in)
         plain[w.BOX_NAMES[f.box_type]] = {
             "gpairs_s": round(pairs[k] / (statistics.mean(ts) / 1e3) / 1e9, 3),
             "ms": round(statistics.mean(ts), 3),
@@ -854,11 +884,14 @@ def main(argv=None) -> int:
     ap.add_argument("--scan-bins", type=int, nargs="*",
                     default=[1024, 4096, 16384, 32768, 50000, 60000, 100000, 160000, 250000])
     ap.add_argument("--scan-reps", type=int, default=3)
-    ap.add_argument("--scan-boxes", nargs="*", default=["ortho", "triclinic"], choices=["none", "ortho", "triclinic"])
+    ap.add_argument("--scan-boxes", nargs="*", default=["ortho", "triclinic"],
+                    choices=["none", "ortho", "triclinic", "c1", "c2", "c3"],
+                    help="synthetic frames of each box type, or the configurations C1-C3 as they are")
     ap.add_argument("--scan-shapes", nargs="*", default=["256x1", "256x2", "256x4", "512x1", "512x2", "1024x1"],
-                    help="threads x lane-interleaved histogram copies per block")
+                    help="threads x histogram copies per block, suffix a: warp-aggregated increments")
     args = ap.parse_args(argv)
-    args.scan_shapes = [tuple(int(v) for v in s.split("x")) for s in args.scan_shapes]
+    args.scan_shapes = [(int(s.split("x")[0]), int(s.split("x")[1].rstrip("a")), int(s.endswith("a")))
+                        for s in args.scan_shapes]
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_env()

@@ -132,6 +132,8 @@ typedef struct {
   int32_t block_threads;   /*   and threads per block */
   uint64_t uniform_pairs;  /* pairs evaluated with one nearest image for their whole tile (no per-pair rounding) */
   uint64_t axis_pairs;     /* pairs whose tile image is uniform on all axes but one (that axis wrapped per pair) */
+  int32_t warp_agg;        /* 1 when the largest launch aggregated its increments per warp (tune cache agg) */
+  int32_t reserved;
 } dh_stats;
 
 /* Create a context on config->device (NULL: device 0, defaults).  Owns a CUDA
@@ -218,13 +220,16 @@ dh_status dh_bin_thresholds(double r_max, int32_t nbins, double* thresholds);
  * that dh_create reads and the autotuner rewrites (DH_CFG_AUTOTUNE with
  * dh_config.tune_cache): lines starting with '#' are comments, every other line
  * is one launch key and its measured shape,
- *   sms variant width_log2 n_log2 frames_log4 tile_j block depth bps gpairs_s
+ *   sms variant width_log2 n_log2 frames_log4 tile_j block depth bps gpairs_s [agg]
  * (variant: 0 none, 1 orthorhombic, 2 triclinic, 3 triclinic with the
  * 27-image search; width_log2 = ceil(log2 of the shared-memory histogram
  * width); n_log2 = round(log2 of the mean particles per frame); frames_log4 =
  * min(3, floor(log4 of the frames per launch)); tile_j in {256, 512, 1024};
  * block, the threads per block, in {256, 512, 1024}; depth in {1, 2, 4, 8}; bps, the
- * blocks per SM, >= 1 (at most what fits is used); gpairs_s > 0).  *n_entries receives the number
+ * blocks per SM, >= 1 (at most what fits is used); gpairs_s > 0; agg, optional,
+ * 1 for warp-aggregated histogram increments (match.any: the lanes of a warp
+ * that hit one bin add their count once), only with 256-thread blocks and a
+ * single bin sweep, else 0).  *n_entries receives the number
  * of distinct launch keys with a well-formed line for a GPU with sm_count SMs
  * (a later line replaces an earlier one of the same key); lines for other SM
  * counts and malformed lines are skipped.  DH_ERR_NOTFOUND if the file cannot
@@ -267,8 +272,9 @@ dh_status dh_selfcheck(dh_ctx* ctx, int32_t what, const dh_frame* frame, uint64_
  * in MHz over the measured launch, out[3] = its duration in ms.  An operation
  * is one lane's result (a packed float32x2 instruction counts 2), one shared or
  * global atomic, one match.  width: histogram bins of the atomic benchmarks
- * (shared: 64..57,344 uint32 bins of one block-private histogram; global:
- * 64..2^24 uint64 bins), ignored otherwise.  The call allocates and frees a few
+ * (shared: 64..57,344 uint32 bins of one block-private histogram; cluster:
+ * 64 c..57,344 c bins over a cluster of c blocks; global: 64..2^24 uint64
+ * bins), ignored otherwise.  The call allocates and frees a few
  * small device buffers and its own stream.  DH_ERR_INVALID for an unknown pipe
  * or a width out of range. */
 #define DH_PIPE_FFMA2 0                 /* fma.rn.f32x2 */
@@ -288,6 +294,9 @@ dh_status dh_selfcheck(dh_ctx* ctx, int32_t what, const dh_frame* frame, uint64_
 #define DH_PIPE_SMEM_ATOMIC_SAME 14     /* the same, all lanes of a warp on one bin */
 #define DH_PIPE_SMEM_ATOMIC_SEQUENTIAL 15 /* the same, lane l on bin base + l (no bank conflict) */
 #define DH_PIPE_GLOBAL_ATOMIC64 16      /* atom.global.add.u64, uniform random bins */
+#define DH_PIPE_DSMEM_ATOMIC_C2 17      /* red.shared::cluster.add.u32: one histogram split over a cluster of 2, */
+#define DH_PIPE_DSMEM_ATOMIC_C4 18      /*   4 or 8 blocks (width = the whole histogram), uniform random bins, */
+#define DH_PIPE_DSMEM_ATOMIC_C8 19      /*   most of them in another block's shared memory */
 dh_status dh_pipe_rate(int32_t device, int32_t pipe, int32_t width, double* out);
 
 /* Allocation-free histogram (the paper has no counterpart of this entry point).

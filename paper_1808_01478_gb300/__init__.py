@@ -67,7 +67,8 @@ class dh_stats(ctypes.Structure):
                 ("tune_runs", ctypes.c_int32), ("pair_kernel_ms", ctypes.c_double),
                 ("tile_j", ctypes.c_int32), ("hist_depth", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("uniform_pairs", ctypes.c_uint64), ("axis_pairs", ctypes.c_uint64)]
+                ("uniform_pairs", ctypes.c_uint64), ("axis_pairs", ctypes.c_uint64),
+                ("warp_agg", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -113,7 +114,7 @@ DH_NOALLOC_MAX_BINS = 65536
 PIPES = {"ffma2": 0, "fadd2": 1, "fmul2": 2, "ffma": 3, "sqrt": 4, "frnd": 5, "f2i": 6, "lop3": 7,
          "iadd": 8, "imad": 9, "dfma": 10, "match": 11, "smem_atomic_random": 12,
          "smem_atomic_clustered": 13, "smem_atomic_same": 14, "smem_atomic_sequential": 15,
-         "global_atomic64": 16}
+         "global_atomic64": 16, "dsmem_atomic_c2": 17, "dsmem_atomic_c4": 18, "dsmem_atomic_c8": 19}
 
 DH_CHECK_SQRT = 0
 DH_CHECK_WINDOW = 1

@@ -133,7 +133,7 @@ struct PairLaunch {
   int32_t hist_depth;  // private histogram copies per block (warp w uses copy w mod depth); 0 means 1
   int32_t multi;       // nonzero when some sweep of the launch starts above bin 0
   int32_t block;       // threads per block: kBlockSmall (0 means it), kBlockLarge or kBlockHuge
-  int32_t pad;
+  int32_t agg;         // 256-thread blocks, one sweep: warp-aggregated histogram increments (match.any)
 };
 
 // ---- launchers (dh_kernels.cu); all enqueue on `stream` and return the launch error

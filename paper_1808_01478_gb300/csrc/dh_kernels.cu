@@ -825,6 +825,35 @@ __device__ __forceinline__ void count_or_defer(float sm, float e, float bound, u
       : "r"(__float_as_uint(sm)), "f"(e), "f"(bound), "r"(hbase), "r"(bit));
 }
 
+// The same with the increments of the warp aggregated in software (the hybrid
+// strategy of Sec. 2.4 taken to the warp: lanes that hit one word add their
+// count once): the lanes with equal addresses are found with match.any, and the
+// lowest of them adds their number.  Called by all 32 lanes together.  The
+// address is formed in the same instructions as count_or_defer.
+__device__ __forceinline__ void count_or_defer_agg(float sm, float e, float bound, uint32_t hbase, uint32_t bit,
+                                                   uint32_t& dmask) {
+  asm volatile(
+      "{\n\t.reg .pred pn, pl;\n\t.reg .u32 eb, sg, v, addr, peers, lm, cnt;\n\t.reg .f32 ae;\n\t"
+      "mov.b32 eb, %2;\n\t"
+      "shr.u32 sg, eb, 31;\n\t"
+      "add.u32 v, %1, sg;\n\t"
+      "shl.b32 addr, v, 2;\n\t"
+      "add.u32 addr, addr, %4;\n\t"
+      "abs.f32 ae, %2;\n\t"
+      "setp.gtu.f32 pn, ae, %3;\n\t"
+      "@!pn or.b32 %0, %0, %5;\n\t"
+      "match.any.sync.b32 peers, addr, 0xffffffff;\n\t"
+      "mov.u32 lm, %%lanemask_lt;\n\t"
+      "and.b32 lm, lm, peers;\n\t"
+      "setp.eq.u32 pl, lm, 0;\n\t"
+      "popc.b32 cnt, peers;\n\t"
+      "@pl red.shared.add.u32 [addr], cnt;\n\t"
+      "}"
+      : "+r"(dmask)
+      : "r"(__float_as_uint(sm)), "f"(e), "f"(bound), "r"(hbase), "r"(bit)
+      : "memory");
+}
+
 // The float32 decision of two pairs (j, j+1 against one i).  With q = r^2 S^2
 // (= t^2) and n the integer nearest to the clamped root s_c, the residual
 // e = n^2 - q is rounded once (fma), so its sign gives floor(t) = n or n-1, and
@@ -1158,7 +1187,7 @@ __device__ __forceinline__ int drain_queue(const FrameDev* F, int pass, int i0, 
 // j tile in shared memory as pairs of particles: A[p] = {x_2p, x_2p+1, y_2p, y_2p+1},
 // Z[p] = {z_2p, z_2p+1}, so one LDS.128 + one LDS.64 feed two j particles.
 // j particles [jb, je) of the staged tile (jb a multiple of kSubJ).
-template <int V, bool MASKED, bool MULTI, int RI, int MODE>
+template <int V, bool MASKED, bool MULTI, int RI, int MODE, bool AGG>
 __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
                                          const float4* __restrict__ sjA, const float2* __restrict__ sjZ,
                                          uint32_t* sh, uint32_t* q, int tid, int lane, unsigned& ndeferred,
@@ -1229,8 +1258,13 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
         }
         float2 sm, e, bound;
         decide_arith2<V, MULTI, MODE>(dx, dy, dz, P, chi, clo, sm, e, bound);
-        count_or_defer(sm.x, e.x, bound.x, hbase, 1u << (u * RI + r), dmask);
-        count_or_defer(sm.y, e.y, bound.y, hbase, 1u << ((u + 1) * RI + r), dmask);
+        if (AGG) {
+          count_or_defer_agg(sm.x, e.x, bound.x, hbase, 1u << (u * RI + r), dmask);
+          count_or_defer_agg(sm.y, e.y, bound.y, hbase, 1u << ((u + 1) * RI + r), dmask);
+        } else {
+          count_or_defer(sm.x, e.x, bound.x, hbase, 1u << (u * RI + r), dmask);
+          count_or_defer(sm.y, e.y, bound.y, hbase, 1u << ((u + 1) * RI + r), dmask);
+        }
       }
     }
     // queue the deferred pairs: one per lane per round, compacted with a ballot
@@ -1265,7 +1299,7 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
 // particles; img[c] is this warp's tile image and mode (w) for sub-chunk c.
 // Items that mask j <= i take the per-pair path in the M_AXIS modes (fewer
 // instances; such items are the diagonal of a species block).
-template <int V, bool MULTI, int RI>
+template <int V, bool MULTI, int RI, bool AGG>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
                          uint32_t* q, int tid, int lane, unsigned& ndeferred, const float4* img, const float* tbeta) {
   FastParams P;
@@ -1280,7 +1314,7 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
       // the tile's own beta; masked tiles demoted to per-pair images take the frame's
       if (mode == (int)im.w) set_bound_beta(*F, P, tbeta[c]);
       else set_bound(*F, P, mode);
-#define DH_TILE(M_, K_) run_tile<V, M_, MULTI, RI, K_>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je)
+#define DH_TILE(M_, K_) run_tile<V, M_, MULTI, RI, K_, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je)
       if (it.masked) {
         if (mode == M_UNI) DH_TILE(true, M_UNI);
         else DH_TILE(true, M_PAIR);
@@ -1299,12 +1333,12 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
   }
   const float3 k0 = make_float3(0.f, 0.f, 0.f);
   if (it.masked) {
-    run_tile<V, true, MULTI, RI, M_PAIR>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+    run_tile<V, true, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
   } else if (V == V_NONE && F->in_range && it.ni == kTile && (it.nj % kJUMax) == 0) {
     // every pair real (no NaN padding) and in range: the root needs no clamp
-    run_tile<V, false, MULTI, RI, M_UNI>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+    run_tile<V, false, MULTI, RI, M_UNI, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
   } else {
-    run_tile<V, false, MULTI, RI, M_PAIR>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+    run_tile<V, false, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
   }
 }
 
@@ -1455,7 +1489,8 @@ constexpr int min_blocks_per_sm() {
   return RI < 4 ? 1 : ((V == V_NONE || V == V_ORTHO) ? 3 : 2);
 }
 
-template <int V, bool MULTI, int RI>
+// AGG: the increments of a warp aggregated in software (count_or_defer_agg).
+template <int V, bool MULTI, int RI, bool AGG = false>
 __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_kernel(PairLaunch L) {
   constexpr int BLOCK = kTile / RI;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1592,7 +1627,7 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
         __syncwarp();
       }
       unsigned ndef = 0;
-      run_item<V, MULTI, RI>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, s_img[kTileImage ? warp : 0],
+      run_item<V, MULTI, RI, AGG>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, s_img[kTileImage ? warp : 0],
                              s_beta[kTileImage ? warp : 0]);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
@@ -1913,6 +1948,18 @@ int blocks_per_sm_vr(size_t smem) {
 template <int V>
 int blocks_per_sm_v(int hist_width, int depth, int block) {
   size_t smem = pair_kernel_smem(hist_width, depth, block);
+  if (block == kBlockSmall) {  // the aggregated-increment instance must fit as well
+    int na = 0;
+    if (cudaFuncSetAttribute(pair_kernel<V, false, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&na, pair_kernel<V, false, 4, true>, kBlockSmall, smem) !=
+            cudaSuccess) {
+      (void)cudaGetLastError();
+      return 0;
+    }
+    const int nb = blocks_per_sm_vr<V, 4>(smem);
+    return na < nb ? na : nb;
+  }
   return block == kBlockHuge ? blocks_per_sm_vr<V, 1>(smem)
          : block == kBlockLarge ? blocks_per_sm_vr<V, 2>(smem) : blocks_per_sm_vr<V, 4>(smem);
 }
@@ -1962,18 +2009,20 @@ cudaError_t launch_thresholds(double r_max, int32_t nbins, double* T, int32_t* s
   return cudaGetLastError();
 }
 
-template <int V, bool MULTI, int RI>
+template <int V, bool MULTI, int RI, bool AGG = false>
 cudaError_t launch_pairs_vmr(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
   clear_stale_error();
   cudaError_t e =
-      cudaFuncSetAttribute(pair_kernel<V, MULTI, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(pair_kernel<V, MULTI, RI, AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  pair_kernel<V, MULTI, RI><<<grid, kTile / RI, smem, stream>>>(p);
+  pair_kernel<V, MULTI, RI, AGG><<<grid, kTile / RI, smem, stream>>>(p);
   return cudaGetLastError();
 }
 
 template <int V, bool MULTI>
 cudaError_t launch_pairs_vm(const PairLaunch& p, int grid, size_t smem, cudaStream_t stream) {
+  if constexpr (!MULTI)  // aggregated increments: 256-thread blocks, one sweep
+    if (p.agg && (p.block == kBlockSmall || p.block == 0)) return launch_pairs_vmr<V, false, 4, true>(p, grid, smem, stream);
   return p.block == kBlockHuge    ? launch_pairs_vmr<V, MULTI, 1>(p, grid, smem, stream)
          : p.block == kBlockLarge ? launch_pairs_vmr<V, MULTI, 2>(p, grid, smem, stream)
                                   : launch_pairs_vmr<V, MULTI, 4>(p, grid, smem, stream);

@@ -232,6 +232,44 @@ __global__ void __launch_bounds__(kPeakBlock) smem_atomic_kernel(int iters, uint
   keep_u(s, sink);
 }
 
+// Cluster-distributed histogram increments (red.shared::cluster.add.u32): a
+// cluster of `csize` blocks holds one histogram of `width` bins, block r the
+// bins [r w, (r + 1) w), w = width / csize; every lane increments uniform random
+// bins of the whole histogram, (csize - 1) / csize of them in another block's
+// shared memory.  16 cluster addresses per lane are formed before the timed
+// loop (mapa).  The cluster waits for all its blocks before the first and after
+// the last increment, so that no block leaves while others still write to it.
+constexpr int kClusterBlock = 1024;  // one block per SM holds a large slice: all 32 warps of the SM in it
+__global__ void __launch_bounds__(kClusterBlock) dsmem_atomic_kernel(int iters, uint32_t width, float* sink,
+                                                                  unsigned long long* cycles) {
+  extern __shared__ uint32_t hist[];
+  uint32_t csize, crank;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+  const uint32_t w = width / csize;
+  for (uint32_t k = threadIdx.x; k < w; k += blockDim.x) hist[k] = 0u;
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(hist);
+  uint32_t addr[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const uint32_t b = __umulhi(mixh(threadIdx.x * 0x9E3779B9u + blockIdx.x * 0x85EBCA6Bu + (uint32_t)k * 0x27D4EB2Fu),
+                                w * csize);
+    const uint32_t owner = b / w, local = base + 4u * (b - owner * w);
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(addr[k]) : "r"(local), "r"(owner));
+  }
+  asm volatile("barrier.cluster.arrive.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+  const uint64_t g0 = gtimer_ns(), t0 = clk64();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) asm volatile("red.shared::cluster.add.u32 [%0], 1;" ::"r"(addr[k]) : "memory");
+  }
+  record_cycles(t0, g0, cycles);
+  asm volatile("barrier.cluster.arrive.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+  uint32_t sum = 0;
+  for (uint32_t k = threadIdx.x; k < w; k += blockDim.x) sum += hist[k];
+  keep_u(sum, sink);
+}
+
 // 64-bit global atomics (the A8 merge): `iters` x 4 atomicAdd per thread on
 // uniform random bins of a uint64 array of `width` entries (L2 resident).
 __global__ void __launch_bounds__(kPeakBlock, 8) global_atomic_kernel(int iters, uint32_t width, uint64_t* g,
@@ -267,6 +305,7 @@ PeakSpec spec_of(int pipe) {
     case DH_PIPE_SMEM_ATOMIC_RANDOM: case DH_PIPE_SMEM_ATOMIC_CLUSTERED:
     case DH_PIPE_SMEM_ATOMIC_SAME: case DH_PIPE_SMEM_ATOMIC_SEQUENTIAL: return {16.0, 1024};
     case DH_PIPE_GLOBAL_ATOMIC64: return {4.0, 256};
+    case DH_PIPE_DSMEM_ATOMIC_C2: case DH_PIPE_DSMEM_ATOMIC_C4: case DH_PIPE_DSMEM_ATOMIC_C8: return {16.0, 256};
     default: return {0.0, 0};
   }
 }
@@ -289,8 +328,14 @@ const void* kernel_of(int pipe) {
     case DH_PIPE_SMEM_ATOMIC_CLUSTERED: return (const void*)smem_atomic_kernel<1>;
     case DH_PIPE_SMEM_ATOMIC_SAME: return (const void*)smem_atomic_kernel<2>;
     case DH_PIPE_SMEM_ATOMIC_SEQUENTIAL: return (const void*)smem_atomic_kernel<3>;
+    case DH_PIPE_DSMEM_ATOMIC_C2: case DH_PIPE_DSMEM_ATOMIC_C4: case DH_PIPE_DSMEM_ATOMIC_C8:
+      return (const void*)dsmem_atomic_kernel;
     default: return (const void*)global_atomic_kernel;
   }
+}
+
+int cluster_of(int pipe) {
+  return pipe == DH_PIPE_DSMEM_ATOMIC_C2 ? 2 : pipe == DH_PIPE_DSMEM_ATOMIC_C4 ? 4 : pipe == DH_PIPE_DSMEM_ATOMIC_C8 ? 8 : 1;
 }
 
 }  // namespace
@@ -302,10 +347,12 @@ extern "C" dh_status dh_pipe_rate(int32_t device, int32_t pipe, int32_t width, d
   if (!out) return fail(DH_ERR_INVALID, "out is NULL");
   const PeakSpec sp = spec_of(pipe);
   if (sp.iters == 0) return fail(DH_ERR_INVALID, "unknown pipe %d", pipe);
-  const bool smem = pipe >= DH_PIPE_SMEM_ATOMIC_RANDOM && pipe <= DH_PIPE_SMEM_ATOMIC_SEQUENTIAL;
+  const int csize = cluster_of(pipe);
+  const bool smem = (pipe >= DH_PIPE_SMEM_ATOMIC_RANDOM && pipe <= DH_PIPE_SMEM_ATOMIC_SEQUENTIAL) || csize > 1;
   const bool glob = pipe == DH_PIPE_GLOBAL_ATOMIC64;
-  if ((smem || glob) && (width < 64 || width > (smem ? 56 * 1024 : 1 << 24)))
-    return fail(DH_ERR_INVALID, "width %d outside [64, %d]", width, smem ? 56 * 1024 : 1 << 24);
+  const int wmax = smem ? 56 * 1024 * csize : 1 << 24;
+  if ((smem || glob) && (width < 64 * csize || width > wmax))
+    return fail(DH_ERR_INVALID, "width %d outside [%d, %d]", width, 64 * csize, wmax);
   DH_CUDA_TRY(cudaSetDevice(device));
   int sms = 0;
   DH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
@@ -316,7 +363,7 @@ extern "C" dh_status dh_pipe_rate(int32_t device, int32_t pipe, int32_t width, d
   unsigned long long* cyc = nullptr;
   uint64_t* g = nullptr;
   dh_status result = DH_OK;
-  const size_t smem_bytes = smem ? 4 * (size_t)width : 0;
+  const size_t smem_bytes = smem ? 4 * (size_t)(width / csize) : 0;
   auto run = [&](int iters, int grid) -> cudaError_t {
     switch (pipe) {
       case DH_PIPE_FFMA2: packed_kernel<0><<<grid, kPeakBlock, 0, st>>>(iters, sink, cyc); break;
@@ -339,6 +386,21 @@ extern "C" dh_status dh_pipe_rate(int32_t device, int32_t pipe, int32_t width, d
         smem_atomic_kernel<2><<<grid, kPeakBlock, smem_bytes, st>>>(iters, (uint32_t)width, sink, cyc); break;
       case DH_PIPE_SMEM_ATOMIC_SEQUENTIAL:
         smem_atomic_kernel<3><<<grid, kPeakBlock, smem_bytes, st>>>(iters, (uint32_t)width, sink, cyc); break;
+      case DH_PIPE_DSMEM_ATOMIC_C2: case DH_PIPE_DSMEM_ATOMIC_C4: case DH_PIPE_DSMEM_ATOMIC_C8: {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(kClusterBlock);
+        cfg.dynamicSmemBytes = smem_bytes;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, dsmem_atomic_kernel, iters, (uint32_t)width, sink, cyc);
+      }
       default: global_atomic_kernel<<<grid, kPeakBlock, 0, st>>>(iters, (uint32_t)width, g, cyc); break;
     }
     return cudaGetLastError();
@@ -346,7 +408,7 @@ extern "C" dh_status dh_pipe_rate(int32_t device, int32_t pipe, int32_t width, d
   do {
     cudaError_t e;
     if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess ||
-        (e = cudaMalloc(&sink, sizeof(float) * kPeakBlock)) != cudaSuccess ||
+        (e = cudaMalloc(&sink, sizeof(float) * kClusterBlock)) != cudaSuccess ||
         (e = cudaMalloc(&cyc, 2 * sizeof(unsigned long long))) != cudaSuccess ||
         (glob && (e = cudaMalloc(&g, 8 * (size_t)width)) != cudaSuccess)) {
       result = fail(DH_ERR_CUDA, "dh_pipe_rate setup: %s", cudaGetErrorString(e));
@@ -367,12 +429,32 @@ extern "C" dh_status dh_pipe_rate(int32_t device, int32_t pipe, int32_t width, d
       result = fail(DH_ERR_CUDA, "dh_pipe_rate: %s", cudaGetErrorString(e));
       break;
     }
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kPeakBlock, smem_bytes)) != cudaSuccess ||
+    const int threads = csize > 1 ? kClusterBlock : kPeakBlock;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem_bytes)) != cudaSuccess ||
         bps < 1) {
       result = fail(DH_ERR_CUDA, "dh_pipe_rate: no block fits");
       break;
     }
-    const int grid = sms * bps;
+    int grid = sms * bps;
+    if (csize > 1) {  // whole clusters, as many as are resident at once
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)csize;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)(csize * 64));
+      cfg.blockDim = dim3(kClusterBlock);
+      cfg.dynamicSmemBytes = smem_bytes;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if ((e = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg)) != cudaSuccess || clusters < 1) {
+        result = fail(DH_ERR_CUDA, "dh_pipe_rate: no cluster of %d fits", csize);
+        break;
+      }
+      grid = clusters * csize;
+    }
     // warm-up (clocks up, code loaded), then the measured launch
     if ((e = run(sp.iters / 8 > 0 ? sp.iters / 8 : 1, grid)) != cudaSuccess ||
         (e = cudaMemsetAsync(cyc, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess ||
@@ -388,7 +470,7 @@ extern "C" dh_status dh_pipe_rate(int32_t device, int32_t pipe, int32_t width, d
       result = fail(DH_ERR_CUDA, "dh_pipe_rate: %s", cudaGetErrorString(e));
       break;
     }
-    const double ops = sp.ops_per_iter * (double)sp.iters * (double)kPeakBlock * (double)grid;
+    const double ops = sp.ops_per_iter * (double)sp.iters * (double)threads * (double)grid;
     const double mhz = cg[1] > 0 ? 1e3 * (double)cg[0] / (double)cg[1] : 0.0;
     out[1] = ops / (ms * 1e-3);                                   // per second
     out[0] = mhz > 0.0 ? out[1] / ((double)sms * mhz * 1e6) : 0.0;  // per clock per SM at that clock

@@ -628,6 +628,7 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
       L.hist_depth = P.vparams[v].depth;
       L.multi = P.vmulti[v];
       L.block = P.vparams[v].block;
+      L.agg = (P.vparams[v].agg && L.block == kBlockSmall && !L.multi) ? 1 : 0;
       L.ctl = (Control*)c->ctl.p + v;
       DH_CUDA_TRY(launch_pairs(L, v, P.vgrid[v],
                                pair_kernel_smem(P.vwidth[v], P.vparams[v].depth, P.vparams[v].block), st));
@@ -654,6 +655,7 @@ dh_status record_frames(dh_ctx* c, const std::vector<PlannedFrame>& pfs, CallPla
     S.hist_depth = P.vparams[top].depth;
     S.blocks_per_sm = P.vparams[top].bps;
     S.block_threads = P.vparams[top].block;
+    S.warp_agg = (P.vparams[top].agg && P.vparams[top].block == kBlockSmall && !P.vmulti[top]) ? 1 : 0;
   }
   return DH_OK;
 }
@@ -947,6 +949,17 @@ dh_status tune_variant(dh_ctx* c, int v, const VariantSummary& vs) {
           }
         }
       }
+  // warp-aggregated increments (256-thread blocks, one sweep): the default
+  // shape's copies and blocks with the aggregation
+  if (s == DH_OK && !vs.multi && def.block == kBlockSmall) {
+    LaunchParams p = def;
+    p.agg = 1;
+    s = measure(p, &g);
+    if (s == DH_OK && g > best.gpairs_s && g > 1.02 * g_def) {
+      best.p = p;
+      best.gpairs_s = g;
+    }
+  }
   c->tune_forced = false;
   c->tune_cap_pairs = 0.0;
   if (own_events) {

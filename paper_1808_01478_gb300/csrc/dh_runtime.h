@@ -102,6 +102,7 @@ struct LaunchParams {
   int32_t depth = 1;             // private histogram copies per block
   int32_t bps = 0;               // blocks per SM (0: as many as fit)
   int32_t block = kBlockSmall;   // threads per block (kBlockSmall, kBlockLarge or kBlockHuge)
+  int32_t agg = 0;               // 256-thread blocks, one sweep: warp-aggregated increments
 };
 
 // Autotuner key of a launch: variant, histogram width, frame size, frame count (all bucketed).

@@ -24,16 +24,18 @@ int ceil_log2(int64_t v) {
 
 bool valid_shape(const LaunchParams& p) {
   return (p.jm == 1 || p.jm == 2 || p.jm == 4) && (p.depth == 1 || p.depth == 2 || p.depth == 4 || p.depth == 8) &&
-         p.bps >= 1 && p.bps <= 32 && (p.block == kBlockSmall || p.block == kBlockLarge || p.block == kBlockHuge);
+         p.bps >= 1 && p.bps <= 32 && (p.block == kBlockSmall || p.block == kBlockLarge || p.block == kBlockHuge) &&
+         (p.agg == 0 || (p.agg == 1 && p.block == kBlockSmall));
 }
 
 // One cache line -> (sms, key, entry); false if malformed.
 bool parse_line(const char* line, int* sms, TuneKey* k, TuneEntry* e) {
-  int tile_j = 0;
+  int tile_j = 0, agg = 0;
   double g = 0.0;
-  int n = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %lf", sms, &k->variant, &k->width_log2, &k->n_log2,
-                      &k->frames_log4, &tile_j, &e->p.block, &e->p.depth, &e->p.bps, &g);
-  if (n != 10) return false;
+  int n = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %lf %d", sms, &k->variant, &k->width_log2, &k->n_log2,
+                      &k->frames_log4, &tile_j, &e->p.block, &e->p.depth, &e->p.bps, &g, &agg);
+  if (n != 10 && n != 11) return false;
+  e->p.agg = agg;
   if (tile_j != 256 && tile_j != 512 && tile_j != 1024) return false;
   e->p.jm = kTile / tile_j;
   e->gpairs_s = g;
@@ -111,14 +113,14 @@ bool Tuner::save(const std::string& path, int sms) {
   std::string tmp = path + ".tmp";
   FILE* fp = std::fopen(tmp.c_str(), "w");
   if (!fp) return false;
-  std::fprintf(fp, "# dh autotune cache: sms variant width_log2 n_log2 frames_log4 tile_j block depth bps gpairs_s\n");
+  std::fprintf(fp, "# dh autotune cache: sms variant width_log2 n_log2 frames_log4 tile_j block depth bps gpairs_s agg\n");
   std::fputs(keep.c_str(), fp);
   {
     std::lock_guard<std::mutex> g(mu_);
     for (const auto& kv : map_)
-      std::fprintf(fp, "%d %d %d %d %d %d %d %d %d %.3f\n", sms, kv.first.variant, kv.first.width_log2,
+      std::fprintf(fp, "%d %d %d %d %d %d %d %d %d %.3f %d\n", sms, kv.first.variant, kv.first.width_log2,
                    kv.first.n_log2, kv.first.frames_log4, kTile / kv.second.p.jm, kv.second.p.block,
-                   kv.second.p.depth, kv.second.p.bps, kv.second.gpairs_s);
+                   kv.second.p.depth, kv.second.p.bps, kv.second.gpairs_s, kv.second.p.agg);
   }
   bool ok = std::fclose(fp) == 0;
   return ok && std::rename(tmp.c_str(), path.c_str()) == 0;

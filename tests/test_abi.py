@@ -91,8 +91,11 @@ def test_tune_cache_file_parsing(lib, tmp_path):
         "152 2 15 19 0 1024 256 1 3 -1",       # non-positive throughput
         "152 2 15 19 0 1024 1 3 1000.0",       # a field missing
         "152 3 16 20 1 1024 512 1 2 500.0",
+        "152 0 10 11 0 1024 256 1 3 20.0 1",   # warp-aggregated increments
+        "152 0 10 12 0 1024 512 1 1 20.0 1",   # aggregation needs 256-thread blocks
+        "152 0 10 13 0 1024 256 1 3 20.0 2",   # agg is 0 or 1
     ]) + "\n")
-    assert dh.dh_tune_cache_count(str(p), 152) == 3
+    assert dh.dh_tune_cache_count(str(p), 152) == 4
     assert dh.dh_tune_cache_count(str(p), 148) == 1
     assert dh.dh_tune_cache_count(str(p), 132) == 0
     with pytest.raises(dh.DHError) as e:

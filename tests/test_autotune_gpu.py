@@ -50,10 +50,11 @@ def tune_key(frames):
     return variant_of(frames[0]), wl, nl, f4
 
 
-def write_cache(path, sms, keys, tile_j, depth, bps, block=256):
+def write_cache(path, sms, keys, tile_j, depth, bps, block=256, agg=None):
     lines = ["# forced shapes"]
     for v, wl, nl, f4 in keys:
-        lines.append(f"{sms} {v} {wl} {nl} {f4} {tile_j} {block} {depth} {bps} 1.0")
+        tail = "" if agg is None else f" {agg}"
+        lines.append(f"{sms} {v} {wl} {nl} {f4} {tile_j} {block} {depth} {bps} 1.0{tail}")
     path.write_text("\n".join(lines) + "\n")
 
 
@@ -95,6 +96,31 @@ def test_forced_shapes_match_oracle(torch_mod, oracle_mod, tmp_path, shape):
             assert 1 <= st["blocks_per_sm"] <= bps
             assert st["tune_runs"] == 0
             assert np.array_equal(got, oracle_mod.histogram_frame(f)), name
+
+
+@pytest.mark.parametrize("tile_j", [1024, 256])
+def test_forced_warp_aggregated_increments(torch_mod, oracle_mod, tmp_path, tile_j):
+    # the lanes of a warp that hit one bin add their count once (match.any);
+    # every variant, masked diagonal tiles and ragged tails
+    sms = sm_count(torch_mod)
+    path = tmp_path / "tune.txt"
+    write_cache(path, sms, [tune_key([f]) for f in FRAMES.values()], tile_j, 1, 3, 256, agg=1)
+    with dh.Context(0, tune_cache=str(path)) as ctx:
+        for name, f in FRAMES.items():
+            x = torch_mod.from_numpy(f.coords).cuda()
+            got = ctx.histogram(x, f.offsets, f.box_type, f.box, f.r_max, f.nbins).cpu().numpy().view(np.uint64)
+            st = ctx.stats()
+            assert st["warp_agg"] == 1 and st["block_threads"] == 256 and st["tile_j"] == tile_j, name
+            assert np.array_equal(got, oracle_mod.histogram_frame(f)), name
+        # clustered bins: a small cube whose pairs share few bins
+        g = w.frame_from((w.rng_for(37).random((5000, 3)) * 2.0).astype(np.float32), [0, 5000], w.BOX_NONE,
+                         np.zeros(9), 3.5, 40, "clustered")
+        write_cache(path, sms, [tune_key([g])], tile_j, 1, 3, 256, agg=1)
+    with dh.Context(0, tune_cache=str(path)) as ctx:
+        got = ctx.histogram(torch_mod.from_numpy(g.coords).cuda(), g.offsets, g.box_type, g.box, g.r_max,
+                            g.nbins).cpu().numpy().view(np.uint64)
+        assert ctx.stats()["warp_agg"] == 1
+        assert np.array_equal(got, oracle_mod.histogram_frame(g))
 
 
 def test_forced_shape_multi_sweep(torch_mod, oracle_mod, tmp_path):
