@@ -655,6 +655,28 @@ def run_scan(args, world, rank, local):
     return 0
 
 
+def run_pipes(args, world, rank, local):
+    """Measured throughput of every pipe dh_pipe_rate covers, one JSON line per
+    pipe and width (shared atomics at several histogram widths, cluster atomics
+    at several cluster sizes); not the bench contract line."""
+    import paper_1808_01478_gb300 as dh
+
+    if rank != 0:
+        return 0
+    points = [(name, 0) for name in PIPE_SET]
+    points += [("smem_atomic_random", wd) for wd in (1024, 4096, 10000, 20000, 50000)]
+    points += [("dsmem_atomic_c2", 100000), ("dsmem_atomic_c4", 200000), ("dsmem_atomic_c8", 400000)]
+    points += [("global_atomic64", 10000), ("global_atomic64", 1 << 20)]
+    for name, wd in points:
+        if name.startswith("smem") and wd == 0:
+            wd = 10000
+        r = dh.dh_pipe_rate(local, name, wd)
+        print(json.dumps({"pipe": name, "width": wd, "per_clk_sm": round(r["per_clk_sm"], 3),
+                          "per_s": r["per_s"], "sm_mhz": round(r["sm_mhz"], 1), "ms": round(r["ms"], 3)}),
+              flush=True)
+    return 0
+
+
 def run_gpu(args, world, rank, local):
     import torch
 
@@ -878,6 +900,8 @@ def main(argv=None) -> int:
     ap.add_argument("--no-configs", dest="configs", action="store_false",
                     help="skip the C1-C3 configurations")
     ap.add_argument("--served-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95])
+    ap.add_argument("--pipes", action="store_true",
+                    help="instead of the bench line: the measured throughput of each pipe (dh_pipe_rate)")
     ap.add_argument("--scan", action="store_true",
                     help="instead of the bench line: throughput against nbins and histogram copies")
     ap.add_argument("--scan-particles", type=int, nargs="*", default=[200_000])
@@ -899,6 +923,8 @@ def main(argv=None) -> int:
         return run_reference(args, world, rank)
     if args.scan:
         return run_scan(args, world, rank, local)
+    if args.pipes:
+        return run_pipes(args, world, rank, local)
     return run_gpu(args, world, rank, local)
 
 
