@@ -38,12 +38,25 @@ using Clock = std::chrono::steady_clock;
 
 constexpr size_t kAlign = 256;
 constexpr int kWaveSlots = 4;          // waves that may be in flight at once
+// Histogram-width classes of a wave: one pair-kernel launch per class,
+// ceil(log2 of the sweep width) up to 16 and one class above it.
+constexpr int kWidthClasses = 8;
+int width_class(int width) {
+  int b = 0;
+  while (b < 30 && (1 << b) < width) ++b;
+  return b <= 9 ? 0 : (b >= 16 ? kWidthClasses - 1 : b - 9);
+}
 // Waves in flight per lane.  One: the next wave is built when the running one
 // completes (the scheduler polls every 50 us), so a request that arrives waits
 // for the running wave only, not also for one queued behind it; the idle gap
 // per wave is a few tens of microseconds, and the other lanes fill it.
 constexpr int kWavesAhead = 1;
 constexpr double kWaveSecondsDefault = 0.006;  // target device time of one wave
+// While requests wait for admission (the server is saturated), waves are this
+// many times longer: a wave's tail (its last items finishing on part of the
+// SMs) and the gap before the next wave are then a smaller share of the time,
+// and a new request waits for the queue ahead of it anyway.
+constexpr double kSaturatedWaveFactor = 4.0;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -229,7 +242,7 @@ dh_status Server::start() {
     DH_CUDA_TRY(ln.tstat.ensure(64));
     DH_CUDA_TRY(cudaMemsetAsync(ln.tstat.p, 0, 64, ln.stream));
     for (auto& w : ln.slots) {
-      DH_CUDA_TRY(w.ctl.ensure(sizeof(Control)));
+      DH_CUDA_TRY(w.ctl.ensure(sizeof(Control) * kWidthClasses));
       DH_CUDA_TRY(cudaEventCreate(&w.ev0));
       DH_CUDA_TRY(cudaEventCreate(&w.ev1));
     }
@@ -531,10 +544,16 @@ bool Server::launch_wave(int v) {
   // to the larger ones in equal parts.
   std::stable_sort(run.begin(), run.end(),
                    [](const Request* a, const Request* b) { return a->n_items - a->next < b->n_items - b->next; });
-  double budget_left = ln.rate * wave_seconds_;
-  std::vector<Segment> wsegs;
+  double budget_left = ln.rate * wave_seconds_ * (queue_.empty() ? 1.0 : kSaturatedWaveFactor);
+  // segments per histogram-width class: requests of very different widths run
+  // in separate launches, each with the launch shape of its own width (one
+  // wide request would otherwise give every request of the wave the shape of
+  // the widest histogram: larger blocks and fewer of them per SM)
+  std::vector<Segment> csegs[kWidthClasses];
+  int64_t citems[kWidthClasses] = {};
+  int cwidth[kWidthClasses], cmulti[kWidthClasses] = {};
+  for (int q = 0; q < kWidthClasses; ++q) cwidth[q] = 1;
   int64_t witems = 0;
-  int width = 1, multi = 0;
   double wpairs = 0;
   std::vector<Request*> finishing;
   for (size_t q = 0; q < run.size(); ++q) {
@@ -552,45 +571,59 @@ bool Server::launch_wave(int v) {
     take = std::min(take, r->n_items - r->next);
     budget_left -= (double)take * pairs_per_item;
     int64_t lo = r->next, hi = r->next + take;
+    const int cl = width_class(r->pf.sweep_width);
     for (const Segment& sg : r->segs) {
       int64_t count = sg.intra ? (int64_t)sg.n_ti * (sg.n_ti + 1) / 2 : (int64_t)sg.n_ti * sg.n_tj;
       int64_t a = std::max(lo, sg.item0), b = std::min(hi, sg.item0 + count);
       if (a >= b) continue;
       Segment w = sg;
-      w.item0 = witems;
+      w.item0 = citems[cl];
       w.item_base = a - sg.item0;
+      citems[cl] += b - a;
       witems += b - a;
-      wsegs.push_back(w);
+      csegs[cl].push_back(w);
     }
     r->next = hi;
     r->last_wave = ln.wave_seq + 1;
-    width = std::max(width, r->pf.sweep_width);
-    multi |= r->pf.sweeps > 1;
+    cwidth[cl] = std::max(cwidth[cl], r->pf.sweep_width);
+    cmulti[cl] |= r->pf.sweeps > 1;
     wpairs += (double)std::min<uint64_t>(r->pf.pairs, (uint64_t)((double)take * pairs_per_item));
     if (r->next >= r->n_items) finishing.push_back(r);
   }
   if (witems == 0) return false;
-  size_t bytes = sizeof(Segment) * wsegs.size();
+  size_t nseg = 0;
+  for (int q = 0; q < kWidthClasses; ++q) nseg += csegs[q].size();
+  size_t bytes = sizeof(Segment) * nseg;
   if (W.segs.ensure(bytes) != cudaSuccess || W.hsegs.ensure(bytes) != cudaSuccess) {
     thread_error_ = "out of memory for wave descriptors";
     return false;
   }
-  std::memcpy(W.hsegs.p, wsegs.data(), bytes);
+  size_t at = 0;
+  for (int q = 0; q < kWidthClasses; ++q) {
+    if (!csegs[q].empty()) std::memcpy((Segment*)W.hsegs.p + at, csegs[q].data(), sizeof(Segment) * csegs[q].size());
+    at += csegs[q].size();
+  }
   cudaMemcpyAsync(W.segs.p, W.hsegs.p, bytes, cudaMemcpyHostToDevice, ln.stream);
-  cudaMemsetAsync(W.ctl.p, 0, sizeof(Control), ln.stream);
-  PairLaunch L;
-  std::memset(&L, 0, sizeof L);
-  L.segs = (const Segment*)W.segs.p;
-  L.n_segs = (int32_t)wsegs.size();
-  L.n_items = witems;
-  L.hist_width = width;
-  L.multi = multi;
-  L.block = default_block(v, width);
-  L.ctl = (Control*)W.ctl.p;
-  int bps = pair_kernel_blocks_per_sm(v, width, 1, L.block);
+  cudaMemsetAsync(W.ctl.p, 0, sizeof(Control) * kWidthClasses, ln.stream);
   cudaEventRecord(W.ev0, ln.stream);
-  cudaError_t e = launch_pairs(L, v, pair_grid(ctx_->num_sms, bps, witems), pair_kernel_smem(width, 1, L.block),
-                               ln.stream);
+  cudaError_t e = cudaSuccess;
+  at = 0;
+  for (int q = 0; q < kWidthClasses && e == cudaSuccess; ++q) {
+    if (csegs[q].empty()) continue;
+    PairLaunch L;
+    std::memset(&L, 0, sizeof L);
+    L.segs = (const Segment*)W.segs.p + at;
+    L.n_segs = (int32_t)csegs[q].size();
+    L.n_items = citems[q];
+    L.hist_width = cwidth[q];
+    L.multi = cmulti[q];
+    L.block = default_block(v, cwidth[q]);
+    L.ctl = (Control*)W.ctl.p + q;
+    const int bps = pair_kernel_blocks_per_sm(v, cwidth[q], 1, L.block);
+    e = launch_pairs(L, v, pair_grid(ctx_->num_sms, bps, citems[q]), pair_kernel_smem(cwidth[q], 1, L.block),
+                     ln.stream);
+    at += csegs[q].size();
+  }
   cudaEventRecord(W.ev1, ln.stream);
   if (e != cudaSuccess) thread_error_ = cudaGetErrorString(e);
   W.busy = true;
