@@ -143,7 +143,8 @@ def pair_bound(box_type: int, width: int, f_uni: float, f_axis: float, pipes: di
 
 def roofline_entry(pairs: float, seconds: float, mhz: float, bound: dict) -> dict:
     """Achieved pairs per clock per SM (at the SM clock sampled under load)
-    against the frame's bound."""
+    against the frame's bound; `pairs` are the pairs the kernel evaluated (its
+    tiles skipped as out of range or out of the sweep are not counted)."""
     achieved = pairs / seconds / (SM_COUNT * mhz * 1e6)
     return {"achieved_pairs_per_clk_sm": round(achieved, 3), "bound_pairs_per_clk_sm": round(bound["pairs_per_clk_sm"], 3),
             "frac": round(achieved / bound["pairs_per_clk_sm"], 4), "binding": bound["binding"],
@@ -421,16 +422,18 @@ def run_configs(ctx, stream, dev, args, pipes, mhz, flush_l2):
             ts.append(e0.elapsed_time(e1))
             pk.append(ctx.stats()["pair_kernel_ms"])
         st = ctx.stats()
-        fu = st["uniform_pairs"] / max(1, st["pairs"])
-        fa_ = st["axis_pairs"] / max(1, st["pairs"])
         pairs = f.n_pairs()
-        bound = pair_bound(f.box_type, f.nbins, fu, fa_, pipes, int(o.sum().item()) / max(1, pairs))
+        f_cull = st["culled_pairs"] / max(1, st["pairs"] * st["sweeps"])
+        ev = pairs * (1.0 - f_cull)
+        fu = st["uniform_pairs"] / max(1.0, ev)
+        fa_ = st["axis_pairs"] / max(1.0, ev)
+        bound = pair_bound(f.box_type, f.nbins, fu, fa_, pipes, int(o.sum().item()) / max(1.0, ev))
         out[name] = {"workload": f.name, "pairs": pairs, "gpairs_s": round(pairs / (statistics.median(ts) / 1e3) / 1e9, 3),
                      "ms": round(statistics.median(ts), 4), "pair_kernel_ms": round(statistics.median(pk), 4),
                      "deferred_frac": round(st["deferred"] / max(1, st["pairs"]), 6),
                      "binary64_frac": round(st["exact_fallback"] / max(1, st["pairs"]), 8),
-                     "tile_image_frac": round(fu, 4), "axis_image_frac": round(fa_, 4),
-                     "roofline": roofline_entry(pairs, statistics.median(pk) / 1e3, mhz, bound)}
+                     "tile_image_frac": round(fu, 4), "axis_image_frac": round(fa_, 4), "culled_frac": round(f_cull, 4),
+                     "roofline": roofline_entry(ev, statistics.median(pk) / 1e3, mhz, bound)}
         del x, o
     return out
 
@@ -650,6 +653,7 @@ def run_scan(args, world, rank, local):
                                   "sweeps": st["sweeps"], "block_threads": block,
                                   "hist_depth": depth, "warp_agg": agg, "blocks_per_sm": st["blocks_per_sm"],
                                   "pair_kernel_ms": round(min(ms), 3),
+                                  "culled_frac": round(st["culled_pairs"] / max(1, st["pairs"] * st["sweeps"]), 4),
                                   "gpairs_s": round(f.n_pairs() / (min(ms) / 1e3) / 1e9, 2),
                                   "same_as_first_shape": bool(torch.equal(got, ref))}), flush=True)
     return 0
@@ -739,6 +743,7 @@ def run_gpu(args, world, rank, local):
     # ---- plain per-frame path (and the pair kernel's own device time per frame)
     plain = {}
     bounds = {}
+    evaluated = {}
     for k, f in enumerate(frames):
         ctx.histogram(X[k], f.offsets, f.box_type, f.box, f.r_max, f.nbins, OUT[k])
         ts, pk = [], []
@@ -755,7 +760,10 @@ def run_gpu(args, world, rank, local):
         st = ctx.stats()
         fu = st["uniform_pairs"] / max(1, st["pairs"])
         fa_ = st["axis_pairs"] / max(1, st["pairs"])
-        f_in = int(OUT[k].sum().item()) / max(1, pairs[k])  # pairs inside r_max
+        f_cull = st["culled_pairs"] / max(1, st["pairs"] * st["sweeps"])  # of the pairs of all sweeps
+        evaluated[k] = pairs[k] * (1.0 - f_cull)
+        f_in = int(OUT[k].sum().item()) / max(1.0, evaluated[k])  # evaluated pairs inside r_max
+        fu, fa_ = fu / (1.0 - f_cull) if f_cull < 1 else 0.0, fa_ / (1.0 - f_cull) if f_cull < 1 else 0.0
         bounds[k] = pair_bound(f.box_type, f.nbins, fu, fa_, pipes, f_in)
         plain[w.BOX_NAMES[f.box_type]] = {
             "gpairs_s": round(pairs[k] / (statistics.mean(ts) / 1e3) / 1e9, 3),
@@ -764,7 +772,8 @@ def run_gpu(args, world, rank, local):
             "deferred_frac": round(st["deferred"] / max(1, st["pairs"]), 6),
             "tile_image_frac": round(fu, 4),
             "axis_image_frac": round(fa_, 4),
-            "roofline": roofline_entry(pairs[k], statistics.mean(pk) / 1e3, mhz, bounds[k]),
+            "culled_frac": round(f_cull, 4),
+            "roofline": roofline_entry(evaluated[k], statistics.mean(pk) / 1e3, mhz, bounds[k]),
         }
 
     # ---- roofline of the pair kernel in the timed batched steps: pairs per
@@ -772,13 +781,15 @@ def run_gpu(args, world, rank, local):
     # the step's frames, min over pipes of measured rate / operations per pair,
     # scaled by the SMs and the median SM clock sampled during the timed steps
     mean_pair_s = statistics.mean(pair_ms) / 1e3
-    clk_per_step = sum(p / bounds[k]["pairs_per_clk_sm"] for k, p in enumerate(pairs))  # SM-clocks
-    peak_gpairs = pairs_step / clk_per_step * SM_COUNT * mhz * 1e6 / 1e9
-    achieved_gpairs = pairs_step / mean_pair_s / 1e9
+    eval_step = sum(evaluated.values())
+    clk_per_step = sum(evaluated[k] / bounds[k]["pairs_per_clk_sm"] for k in range(len(pairs)))  # SM-clocks
+    peak_gpairs = eval_step / clk_per_step * SM_COUNT * mhz * 1e6 / 1e9
+    achieved_gpairs = eval_step / mean_pair_s / 1e9
     headline_size = (args.n, args.nbins) == (1_000_000, 10_000)
     traffic = committed_traffic() if headline_size else None
     roofline = {"bound": "alu", "achieved": round(achieved_gpairs, 3), "peak": round(peak_gpairs, 3),
-                "unit": "Gpairs/s", "frac": round(achieved_gpairs / peak_gpairs, 4), "traffic": traffic,
+                "unit": "Gpairs/s (evaluated: pairs of tiles skipped as outside the bins not counted)",
+                "frac": round(achieved_gpairs / peak_gpairs, 4), "traffic": traffic,
                 "traffic_basis": ("DRAM bytes read + written by the step's three pair-kernel launches (ncu, "
                                   f"{TRAFFIC_FILE}); algorithmic: 3 x (16 B x N + 8 B x nbins)"
                                   if traffic else None),

@@ -134,6 +134,8 @@ typedef struct {
   uint64_t axis_pairs;     /* pairs whose tile image is uniform on all axes but one (that axis wrapped per pair) */
   int32_t warp_agg;        /* 1 when the largest launch aggregated its increments per warp (tune cache agg) */
   int32_t reserved;
+  uint64_t culled_pairs;   /* pairs (counted once per bin sweep) of tiles skipped because their distance
+                              bounds put no pair in the sweep's bins (periodic frames) */
 } dh_stats;
 
 /* Create a context on config->device (NULL: device 0, defaults).  Owns a CUDA

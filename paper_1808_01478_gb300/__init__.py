@@ -68,7 +68,8 @@ class dh_stats(ctypes.Structure):
                 ("tile_j", ctypes.c_int32), ("hist_depth", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("uniform_pairs", ctypes.c_uint64), ("axis_pairs", ctypes.c_uint64),
-                ("warp_agg", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("warp_agg", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("culled_pairs", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -74,6 +74,7 @@ struct FrameDev {
   unsigned long long exact;     // pairs that also needed the binary64 replay
   unsigned long long uniform_pairs;  // pairs of (warp i run, j tile) blocks with one nearest image for all
   unsigned long long axis_pairs;     // pairs of such blocks whose image is uniform on all axes but one
+  unsigned long long culled_pairs;   // pairs of blocks skipped: no pair of them has its bin in the sweep
 };
 
 // One species pair (a,b) of one frame and one bin sweep, cut into kTile x kTile

@@ -553,6 +553,7 @@ constexpr int kJUMax = 32;
 // No box: M_UNI marks a tile of an in-range frame without padding, whose
 // roots need no clamp.
 constexpr int M_PAIR = 0, M_UNI = 1, M_AXIS = 2;
+constexpr int M_SKIP = -1;  // a tile none of whose pairs has its bin in the current sweep
 constexpr bool shifted_mode(int mode) { return mode >= M_UNI; }
 
 struct FastParams {
@@ -1310,6 +1311,7 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
       const float4 im = img[c];
       const float3 kt = make_float3(im.x, im.y, im.z);
       int mode = (int)im.w;
+      if (mode == M_SKIP) continue;  // no pair of this tile has its bin in the sweep
       if (it.masked && mode >= M_AXIS) mode = M_PAIR;
       // the tile's own beta; masked tiles demoted to per-pair images take the frame's
       if (mode == (int)im.w) set_bound_beta(*F, P, tbeta[c]);
@@ -1398,6 +1400,104 @@ __device__ float4 tile_image(const FrameDev& F, const float* imin, const float* 
     if (!(nint_scaled(xhi, F.invf[0]) == kx) || fabsf(kx) > 1.0f) return make_float4(0.f, ky, kz, (float)M_AXIS);
     return make_float4(kx, ky, kz, (float)M_UNI);
   }
+}
+
+// Range [lo, hi] of a real value (outward-rounded float32 bounds) and its
+// distance from zero, its largest magnitude, and its distance from the lattice
+// L Z for a period known to lie in [L - dL, L + dL] (all rounded so as to stay
+// bounds: distances down, magnitudes up).
+__device__ __forceinline__ float iv_dist0(float lo, float hi) { return lo > 0.0f ? lo : (hi < 0.0f ? -hi : 0.0f); }
+__device__ __forceinline__ float iv_absmax(float lo, float hi) { return fmaxf(fabsf(lo), fabsf(hi)); }
+__device__ __forceinline__ float iv_dist_lattice(float lo, float hi, float L, float dL, float invL) {
+  // the nearest multiples of the period lie among m - 1 .. m + 2, m = floor(hi / L)
+  // taken with the rounded reciprocal invL (within one of the exact floor)
+  const float m = floorf(hi * invL);
+  float d = INFINITY;
+#pragma unroll
+  for (int q = -1; q <= 2; ++q) {
+    const float k = m + (float)q, ak = fabsf(k);
+    const float x_hi = __fadd_ru(__fmul_ru(k, L), __fmul_ru(ak, dL));  // k * (true period), bounds
+    const float x_lo = __fsub_rd(__fmul_rd(k, L), __fmul_ru(ak, dL));
+    d = fminf(d, fmaxf(0.0f, fmaxf(__fsub_rd(lo, x_hi), __fsub_rd(x_lo, hi))));
+  }
+  return d;
+}
+
+// Whether no pair of a warp tile (i run bounds imin..imax, j sub-chunk bounds
+// jmin..jmax, tile image img from tile_image) can have its binary64 bin in
+// [lo_bin, hi_bin): then the tile contributes nothing to this sweep and is
+// skipped (the tile analogue of a cell list).  Bounds on the exact minimum-image
+// distance r of every pair, in float32 with directed rounding: per axis, the
+// displacement range [jmin - imax, jmax - imin] (widened by the binary64-input
+// conversion error), minus the tile's uniform image where it has one (the box
+// vectors within their float32 rounding error dBf of binary64), or, on an axis
+// wrapped per pair, at least its distance from the lattice and at most half the
+// period.  Pairs with r below r_max have the same nearest images in float32 and
+// binary64 (the frame's precondition), and a translate shorter than
+// r_max <= h_min/2 is the minimum image, so a tile whose image-based distances all
+// lie outside the sweep's distances has no pair in the sweep.  The sweep's edges
+// are widened by 2^-16 (relative) for the float32 roundings here and the
+// binary64 roundings of r and of floor(nbins r / r_max).  Orthorhombic: every
+// mode; triclinic: uniform tiles and tiles uniform on all axes but x (per-pair
+// tiles are never skipped).
+template <int V>
+__device__ bool tile_outside_sweep(const FrameDev& F, const float* imin, const float* imax, const float* jmin,
+                                   const float* jmax, float4 img, int lo_bin, int hi_bin) {
+  const int mode = (int)img.w;
+  if (F.all_defer || (V == V_TRIC && mode == M_PAIR)) return false;
+  float lo[3], hi[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float cv = 2.0f * F.convf[c];
+    lo[c] = __fsub_rd(__fsub_rd(jmin[c], imax[c]), cv);
+    hi[c] = __fadd_ru(__fsub_ru(jmax[c], imin[c]), cv);
+  }
+  float l[3], u[3];
+  const float* b = F.Bf;
+  const float* db = F.dBf;
+  if (V == V_ORTHO) {
+    const float kk[3] = {img.x, img.y, img.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float L = b[4 * c], dL = db[4 * c];
+      if (mode == M_PAIR || mode == M_AXIS + c) {  // wrapped per pair
+        l[c] = iv_dist_lattice(lo[c], hi[c], L, dL, F.invf[c]);
+        u[c] = __fmul_ru(__fadd_ru(L, dL), 0.5f);
+      } else {  // |k| <= 1: the true shift lies in [k L32 - |k| dL, k L32 + |k| dL]
+        const float s = kk[c] * L, e = fabsf(kk[c]) * dL;
+        const float a = __fsub_rd(lo[c], __fadd_ru(s, e)), z = __fsub_ru(hi[c], __fsub_rd(s, e));
+        l[c] = iv_dist0(a, z);
+        u[c] = iv_absmax(a, z);
+      }
+    }
+  } else {  // V_TRIC: the image vector B k (kx = 0 in the M_AXIS mode), each term |k| <= 1
+    const float kx = img.x, ky = img.y, kz = img.z;
+    const float ex = fabsf(kx) * db[0] + fabsf(ky) * db[1] + fabsf(kz) * db[2];
+    const float ey = fabsf(ky) * db[4] + fabsf(kz) * db[5], ez = fabsf(kz) * db[8];
+    const float sx_hi = __fadd_ru(__fadd_ru(__fadd_ru(kx * b[0], ky * b[1]), kz * b[2]), __fmul_ru(ex, 1.0f + 0x1p-20f));
+    const float sx_lo = __fsub_rd(__fadd_rd(__fadd_rd(kx * b[0], ky * b[1]), kz * b[2]), __fmul_ru(ex, 1.0f + 0x1p-20f));
+    const float sy_hi = __fadd_ru(__fadd_ru(ky * b[4], kz * b[5]), __fmul_ru(ey, 1.0f + 0x1p-20f));
+    const float sy_lo = __fsub_rd(__fadd_rd(ky * b[4], kz * b[5]), __fmul_ru(ey, 1.0f + 0x1p-20f));
+    const float sz_hi = __fadd_ru(kz * b[8], ez), sz_lo = __fsub_rd(kz * b[8], ez);
+    const float ax = __fsub_rd(lo[0], sx_hi), bx = __fsub_ru(hi[0], sx_lo);
+    const float ay = __fsub_rd(lo[1], sy_hi), by = __fsub_ru(hi[1], sy_lo);
+    const float az = __fsub_rd(lo[2], sz_hi), bz = __fsub_ru(hi[2], sz_lo);
+    if (mode == M_UNI) {
+      l[0] = iv_dist0(ax, bx);
+      u[0] = iv_absmax(ax, bx);
+    } else {  // x wrapped per pair along a
+      l[0] = iv_dist_lattice(ax, bx, b[0], db[0], F.invf[0]);
+      u[0] = __fmul_ru(__fadd_ru(b[0], db[0]), 0.5f);
+    }
+    l[1] = iv_dist0(ay, by); u[1] = iv_absmax(ay, by);
+    l[2] = iv_dist0(az, bz); u[2] = iv_absmax(az, bz);
+  }
+  const float lb2 = __fmaf_rd(l[2], l[2], __fmaf_rd(l[1], l[1], __fmul_rd(l[0], l[0])));
+  const float ub2 = __fmaf_ru(u[2], u[2], __fmaf_ru(u[1], u[1], __fmul_ru(u[0], u[0])));
+  // the sweep's edges in distance (squared), widened
+  const float dr = (float)(F.r_max / (double)F.nbins);
+  const float r_lo = (float)lo_bin * dr, r_hi = (hi_bin >= F.nbins) ? (float)F.r_max : (float)hi_bin * dr;
+  return (lo_bin > 0 && ub2 < r_lo * r_lo * (1.0f - 0x1p-16f)) || lb2 >= r_hi * r_hi * (1.0f + 0x1p-16f);
 }
 
 // Adds the `depth` private copies (stride words apart) bin by bin into the
@@ -1611,17 +1711,26 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
         }
         __syncthreads();
         const int ni_w = min(32 * RI, it.ni - warp * 32 * RI);  // i particles of this warp
+        const int lo_bin = it.pass * F.sweep_width, hi_bin = min(F.nbins, lo_bin + F.sweep_width);
         for (int c = 0; c * kSubJ < it.nj; ++c) {
           float4 img = make_float4(0.f, 0.f, 0.f, 0.f);
           if (ni_w > 0) img = tile_image<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3);
           const float tb = tile_beta<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3, img);
+          const unsigned long long np =
+              (unsigned long long)max(ni_w, 0) * (unsigned long long)(min(it.nj, (c + 1) * kSubJ) - c * kSubJ);
+          const bool skip = ni_w > 0 && tile_outside_sweep<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3, img, lo_bin,
+                                                             hi_bin);
           if (lane == 0) {
+            if (skip) {
+              img.w = (float)M_SKIP;
+              atomicAdd(&it.fd->culled_pairs, np);
+            } else if (img.w == (float)M_UNI) {
+              atomicAdd(&it.fd->uniform_pairs, np);
+            } else if (img.w >= (float)M_AXIS) {
+              atomicAdd(&it.fd->axis_pairs, np);
+            }
             s_img[warp][c] = img;
             s_beta[warp][c] = tb;
-            const unsigned long long np =
-                (unsigned long long)ni_w * (unsigned long long)(min(it.nj, (c + 1) * kSubJ) - c * kSubJ);
-            if (img.w == (float)M_UNI) atomicAdd(&it.fd->uniform_pairs, np);
-            else if (img.w >= (float)M_AXIS) atomicAdd(&it.fd->axis_pairs, np);
           }
         }
         __syncwarp();

@@ -688,6 +688,7 @@ dh_status finish_frames(dh_ctx* c, int k) {
     c->stats.exact_fallback += hF[f].exact;
     c->stats.uniform_pairs += hF[f].uniform_pairs;
     c->stats.axis_pairs += hF[f].axis_pairs;
+    c->stats.culled_pairs += hF[f].culled_pairs;
     if (hF[f].bad) return fail(DH_ERR_INVALID, "frame %d has non-finite coordinates", f);
   }
   return DH_OK;

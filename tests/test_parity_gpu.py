@@ -242,3 +242,24 @@ def test_tile_images_at_larger_n_match_the_unsorted_path(ctx, torch_mod, oracle_
         want = oracle_mod.histogram_one(g.coords, g.offsets, g.box_type, g.box, g.r_max, g.nbins, a, c)
         assert np.array_equal(h[k], want), (a, c)
     assert np.array_equal(h.sum(0), got[0])  # the split histograms add up to the frame's
+
+
+@pytest.mark.parametrize("box_type,n,nbins", [(w.BOX_ORTHO, 40000, 150_000), (w.BOX_TRICLINIC, 30000, 120_000),
+                                              (w.BOX_ORTHO, 60000, 10_000)])
+def test_tiles_outside_the_sweep_are_skipped(ctx, torch_mod, oracle_mod, box_type, n, nbins):
+    # spatially sorted periodic frames at density 0.1: warp tiles whose distance
+    # bounds put no pair in the current bin sweep (or beyond r_max) are skipped;
+    # several sweeps, and one, against the oracle bin for bin
+    if box_type == w.BOX_ORTHO:
+        box = w.ortho_box((n / 0.1) ** (1.0 / 3.0))
+        r_max = box[0] / 2.0
+    else:
+        box = w.scale_box(w.triclinic_box(1.0, 1.0, 1.0, *w.C3_ANGLES), n / 0.1)
+        r_max = 0.95 * float(w.box_heights(box).min()) / 2.0
+    f = w.uniform_frame(66, n, box_type, box, r_max, nbins, n_species=2)
+    got = gpu_hist(ctx, torch_mod, f)
+    st = ctx.stats()
+    assert st["culled_pairs"] > 0, st
+    if nbins > 100_000:
+        assert st["sweeps"] >= 2, st
+    assert_same(got, oracle_mod.histogram_frame(f), f"cull-{n}-{nbins}")
