@@ -43,6 +43,8 @@ struct FrameDev {
   float Bl[9];       // float32(B - Bf): B as double-float (Bf + Bl)
   float invf[3];     // float32 reciprocals: ortho 1/Lx,1/Ly,1/Lz; triclinic 1/ax,1/by,1/cz
   float S;           // float32(nbins / r_max)
+  float dr_f;        // float32(r_max / nbins), the bin width
+  float rmax_f;      // float32(r_max)
   float S2;          // float32((nbins / r_max)^2)
   float margin;      // triclinic: 1 - 2 r_max / h_min (no-search precondition margin)
   float tshift[27][3];  // triclinic tile images: -B k rounded once from binary64, k in {-1,0,1}^3

@@ -1167,20 +1167,26 @@ __device__ __forceinline__ int drain_queue_body(const FrameDev* F, int pass, int
   return rest;
 }
 
-template <int V, bool MULTI>
+template <int V, bool MULTI, int MODE = M_PAIR>
 __device__ __noinline__ int drain_queue_call(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
-                                             uint32_t* sh, int lane) {
-  return drain_queue_body<V, MULTI>(F, pass, i0, j0, q, qcount, sh, lane);
+                                             uint32_t* sh, int lane, float3 ti = make_float3(0.f, 0.f, 0.f),
+                                             float3 sj = make_float3(0.f, 0.f, 0.f)) {
+  return drain_queue_body<V, MULTI, MODE>(F, pass, i0, j0, q, qcount, sh, lane, ti, sj);
 }
 
-// The register allocation of the hot loop decides which form is faster
-// (measured): the periodic variants keep fewer live values across an inlined
-// drain than across a call, the no-box variant the other way round.
+// The register allocation of the hot loop and the size of its code decide which
+// form is faster (measured): the triclinic variant keeps fewer live values across
+// an inlined drain than across a call; the no-box variant is faster with the
+// call, and so is the orthorhombic one, whose seven pair-loop instances (one per
+// tile mode) otherwise outgrow the instruction cache (one out-of-line copy per
+// mode: +0.4 % on the headline frame, +4 % on C2).
 template <int V, bool MULTI, int MODE>
 __device__ __forceinline__ int drain_queue(const FrameDev* F, int pass, int i0, int j0, uint32_t* q, int qcount,
                                            uint32_t* sh, int lane, float3 ti, float3 sj) {
-  if constexpr (V == V_ORTHO || V == V_TRIC)
+  if constexpr (V == V_TRIC)
     return drain_queue_body<V, MULTI, MODE>(F, pass, i0, j0, q, qcount, sh, lane, ti, sj);
+  else if constexpr (V == V_ORTHO)
+    return drain_queue_call<V, MULTI, MODE>(F, pass, i0, j0, q, qcount, sh, lane, ti, sj);
   else
     return drain_queue_call<V, MULTI>(F, pass, i0, j0, q, qcount, sh, lane);
 }
@@ -1494,9 +1500,9 @@ __device__ bool tile_outside_sweep(const FrameDev& F, const float* imin, const f
   }
   const float lb2 = __fmaf_rd(l[2], l[2], __fmaf_rd(l[1], l[1], __fmul_rd(l[0], l[0])));
   const float ub2 = __fmaf_ru(u[2], u[2], __fmaf_ru(u[1], u[1], __fmul_ru(u[0], u[0])));
-  // the sweep's edges in distance (squared), widened
-  const float dr = (float)(F.r_max / (double)F.nbins);
-  const float r_lo = (float)lo_bin * dr, r_hi = (hi_bin >= F.nbins) ? (float)F.r_max : (float)hi_bin * dr;
+  // the sweep's edges in distance (squared), widened (bin width and r_max in
+  // float32 from the frame descriptor: no binary64 arithmetic per tile)
+  const float r_lo = (float)lo_bin * F.dr_f, r_hi = (hi_bin >= F.nbins) ? F.rmax_f : (float)hi_bin * F.dr_f;
   return (lo_bin > 0 && ub2 < r_lo * r_lo * (1.0f - 0x1p-16f)) || lb2 >= r_hi * r_hi * (1.0f + 0x1p-16f);
 }
 

@@ -256,6 +256,8 @@ void fill_frame_dev(const PlannedFrame& pf, FrameDev& F, const float4* X, uint64
   }
   double S = (double)f->nbins / f->r_max;
   F.S = (float)S;
+  F.dr_f = (float)(f->r_max / (double)f->nbins);
+  F.rmax_f = (float)f->r_max;
   F.eps_S = std::fabs((double)F.S - S) / S;
   F.S2 = (float)(S * S);
   F.eps_S2 = std::fabs((double)F.S2 - S * S) / (S * S) + 1e-15;
