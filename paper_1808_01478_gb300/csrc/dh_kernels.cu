@@ -1444,13 +1444,13 @@ __device__ __forceinline__ float iv_dist_lattice(float lo, float hi, float L, fl
 // lie outside the sweep's distances has no pair in the sweep.  The sweep's edges
 // are widened by 2^-16 (relative) for the float32 roundings here and the
 // binary64 roundings of r and of floor(nbins r / r_max).  Orthorhombic: every
-// mode; triclinic: uniform tiles and tiles uniform on all axes but x (per-pair
-// tiles are never skipped).
+// mode; triclinic: uniform tiles and tiles uniform on all axes but x, and
+// per-pair tiles by their z and y components alone (below).
 template <int V>
 __device__ bool tile_outside_sweep(const FrameDev& F, const float* imin, const float* imax, const float* jmin,
                                    const float* jmax, float4 img, int lo_bin, int hi_bin) {
   const int mode = (int)img.w;
-  if (F.all_defer || (V == V_TRIC && mode == M_PAIR)) return false;
+  if (F.all_defer) return false;
   float lo[3], hi[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -1461,6 +1461,31 @@ __device__ bool tile_outside_sweep(const FrameDev& F, const float* imin, const f
   float l[3], u[3];
   const float* b = F.Bf;
   const float* db = F.dBf;
+  if (V == V_TRIC && mode == M_PAIR) {
+    // Per-pair images: every image vector d - B k has z component d_z - kz cz and
+    // y component d_y - ky by - kz cy, so |d - B k|^2 is at least, for its kz,
+    // the z residual squared plus the distance of the y range shifted by kz cy
+    // from the lattice by Z, squared.  When the z range is shorter than cz, only
+    // the kz nearest to it can give less than cz^2 > r_max^2: the lower bound is
+    // the minimum over those; only pairs beyond the sweep are skipped this way.
+    if (!(__fsub_ru(hi[2], lo[2]) < b[8] - db[8])) return false;
+    // (m is within one of the exact floor M; M - 1 .. M + 1 are the kz that matter)
+    const float m = floorf(hi[2] * F.invf[2]);
+    float best = INFINITY;
+#pragma unroll
+    for (int q = -2; q <= 2; ++q) {
+      const float kz = m + (float)q, ak = fabsf(kz);
+      const float sz_hi = __fadd_ru(__fmul_ru(kz, b[8]), __fmul_ru(ak, db[8]));
+      const float sz_lo = __fsub_rd(__fmul_rd(kz, b[8]), __fmul_ru(ak, db[8]));
+      const float sy_hi = __fadd_ru(__fmul_ru(kz, b[5]), __fmul_ru(ak, db[5]));
+      const float sy_lo = __fsub_rd(__fmul_rd(kz, b[5]), __fmul_ru(ak, db[5]));
+      const float dz = iv_dist0(__fsub_rd(lo[2], sz_hi), __fsub_ru(hi[2], sz_lo));
+      const float dy = iv_dist_lattice(__fsub_rd(lo[1], sy_hi), __fsub_ru(hi[1], sy_lo), b[4], db[4], F.invf[1]);
+      best = fminf(best, __fmaf_rd(dz, dz, __fmul_rd(dy, dy)));
+    }
+    const float r_hi = (hi_bin >= F.nbins) ? F.rmax_f : (float)hi_bin * F.dr_f;
+    return best >= r_hi * r_hi * (1.0f + 0x1p-16f);
+  }
   if (V == V_ORTHO) {
     const float kk[3] = {img.x, img.y, img.z};
 #pragma unroll
