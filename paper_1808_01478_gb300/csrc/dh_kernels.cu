@@ -944,12 +944,15 @@ __device__ __forceinline__ DF two_prod(float a, float b) {
   float p = __fmul_rn(a, b);
   return {p, __fmaf_rn(a, b, -p)};
 }
-// v - k (bh + bl) for a small integer k
+// v - k (bh + bl) for an integer k, renormalised: after a large image is
+// taken off, the low part of v (the rounding error of a difference of large
+// coordinates) can be far above an ulp of the small result, and the products
+// of df_norm2 are accurate only for a normalised pair (|l| <= ulp(h) / 2)
 __device__ __forceinline__ DF df_sub_kb(DF v, float k, float bh, float bl) {
   DF p = two_prod(k, bh);
   DF s = two_sum(v.h, -p.h);
   float low = __fmaf_rn(-k, bl, __fsub_rn(__fadd_rn(v.l, s.l), p.l));
-  return {s.h, low};
+  return two_sum(s.h, low);
 }
 __device__ __forceinline__ DF df_norm2(DF x, DF y, DF z) {
   DF ax = two_prod(x.h, x.h), ay = two_prod(y.h, y.h), az = two_prod(z.h, z.h);
@@ -970,7 +973,7 @@ __device__ __forceinline__ DF df_diff64(double xj, double xi) {
   const float hj = __double2float_rn(xj), hi = __double2float_rn(xi);
   const float lj = __double2float_rn(__dsub_rn(xj, (double)hj)), li = __double2float_rn(__dsub_rn(xi, (double)hi));
   DF s = two_sum(hj, -hi);
-  return {s.h, __fadd_rn(s.l, __fsub_rn(lj, li))};
+  return two_sum(s.h, __fadd_rn(s.l, __fsub_rn(lj, li)));  // renormalised (see df_sub_kb)
 }
 
 // Bin of a deferred pair from r^2 evaluated in double-float arithmetic (about
@@ -1013,6 +1016,16 @@ __device__ int mid_bin(const FrameDev& F, int i, int j, float4 pi, float4 pj) {
     dx = df_sub_kb(df_sub_kb(df_sub_kb(dx, kz, F.Bf[2], F.Bl[2]), ky, F.Bf[1], F.Bl[1]), kx, F.Bf[0], F.Bl[0]);
     dy = df_sub_kb(df_sub_kb(dy, kz, F.Bf[5], F.Bl[5]), ky, F.Bf[4], F.Bl[4]);
     dz = df_sub_kb(dz, kz, F.Bf[8], F.Bl[8]);
+    // The images are the float32 path's; they are the exact sequential nearest
+    // planes along c, b, a (Babai's step, whose vector is the minimum image of
+    // every pair closer than half the smallest plane spacing) when the wrapped
+    // components lie strictly inside half the periods cz, by, ax: checked here on
+    // the accurate values (the frame's float32 errors may be too large for the
+    // images of its float32 path, e.g. far-unwrapped coordinates).  Otherwise the
+    // binary64 replay decides.
+    const float lim = 0.5f - 0x1p-20f;
+    if (!(fabsf(dz.h * F.invf[2]) < lim && fabsf(dy.h * F.invf[1]) < lim && fabsf(dx.h * F.invf[0]) < lim))
+      return -1;
   }
   DF r2 = df_norm2(dx, dy, dz);
   float s = sqrt_approx(__fmul_rn(r2.h, F.S2));

@@ -263,3 +263,28 @@ def test_tiles_outside_the_sweep_are_skipped(ctx, torch_mod, oracle_mod, box_typ
     if nbins > 100_000:
         assert st["sweeps"] >= 2, st
     assert_same(got, oracle_mod.histogram_frame(f), f"cull-{n}-{nbins}")
+
+
+@pytest.mark.parametrize("cells", [3000, 40000])
+def test_far_unwrapped_triclinic_coordinates(ctx, torch_mod, oracle_mod, cells):
+    # particles of a 20 A triclinic cell moved by random lattice vectors of up to
+    # `cells` cells (unwrapped trajectories): the coordinate ranges are so wide
+    # that the float32 nearest images cannot be trusted, so every pair is
+    # decided without them; r_max just below half the smallest plane spacing
+    box = w.triclinic_box(20, 20, 20, *w.C3_ANGLES)
+    h = float(w.box_heights(box).min())
+    f0 = w.uniform_frame(67, 1500, w.BOX_TRICLINIC, box, 0.99 * h / 2.0, 800, n_species=2)
+    k = w.rng_for(68).integers(-cells, cells + 1, size=(f0.n, 3)).astype(np.float64)
+    x = (f0.coords.astype(np.float64) + k @ w.box_matrix(box).T).astype(np.float32)
+    f = w.frame_from(x, f0.offsets, f0.box_type, f0.box, f0.r_max, f0.nbins, f"tric-unwrapped-{cells}")
+    assert_same(gpu_hist(ctx, torch_mod, f), oracle_mod.histogram_frame(f), f.name)
+
+
+@pytest.mark.parametrize("cells", [3000, 200000])
+def test_far_unwrapped_orthorhombic_coordinates(ctx, torch_mod, oracle_mod, cells):
+    box = w.ortho_box(20.0, 17.0, 23.0)
+    f0 = w.uniform_frame(69, 1500, w.BOX_ORTHO, box, 8.4, 800, n_species=2)
+    k = w.rng_for(70).integers(-cells, cells + 1, size=(f0.n, 3)).astype(np.float64)
+    x = (f0.coords.astype(np.float64) + k * np.array([20.0, 17.0, 23.0])).astype(np.float32)
+    f = w.frame_from(x, f0.offsets, f0.box_type, f0.box, f0.r_max, f0.nbins, f"ortho-unwrapped-{cells}")
+    assert_same(gpu_hist(ctx, torch_mod, f), oracle_mod.histogram_frame(f), f.name)
