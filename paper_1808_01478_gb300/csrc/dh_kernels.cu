@@ -1001,10 +1001,14 @@ __device__ int mid_bin(const FrameDev& F, int i, int j, float4 pi, float4 pj) {
     dx = df_sub_kb(dx, kx, F.Bf[0], F.Bl[0]);
     dy = df_sub_kb(dy, ky, F.Bf[4], F.Bl[4]);
     dz = df_sub_kb(dz, kz, F.Bf[8], F.Bl[8]);
-    // float32 and binary64 may pick different images near |d'_c| = L_c/2
+    // float32 and binary64 may pick different images near |d'_c| = L_c/2; and the
+    // images must be nearest at all (the nearest integer via 1.5 2^23 is exact
+    // only below 2^22 cells): the wrapped components strictly inside L_c/2
     if (fabsf(fabsf(dx.h) - 0.5f * F.Bf[0]) <= F.tie_eps || fabsf(fabsf(dy.h) - 0.5f * F.Bf[4]) <= F.tie_eps ||
         fabsf(fabsf(dz.h) - 0.5f * F.Bf[8]) <= F.tie_eps)
       return -1;
+    const float lim = 0.5f - 0x1p-20f;
+    if (!(fabsf(dx.h * F.invf[0]) < lim && fabsf(dy.h * F.invf[1]) < lim && fabsf(dz.h * F.invf[2]) < lim)) return -1;
   } else if (V == V_TRIC) {
     // the nearest-image integers of the float32 path, replayed exactly
     float kz = nint_scaled(dz.h, F.invf[2]);

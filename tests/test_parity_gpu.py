@@ -280,7 +280,7 @@ def test_far_unwrapped_triclinic_coordinates(ctx, torch_mod, oracle_mod, cells):
     assert_same(gpu_hist(ctx, torch_mod, f), oracle_mod.histogram_frame(f), f.name)
 
 
-@pytest.mark.parametrize("cells", [3000, 200000])
+@pytest.mark.parametrize("cells", [3000, 200000, 3000000])
 def test_far_unwrapped_orthorhombic_coordinates(ctx, torch_mod, oracle_mod, cells):
     box = w.ortho_box(20.0, 17.0, 23.0)
     f0 = w.uniform_frame(69, 1500, w.BOX_ORTHO, box, 8.4, 800, n_species=2)
