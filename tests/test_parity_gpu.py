@@ -288,3 +288,30 @@ def test_far_unwrapped_orthorhombic_coordinates(ctx, torch_mod, oracle_mod, cell
     x = (f0.coords.astype(np.float64) + k * np.array([20.0, 17.0, 23.0])).astype(np.float32)
     f = w.frame_from(x, f0.offsets, f0.box_type, f0.box, f0.r_max, f0.nbins, f"ortho-unwrapped-{cells}")
     assert_same(gpu_hist(ctx, torch_mod, f), oracle_mod.histogram_frame(f), f.name)
+
+
+def test_far_offset_no_box(ctx, torch_mod, oracle_mod):
+    # a compact cluster far from the origin: differences of large, close coordinates
+    rng = w.rng_for(71)
+    x = (1.0e6 + rng.random((2500, 3)) * 30.0).astype(np.float32)
+    f = w.frame_from(x, [0, 1200, 2500], w.BOX_NONE, np.zeros(9), 40.0, 3000, "nobox-offset")
+    assert_same(gpu_hist(ctx, torch_mod, f), oracle_mod.histogram_frame(f), f.name)
+
+
+@pytest.mark.parametrize("box_type,cells", [(w.BOX_TRICLINIC, 5000), (w.BOX_ORTHO, 100000)])
+def test_far_unwrapped_binary64_input(ctx, torch_mod, oracle_mod, box_type, cells):
+    # binary64 coordinates (all 53 bits used) spread over many cells
+    if box_type == w.BOX_TRICLINIC:
+        box = w.triclinic_box(20, 20, 20, *w.C3_ANGLES)
+        r_max = 0.95 * float(w.box_heights(box).min()) / 2.0
+    else:
+        box = w.ortho_box(20.0, 17.0, 23.0)
+        r_max = 8.4
+    rng = w.rng_for(72)
+    m = w.box_matrix(box)
+    x = (m @ rng.random((1500, 3)).T).T
+    x = x + (rng.integers(-cells, cells + 1, size=(1500, 3)).astype(np.float64) @ m.T)
+    offs = w.even_offsets(1500, 2)
+    want = oracle_mod.histogram(x, offs, box_type, box, r_max, 700)
+    got = ctx.histogram(torch_mod.from_numpy(x).cuda(), offs, box_type, box, r_max, 700)
+    assert_same(got.cpu().numpy().view(np.uint64), want, "f64-unwrapped")
