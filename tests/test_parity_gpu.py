@@ -315,3 +315,22 @@ def test_far_unwrapped_binary64_input(ctx, torch_mod, oracle_mod, box_type, cell
     want = oracle_mod.histogram(x, offs, box_type, box, r_max, 700)
     got = ctx.histogram(torch_mod.from_numpy(x).cuda(), offs, box_type, box, r_max, 700)
     assert_same(got.cpu().numpy().view(np.uint64), want, "f64-unwrapped")
+
+
+@pytest.mark.parametrize("box_type", [w.BOX_ORTHO, w.BOX_TRICLINIC])
+def test_half_box_ties_on_a_lattice(ctx, torch_mod, oracle_mod, box_type):
+    # an integer lattice in a box of side 16: many displacements are exactly
+    # L/2 = 8 on one or more axes, where the nearest image of Eq. 5 is a tie
+    # (half to even in binary64 and in float32); r_max beyond L/2 (orthorhombic)
+    # and beyond half the plane spacing (triclinic: the 27-image search)
+    g = np.arange(16, dtype=np.float32)
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)[::3].copy()
+    if box_type == w.BOX_ORTHO:
+        box, r_max, nbins = w.ortho_box(16.0), 12.0, 48
+    else:
+        box = np.array([16.0, 4.0, 2.0, 0.0, 16.0, 4.0, 0.0, 0.0, 16.0])
+        r_max, nbins = 10.0, 40
+    f = w.frame_from(x, [0, 600, x.shape[0]], box_type, box, r_max, nbins, "half-box-ties")
+    got = gpu_hist(ctx, torch_mod, f)
+    assert ctx.stats()["deferred"] > 0
+    assert_same(got, oracle_mod.histogram_frame(f), f.name)
