@@ -788,7 +788,9 @@ def run_gpu(args, world, rank, local):
     headline_size = (args.n, args.nbins) == (1_000_000, 10_000)
     traffic = committed_traffic() if headline_size else None
     roofline = {"bound": "alu", "achieved": round(achieved_gpairs, 3), "peak": round(peak_gpairs, 3),
-                "unit": "Gpairs/s (evaluated: pairs of tiles skipped as outside the bins not counted)",
+                "unit": "Gpairs/s",
+                "achieved_basis": ("pairs the pair kernel evaluated (tiles skipped as outside the bins are not "
+                                   "counted) over the CUDA-event time of its launches in the timed steps"),
                 "frac": round(achieved_gpairs / peak_gpairs, 4), "traffic": traffic,
                 "traffic_basis": ("DRAM bytes read + written by the step's three pair-kernel launches (ncu, "
                                   f"{TRAFFIC_FILE}); algorithmic: 3 x (16 B x N + 8 B x nbins)"
