@@ -78,3 +78,18 @@ def test_random_frame_matches_oracle(torch_mod, oracle_mod, k):
     assert got.shape == want.shape
     bad = np.argwhere(got != want)
     assert bad.size == 0, (k, box_type, x.dtype, x.shape[0], nbins, r_max, len(bad), bad[:3].tolist())
+
+
+def test_random_frames_batched(torch_mod, oracle_mod):
+    # the same generator through dh_histogram_batch (one persistent launch per
+    # variant present, replayed as a CUDA graph), 12 frames per call
+    frames = [random_frame(k) for k in range(500, 524)]
+    with dh.Context(0) as ctx:
+        for b in range(0, len(frames), 12):
+            chunk = frames[b:b + 12]
+            fas = [dh.FrameArgs(torch_mod.from_numpy(x).cuda(), o, bt, bx, r, nb) for (x, o, bt, bx, r, nb) in chunk]
+            ctx.histogram_batch(fas)
+            assert ctx.stats()["graph_replays"] == 1
+            for q, (fa, f) in enumerate(zip(fas, chunk)):
+                got = fa.out.cpu().numpy().view(np.uint64)
+                assert np.array_equal(got, oracle_mod.histogram(*f)), b + q
