@@ -64,6 +64,7 @@ struct FrameDev {
   int32_t bad;       // a non-finite coordinate was seen
   int32_t all_defer; // float32 decisions are not safe for this frame: every pair is deferred
   int32_t in_range;  // no box, one sweep: every pair's root stays below nbins + 1 (the clamp is a no-op)
+  int32_t cull_ok;   // no box: tiles can lie outside a sweep (several sweeps, or r_max below the extent)
   float beta_u;      // beta of tiles that take a uniform image (orthorhombic, triclinic)
   float beta_w[3];   // beta of tiles with a uniform image on all axes but a, wrapped per pair
   float tie_m[3];    // orthorhombic: margin of the uniform-image test (0: not needed)

@@ -208,11 +208,18 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {  // bit k of v -> bit 
   return v;
 }
 
-// Morton cell of a particle from its fractional coordinates in the box
-// (approximate float32; only the order depends on it).
+// Morton cell of a particle from its fractional coordinates in the box, or in
+// the frame's bounding box without one (approximate float32; only the order
+// depends on it).
 __device__ __forceinline__ uint32_t cell_key(const FrameDev& F, float4 p, int g) {
   float s[3];
-  if (F.variant == V_ORTHO) {
+  if (F.variant == V_NONE) {
+    const float q[3] = {p.x, p.y, p.z};
+    for (int c = 0; c < 3; ++c) {
+      const float lo = float_of_ord(F.cmin[c]), hi = float_of_ord(F.cmax[c]);
+      s[c] = (hi > lo) ? fminf((q[c] - lo) / (hi - lo), 0.999999f) : 0.0f;
+    }
+  } else if (F.variant == V_ORTHO) {
     s[0] = p.x * F.invf[0];
     s[1] = p.y * F.invf[1];
     s[2] = p.z * F.invf[2];
@@ -534,6 +541,8 @@ __global__ void frame_setup_kernel(FrameDev* frames, int n_frames) {
     const double D = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
     F.in_range = F.variant == V_NONE && F.sweep_width >= F.nbins && !all_defer &&
                  S * D * (1.0 + 1.0 / 262144.0) < (double)F.nbins + 1.0;
+    // no box: bounding tiles pays only when some tile can miss a sweep
+    F.cull_ok = F.variant == V_NONE && (F.sweep_width < F.nbins || F.r_max < D);
   }
 }
 
@@ -1325,7 +1334,8 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
 // instances; such items are the diagonal of a species block).
 template <int V, bool MULTI, int RI, bool AGG>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
-                         uint32_t* q, int tid, int lane, unsigned& ndeferred, const float4* img, const float* tbeta) {
+                         uint32_t* q, int tid, int lane, unsigned& ndeferred, const float4* img, const float* tbeta,
+                         bool bounds) {
   FastParams P;
   load_fast_params(*F, it.pass, P);
   if (V == V_ORTHO || V == V_TRIC) {
@@ -1357,6 +1367,15 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
     return;
   }
   const float3 k0 = make_float3(0.f, 0.f, 0.f);
+  if (V == V_NONE && bounds) {  // sub-chunk by sub-chunk, culled ones skipped
+    for (int c = 0; c * kSubJ < it.nj; ++c) {
+      if ((int)img[c].w == M_SKIP) continue;
+      const int jb = c * kSubJ, je = min(it.nj, jb + kSubJ);
+      if (it.masked) run_tile<V, true, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, jb, je);
+      else run_tile<V, false, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, jb, je);
+    }
+    return;
+  }
   if (it.masked) {
     run_tile<V, true, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
   } else if (V == V_NONE && F->in_range && it.ni == kTile && (it.nj % kJUMax) == 0) {
@@ -1467,7 +1486,7 @@ template <int V>
 __device__ bool tile_outside_sweep(const FrameDev& F, const float* imin, const float* imax, const float* jmin,
                                    const float* jmax, float4 img, int lo_bin, int hi_bin) {
   const int mode = (int)img.w;
-  if (F.all_defer) return false;
+  if (V != V_NONE && F.all_defer) return false;  // (the no-box bound needs no images)
   float lo[3], hi[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -1503,7 +1522,13 @@ __device__ bool tile_outside_sweep(const FrameDev& F, const float* imin, const f
     const float r_hi = (hi_bin >= F.nbins) ? F.rmax_f : (float)hi_bin * F.dr_f;
     return best >= r_hi * r_hi * (1.0f + 0x1p-16f);
   }
-  if (V == V_ORTHO) {
+  if (V == V_NONE) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      l[c] = iv_dist0(lo[c], hi[c]);
+      u[c] = iv_absmax(lo[c], hi[c]);
+    }
+  } else if (V == V_ORTHO) {
     const float kk[3] = {img.x, img.y, img.z};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -1652,11 +1677,14 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
   uint32_t* sq = reinterpret_cast<uint32_t*>(sjZ + kTile / 2);
   __shared__ ItemDesc s_it;
   constexpr bool kTileImage = (V == V_ORTHO || V == V_TRIC);
+  // tile bounds: always with tile images; without a box for frames whose tiles
+  // can miss a sweep (FrameDev::cull_ok), for culling only
+  constexpr bool kTileBounds = kTileImage || V == V_NONE;
   // per j sub-chunk: j min xyz, j max xyz; per warp and sub-chunk: the tile image
-  __shared__ float s_bnd[kTileImage ? kTile / kSubJ : 1][6];
-  __shared__ float4 s_img[kTileImage ? BLOCK / 32 : 1][kTileImage ? kTile / kSubJ : 1];
+  __shared__ float s_bnd[kTileBounds ? kTile / kSubJ : 1][6];
+  __shared__ float4 s_img[kTileBounds ? BLOCK / 32 : 1][kTileBounds ? kTile / kSubJ : 1];
   __shared__ float s_beta[kTileImage ? BLOCK / 32 : 1][kTileImage ? kTile / kSubJ : 1];  // per-tile beta
-  static_assert(!kTileImage || BLOCK / 32 >= kTile / kSubJ, "one warp per j sub-chunk");
+  static_assert(!kTileBounds || BLOCK / 32 >= kTile / kSubJ, "one warp per j sub-chunk");
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* q = sq + warp * kQueueCap;
@@ -1721,7 +1749,8 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
       // tile images: the bounds of this warp's i run against those of each
       // j sub-chunk of kSubJ particles (warp c reduces sub-chunk c)
       float ib_[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-      if (kTileImage) {
+      const bool bounds = kTileImage || (V == V_NONE && F.cull_ok);  // the same for the whole block
+      if (bounds) {
         const int ib = warp * (32 * RI) + lane;  // this warp's i run (the particles run_tile gives it)
         for (int r = 0; r < RI; ++r) {
           const int li = ib + 32 * r;
@@ -1738,7 +1767,7 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
           }
       }
       __syncthreads();
-      if (kTileImage) {
+      if (bounds) {
         if (warp * kSubJ < it.nj) {
           float jm[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
           const int ke = min(it.nj, (warp + 1) * kSubJ);
@@ -1762,8 +1791,11 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
         const int lo_bin = it.pass * F.sweep_width, hi_bin = min(F.nbins, lo_bin + F.sweep_width);
         for (int c = 0; c * kSubJ < it.nj; ++c) {
           float4 img = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (ni_w > 0) img = tile_image<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3);
-          const float tb = tile_beta<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3, img);
+          float tb = 0.0f;
+          if (kTileImage) {
+            if (ni_w > 0) img = tile_image<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3);
+            tb = tile_beta<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3, img);
+          }
           const unsigned long long np =
               (unsigned long long)max(ni_w, 0) * (unsigned long long)(min(it.nj, (c + 1) * kSubJ) - c * kSubJ);
           const bool skip = ni_w > 0 && tile_outside_sweep<V>(F, ib_, ib_ + 3, s_bnd[c], s_bnd[c] + 3, img, lo_bin,
@@ -1778,14 +1810,14 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
               atomicAdd(&it.fd->axis_pairs, np);
             }
             s_img[warp][c] = img;
-            s_beta[warp][c] = tb;
+            if (kTileImage) s_beta[warp][c] = tb;
           }
         }
         __syncwarp();
       }
       unsigned ndef = 0;
-      run_item<V, MULTI, RI, AGG>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, s_img[kTileImage ? warp : 0],
-                             s_beta[kTileImage ? warp : 0]);
+      run_item<V, MULTI, RI, AGG>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, s_img[kTileBounds ? warp : 0],
+                             s_beta[kTileImage ? warp : 0], bounds);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();

@@ -278,7 +278,7 @@ std::vector<SortSeg> plan_spatial_order(const PlannedFrame& pf, const FrameDev* 
   std::vector<SortSeg> out;
   *keys = 0;
   *chunks = 0;
-  if (pf.variant != V_ORTHO && pf.variant != V_TRIC) return out;
+  if (pf.variant == V_TRIC_SEARCH) return out;
   const int64_t* o = pf.src->species_offsets;
   for (int a = 0; a < pf.src->n_species; ++a) {
     const int64_t na = o[a + 1] - o[a];

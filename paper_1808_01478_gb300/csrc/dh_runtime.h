@@ -124,8 +124,8 @@ TuneKey make_tune_key(int variant, int width, double mean_pairs_per_frame, int f
 // Bytes of a frame's coordinate array (float32 or binary64, 3 or 4 per particle).
 size_t coord_bytes(const dh_frame* f);
 
-// Species of orthorhombic and triclinic frames are put in spatial (Morton)
-// order before the pair kernel, from this many particles on, with about 16
+// Species of frames without the 27-image search are put in spatial (Morton)
+// order before the pair kernel (no box: over the frame's bounding box), from this many particles on, with about 16
 // particles per cell.  plan_spatial_order lists the species of one frame (its
 // particles from x0 in the packed coordinates, its counters from key0) and
 // returns the counters and most staging chunks they need.

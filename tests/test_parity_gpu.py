@@ -245,18 +245,25 @@ def test_tile_images_at_larger_n_match_the_unsorted_path(ctx, torch_mod, oracle_
 
 
 @pytest.mark.parametrize("box_type,n,nbins", [(w.BOX_ORTHO, 40000, 150_000), (w.BOX_TRICLINIC, 30000, 120_000),
-                                              (w.BOX_ORTHO, 60000, 10_000)])
+                                              (w.BOX_ORTHO, 60000, 10_000), (w.BOX_NONE, 40000, 150_000),
+                                              (w.BOX_NONE, 50000, 5_000)])
 def test_tiles_outside_the_sweep_are_skipped(ctx, torch_mod, oracle_mod, box_type, n, nbins):
     # spatially sorted periodic frames at density 0.1: warp tiles whose distance
     # bounds put no pair in the current bin sweep (or beyond r_max) are skipped;
     # several sweeps, and one, against the oracle bin for bin
-    if box_type == w.BOX_ORTHO:
-        box = w.ortho_box((n / 0.1) ** (1.0 / 3.0))
-        r_max = box[0] / 2.0
+    if box_type == w.BOX_NONE:  # a cube, r_max its diagonal (several sweeps) or a fifth of it (one)
+        side = (n / 0.1) ** (1.0 / 3.0)
+        r_max = side * math.sqrt(3.0) * (1.0 if nbins > 100_000 else 0.2)
+        g = w.uniform_frame(66, n, w.BOX_ORTHO, w.ortho_box(side), r_max, nbins, n_species=2)
+        f = w.frame_from(g.coords, g.offsets, w.BOX_NONE, np.zeros(9), r_max, nbins, "nobox-cull")
     else:
-        box = w.scale_box(w.triclinic_box(1.0, 1.0, 1.0, *w.C3_ANGLES), n / 0.1)
-        r_max = 0.95 * float(w.box_heights(box).min()) / 2.0
-    f = w.uniform_frame(66, n, box_type, box, r_max, nbins, n_species=2)
+        if box_type == w.BOX_ORTHO:
+            box = w.ortho_box((n / 0.1) ** (1.0 / 3.0))
+            r_max = box[0] / 2.0
+        else:
+            box = w.scale_box(w.triclinic_box(1.0, 1.0, 1.0, *w.C3_ANGLES), n / 0.1)
+            r_max = 0.95 * float(w.box_heights(box).min()) / 2.0
+        f = w.uniform_frame(66, n, box_type, box, r_max, nbins, n_species=2)
     got = gpu_hist(ctx, torch_mod, f)
     st = ctx.stats()
     assert st["culled_pairs"] > 0, st
