@@ -1219,14 +1219,15 @@ __device__ __forceinline__ int drain_queue(const FrameDev* F, int pass, int i0, 
 
 // j tile in shared memory as pairs of particles: A[p] = {x_2p, x_2p+1, y_2p, y_2p+1},
 // Z[p] = {z_2p, z_2p+1}, so one LDS.128 + one LDS.64 feed two j particles.
-// j particles [jb, je) of the staged tile (jb a multiple of kSubJ).
+// The i run `run` of the item (32 * RI consecutive i particles, lane + 32 r of
+// it in this lane) against j particles [jb, je) of the staged tile (jb a
+// multiple of kSubJ).
 template <int V, bool MASKED, bool MULTI, int RI, int MODE, bool AGG>
 __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P, const ItemDesc& it,
                                          const float4* __restrict__ sjA, const float2* __restrict__ sjZ,
-                                         uint32_t* sh, uint32_t* q, int tid, int lane, unsigned& ndeferred,
+                                         uint32_t* sh, uint32_t* q, int run, int lane, unsigned& ndeferred,
                                          float3 kt, int jb, int je) {
-  // each warp holds 32 * RI consecutive i particles: lane + 32 r of its run
-  const int ib = (tid >> 5) * (32 * RI) + lane;
+  const int ib = run * (32 * RI) + lane;
   // tile images: the image is subtracted from the coordinates, ti from the i's and
   // sj from the j's.  Orthorhombic (exact, see tile_image): k = -1 takes L from
   // the i's, k = +1 from the j's.  Triclinic: the i's move by the image vector
@@ -1324,35 +1325,61 @@ __device__ __forceinline__ void run_tile(const FrameDev* F, const FastParams& P,
   __syncwarp();
 }
 
+// Tiles of an item claimed dynamically: the warps take (i run, j sub-chunk)
+// tiles from lists per cost class, costliest first, so that a block's warps
+// reach the barrier at the end of the item within about one tile of each other
+// whatever mix of tile modes and culled tiles the item holds.
+constexpr int kSubPerTile = kTile / kSubJ;  // j sub-chunks per item
+constexpr int kCostClasses = 3;             // per-pair images, one axis per pair, uniform image
+struct TileLists {
+  unsigned char* list;  // kCostClasses lists of tile indices run * kSubPerTile + c, each `cap` long
+  int* count;           // per class, then the claim counter
+  int cap;
+};
+
+// The cost class of a tile that runs in `mode` (after the demotion of masked tiles).
+__device__ __forceinline__ int cost_class(int mode) { return mode == M_PAIR ? 0 : (mode == M_UNI ? 2 : 1); }
+
 // The decision parameters are reloaded per item (from the L1-cached frame
 // descriptor) so that only the fields of this variant are live in the loop.
 // MULTI: some sweep of the launch starts above bin 0, so the root is also
 // clamped from below (valid for every sweep, a separate kernel for registers).
-// For the periodic variants the j tile is taken in sub-chunks of kSubJ
-// particles; img[c] is this warp's tile image and mode (w) for sub-chunk c.
-// Items that mask j <= i take the per-pair path in the M_AXIS modes (fewer
-// instances; such items are the diagonal of a species block).
+// For the periodic variants (and no-box frames that bound their tiles) the j
+// tile is taken in sub-chunks of kSubJ particles; img[t] and tbeta[t] are the
+// image, mode (w) and beta of tile t = run * kSubPerTile + c, listed in `tl`.
+// Masked items (the diagonal of a species block) run every tile with
+// per-pair images (fewer instances).
 template <int V, bool MULTI, int RI, bool AGG>
 __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sjA, const float2* sjZ, uint32_t* sh,
-                         uint32_t* q, int tid, int lane, unsigned& ndeferred, const float4* img, const float* tbeta,
-                         bool bounds) {
+                         uint32_t* q, int warp, int lane, unsigned& ndeferred, const float4* img, const float* tbeta,
+                         TileLists tl, bool bounds) {
   FastParams P;
   load_fast_params(*F, it.pass, P);
-  if (V == V_ORTHO || V == V_TRIC) {
-    for (int c = 0; c * kSubJ < it.nj; ++c) {
+  if (V == V_ORTHO || V == V_TRIC || (V == V_NONE && bounds)) {
+    const int n0 = tl.count[0], n1 = n0 + tl.count[1], n = n1 + tl.count[2];
+    for (;;) {
+      int g = 0;
+      if (lane == 0) g = atomicAdd(tl.count + kCostClasses, 1);
+      g = __shfl_sync(kFull, g, 0);
+      if (g >= n) break;
+      const int k = g < n0 ? (int)tl.list[g] : (g < n1 ? (int)tl.list[tl.cap + g - n0] : (int)tl.list[2 * tl.cap + g - n1]);
+      const int run = k / kSubPerTile, c = k - run * kSubPerTile;
       const int jb = c * kSubJ, je = min(it.nj, jb + kSubJ);
-      const float4 im = img[c];
+      const float3 k0 = make_float3(0.f, 0.f, 0.f);
+      if (V == V_NONE) {
+        if (it.masked) run_tile<V, true, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, run, lane, ndeferred, k0, jb, je);
+        else run_tile<V, false, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, run, lane, ndeferred, k0, jb, je);
+        continue;
+      }
+      const float4 im = img[k];
       const float3 kt = make_float3(im.x, im.y, im.z);
-      int mode = (int)im.w;
-      if (mode == M_SKIP) continue;  // no pair of this tile has its bin in the sweep
-      if (it.masked && mode >= M_AXIS) mode = M_PAIR;
+      const int mode = it.masked ? M_PAIR : (int)im.w;
       // the tile's own beta; masked tiles demoted to per-pair images take the frame's
-      if (mode == (int)im.w) set_bound_beta(*F, P, tbeta[c]);
+      if (mode == (int)im.w) set_bound_beta(*F, P, tbeta[k]);
       else set_bound(*F, P, mode);
-#define DH_TILE(M_, K_) run_tile<V, M_, MULTI, RI, K_, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, kt, jb, je)
+#define DH_TILE(M_, K_) run_tile<V, M_, MULTI, RI, K_, AGG>(F, P, it, sjA, sjZ, sh, q, run, lane, ndeferred, kt, jb, je)
       if (it.masked) {
-        if (mode == M_UNI) DH_TILE(true, M_UNI);
-        else DH_TILE(true, M_PAIR);
+        DH_TILE(true, M_PAIR);
       } else {
         switch (mode) {
           case M_UNI: DH_TILE(false, M_UNI); break;
@@ -1367,22 +1394,13 @@ __device__ void run_item(const FrameDev* F, const ItemDesc& it, const float4* sj
     return;
   }
   const float3 k0 = make_float3(0.f, 0.f, 0.f);
-  if (V == V_NONE && bounds) {  // sub-chunk by sub-chunk, culled ones skipped
-    for (int c = 0; c * kSubJ < it.nj; ++c) {
-      if ((int)img[c].w == M_SKIP) continue;
-      const int jb = c * kSubJ, je = min(it.nj, jb + kSubJ);
-      if (it.masked) run_tile<V, true, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, jb, je);
-      else run_tile<V, false, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, jb, je);
-    }
-    return;
-  }
   if (it.masked) {
-    run_tile<V, true, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+    run_tile<V, true, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, warp, lane, ndeferred, k0, 0, it.nj);
   } else if (V == V_NONE && F->in_range && it.ni == kTile && (it.nj % kJUMax) == 0) {
     // every pair real (no NaN padding) and in range: the root needs no clamp
-    run_tile<V, false, MULTI, RI, M_UNI, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+    run_tile<V, false, MULTI, RI, M_UNI, AGG>(F, P, it, sjA, sjZ, sh, q, warp, lane, ndeferred, k0, 0, it.nj);
   } else {
-    run_tile<V, false, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, tid, lane, ndeferred, k0, 0, it.nj);
+    run_tile<V, false, MULTI, RI, M_PAIR, AGG>(F, P, it, sjA, sjZ, sh, q, warp, lane, ndeferred, k0, 0, it.nj);
   }
 }
 
@@ -1685,6 +1703,11 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
   __shared__ float4 s_img[kTileBounds ? BLOCK / 32 : 1][kTileBounds ? kTile / kSubJ : 1];
   __shared__ float s_beta[kTileImage ? BLOCK / 32 : 1][kTileImage ? kTile / kSubJ : 1];  // per-tile beta
   static_assert(!kTileBounds || BLOCK / 32 >= kTile / kSubJ, "one warp per j sub-chunk");
+  // the item's tiles to run, per cost class, and the counters of run_item
+  constexpr int kListCap = kTileBounds ? (BLOCK / 32) * kSubPerTile : 1;
+  static_assert(kListCap <= 256, "tile indices fit a byte");
+  __shared__ unsigned char s_list[kTileBounds ? kCostClasses : 1][kListCap];
+  __shared__ int s_cnt[kCostClasses + 1];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* q = sq + warp * kQueueCap;
@@ -1713,6 +1736,7 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
       long long item = run_next++;
       if (item >= L.n_items) s_it.valid = 0;
       else decode_item(L, item, s_it);
+      for (int k = 0; k <= kCostClasses; ++k) s_cnt[k] = 0;
     }
     __syncthreads();
     const ItemDesc it = s_it;
@@ -1811,13 +1835,17 @@ __global__ void __launch_bounds__(kTile / RI, min_blocks_per_sm<V, RI>()) pair_k
             }
             s_img[warp][c] = img;
             if (kTileImage) s_beta[warp][c] = tb;
+            if (!skip && ni_w > 0) {
+              const int cls = cost_class(it.masked ? M_PAIR : (int)img.w);
+              s_list[cls][atomicAdd(&s_cnt[cls], 1)] = (unsigned char)(warp * kSubPerTile + c);
+            }
           }
         }
-        __syncwarp();
+        __syncthreads();  // every tile listed
       }
       unsigned ndef = 0;
-      run_item<V, MULTI, RI, AGG>(it.fd, it, sjA, sjZ, sh, q, tid, lane, ndef, s_img[kTileBounds ? warp : 0],
-                             s_beta[kTileImage ? warp : 0], bounds);
+      run_item<V, MULTI, RI, AGG>(it.fd, it, sjA, sjZ, sh, q, warp, lane, ndef, &s_img[0][0], &s_beta[0][0],
+                                  TileLists{&s_list[0][0], s_cnt, kListCap}, bounds);
       if (lane == 0 && ndef) atomicAdd(&it.fd->deferred, (unsigned long long)ndef);
     }
     __syncthreads();
