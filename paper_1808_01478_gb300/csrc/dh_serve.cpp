@@ -4,8 +4,9 @@
 // The paper's engine (Sec. 3.3) feeds whole frames from a reader queue to
 // worker processes.  Here one scheduler thread per context keeps the GPU busy
 // with "waves": each wave is one launch of the persistent pair kernel over a
-// slice of the work items of every admitted request (a pair budget sized for a
-// few milliseconds, water-filled: the requests with the least work left first).  A request that arrives while others
+// slice of the work items of the admitted requests (a pair budget sized for a
+// few milliseconds, given to the requests with the least work left first; see
+// launch_wave).  A request that arrives while others
 // run is admitted as soon as pool memory and a slot are free, and its items
 // join the next wave next to the remaining items of the running requests, so
 // small frames are not stuck behind large ones.  Each minimum-image variant
@@ -509,8 +510,9 @@ dh_status Server::finalize_enqueue(Request& r) {
   return DH_OK;
 }
 
-// One wave of lane v: the lane's pair budget water-filled over the running
-// requests of that variant, as one pair-kernel launch.
+// One wave of lane v: the lane's pair budget over the running requests of that
+// variant, shortest remaining work first, as one pair-kernel launch per
+// histogram-width class.
 bool Server::launch_wave(int v) {
   Lane& ln = lanes_[v];
   int slot = -1;
@@ -538,13 +540,20 @@ bool Server::launch_wave(int v) {
   if (run.empty()) return false;
   WaveSlot& W = ln.slots[slot];
   const double pairs_per_item = (double)kTile * (double)kTile;
-  // Water-filling of the wave's pair budget: requests with the least work left
-  // first, each taking what it needs up to an equal share of what remains, so
-  // small requests finish in the wave they join and the rest of the budget goes
-  // to the larger ones in equal parts.
+  // The wave's pair budget goes to the requests with the least work left
+  // first, so small requests finish in the wave they join.  While every
+  // admitted request can run (no request waits for admission), the order is
+  // shortest remaining work first: each request takes all it needs and the
+  // rest of the budget goes to the next smallest (equal parts would let two
+  // large requests that overlap each finish about as late as both together).
+  // While requests wait for admission, each takes what it needs up to an equal
+  // share of what remains: the queue, not the order, sets their latency then,
+  // and equal shares keep the saturated throughput higher (measured).  Every
+  // request takes at least one work item per wave.
   std::stable_sort(run.begin(), run.end(),
                    [](const Request* a, const Request* b) { return a->n_items - a->next < b->n_items - b->next; });
-  double budget_left = ln.rate * wave_seconds_ * (queue_.empty() ? 1.0 : kSaturatedWaveFactor);
+  const bool saturated = !queue_.empty();
+  double budget_left = ln.rate * wave_seconds_ * (saturated ? kSaturatedWaveFactor : 1.0);
   // segments per histogram-width class: requests of very different widths run
   // in separate launches, each with the launch shape of its own width (one
   // wide request would otherwise give every request of the wave the shape of
@@ -566,7 +575,7 @@ bool Server::launch_wave(int v) {
         continue;
       }
     }
-    const double share = std::max(0.0, budget_left) / (double)(run.size() - q);
+    const double share = std::max(0.0, budget_left) / (saturated ? (double)(run.size() - q) : 1.0);
     int64_t take = std::max<int64_t>(1, (int64_t)(share / pairs_per_item));
     take = std::min(take, r->n_items - r->next);
     budget_left -= (double)take * pairs_per_item;
