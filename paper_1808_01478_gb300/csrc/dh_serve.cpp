@@ -511,8 +511,8 @@ dh_status Server::finalize_enqueue(Request& r) {
 }
 
 // One wave of lane v: the lane's pair budget over the running requests of that
-// variant, shortest remaining work first, as one pair-kernel launch per
-// histogram-width class.
+// variant, the least work left first (the order is stated below), as one
+// pair-kernel launch per histogram-width class.
 bool Server::launch_wave(int v) {
   Lane& ln = lanes_[v];
   int slot = -1;
