@@ -856,7 +856,7 @@ def run_gpu(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": round(t_total / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (binary64 re-decision of near-edge pairs)", "data": "synthetic",
-        "config": dict(workload_config(args, world), pairs_per_step=pairs_step),
+        "config": workload_config(args, world), "pairs_per_step": pairs_step,
         "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "matches_device_result": e2e_ok},
         "plain": plain,
