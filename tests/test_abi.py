@@ -118,6 +118,17 @@ def test_missing_library_fails_loudly(tmp_path):
     assert out.stdout.startswith("raised") and "libdh.so not found" in out.stdout, out.stdout
 
 
+def test_no_device_fails_loudly(lib):
+    # the library is present but no GPU is usable: creating a context returns
+    # DH_ERR_CUDA (raised by the binding) instead of computing on the CPU
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(dh.DHError) as e:
+        dh.Context(0)
+    assert e.value.status == dh.DH_ERR_CUDA
+
+
 @pytest.mark.parametrize("cname", ["dh_config", "dh_frame", "dh_stats"])
 def test_struct_layouts_match_the_header(tmp_path, cname):
     # the ctypes mirrors of the ABI structs against a C compiler's layout of dh.h
