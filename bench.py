@@ -6,6 +6,7 @@ through one dh_histogram_batch call (one persistent pair-kernel launch per
 minimum-image variant, replayed as a CUDA graph), inputs resident in HBM.  Printed on one JSON line:
 
   value          Gpairs/s of the batched step (device time, CUDA events)
+  pairs_per_step the pairs of one step (every unique pair of the three frames)
   e2e            the same metric through the C ABI with pinned HOST buffers:
                  host->device copy of the coordinates and device->host copy of
                  the histograms inside the timed region
@@ -15,6 +16,10 @@ minimum-image variant, replayed as a CUDA graph), inputs resident in HBM.  Print
   pipes          measured per-SM throughput of the pipes the pair kernel uses
   roofline       the pair kernel's pairs per second against the minimum over
                  those pipes of measured rate / operations per pair
+  batched        the batched step's launch shape, and C4 (256 frames of uneven
+                 N in one batched call against one plain call per frame)
+  served         C5: p50/p99 latency at offered loads 0.5/0.8/0.95 and the
+                 saturated throughput of dh_submit/dh_poll, against the plain path
   cpu_baseline   the FP64 oracle on the host cores, on a bounded sample
   clocks         nvidia-smi SM clocks and throttle reasons during the timed region
 
